@@ -1,0 +1,46 @@
+"""CPU FP64 oracle for the block-tridiagonal solve -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The product
+path (the C-ABI library and its Python binding) never imports, links or calls
+it, and this package never imports the product path.
+
+Contents (each function cites the passage of Terekhov, "A fast parallel
+algorithm for solving block-tridiagonal systems ...", arXiv:1108.4181, that it
+writes out):
+
+* ``blocktri``  -- the system of Section 2 (eq. main-eq) by definition: the
+  operator product, the assembled dense matrix, the exact solution by block
+  Gaussian elimination (block Thomas) and by dense LU, residual and error norms.
+* ``alg2``      -- the segment/interface decomposition of Section 2.2 written
+  out by definition: the responses of eqs. sub1-sub3, the reduced system of
+  eq. red1, Algorithm 1 applied to it, and the superposition of eq.
+  superposition.  Used to pin the GPU path's intermediate products.
+* ``adjoint``   -- gradients of a loss through X = P^{-1} F (not in the paper;
+  the standard adjoint identity dL/dP = -lambda X^T with P^T lambda = dL/dX).
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+against values fixed independently of this code (closed forms, library
+routines, invariants, brute force).  No function is "parity unpinned".
+"""
+
+from .blocktri import (  # noqa: F401
+    apply_P,
+    dense_P,
+    solve_dense,
+    solve_block_thomas,
+    residual,
+    rel_err,
+    rel_res,
+)
+from .alg2 import (  # noqa: F401
+    segment_rows,
+    segment_responses,
+    segment_W,
+    reduced_system,
+    reduced_rhs,
+    dichotomy_tree,
+    dichotomy_solve,
+    alg2_solve,
+)
+from .adjoint import transpose_blocks, adjoint_grads  # noqa: F401
