@@ -1,0 +1,178 @@
+/*
+ * bt.h -- C ABI of the block-tridiagonal dichotomy solver (GB300, sm_103a).
+ *
+ * Solves  -A_j X_{j-1} + C_j X_j - B_j X_{j+1} = F_j,  j = 1..N   (Section 2, eq. main-eq)
+ * for many right-hand-side panels against one factored matrix, by the two-stage
+ * scheme of Algorithm 2 (Section 2.2): a once-per-matrix preliminary stage
+ * (bt_factor) and a per-right-hand-side stage (bt_solve*).
+ *
+ * Conventions shared by every entry point
+ *   - Blocks A, B, C: float64 [N][M][M], row-major, block j at offset j*M*M.
+ *     A_1 (index 0) and B_N (index N-1) are not part of the system (the matrix
+ *     printed with eq. main-eq has no such entries); their contents are ignored.
+ *   - Panels F, X, G, dF: float64 [N][M][K] row-major, i.e. an (N*M) x K matrix
+ *     with K contiguous; block row j is the M x K tile at offset j*M*K.
+ *   - Unless stated otherwise pointers are DEVICE pointers owned by the caller,
+ *     on the CUDA device that is current when the call is made.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Solve calls only enqueue work on it and return; outputs are valid once
+ *     the stream has reached that point.
+ *   - Errors are reported as bt_status codes only; nothing is thrown across
+ *     the ABI.  bt_last_error() gives a human-readable detail string for the
+ *     calling thread's most recent failure.
+ *   - There is no CPU fallback: every arithmetic step runs in this library's
+ *     CUDA kernels; a call on a machine without a usable sm_103 GPU fails
+ *     with BT_ERR_CUDA.
+ */
+#ifndef BT_H_
+#define BT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bt_handle_s* bt_handle;
+
+typedef enum {
+  BT_OK = 0,
+  BT_ERR_ARG = 1,         /* invalid argument (sizes, null pointers, N % S != 0, ...) */
+  BT_ERR_SINGULAR = 2,    /* a pivot block of the factorisation is singular or non-finite */
+  BT_ERR_CUDA = 3,        /* a CUDA runtime call failed (detail in bt_last_error) */
+  BT_ERR_NOCONV = 4,      /* iterative refinement did not reach the requested tolerance */
+  BT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  BT_ERR_OOM = 6,         /* device memory allocation failed */
+  BT_ERR_UNSUPPORTED = 7  /* valid request that this build does not implement */
+} bt_status;
+
+typedef enum {
+  BT_PREC_F64 = 0,   /* every product in FP64 */
+  BT_PREC_TF32 = 1,  /* panel products on tensor cores in TF32, FP32 accumulation */
+  BT_PREC_BF16 = 2   /* panel products on tensor cores in BF16, FP32 accumulation */
+} bt_precision;
+
+/* Options of bt_solve_ex.  Zero-initialised options mean: FP64, defaults. */
+typedef struct {
+  int32_t precision;  /* bt_precision */
+  int32_t max_it;     /* refinement passes after the first solve (0 = default 12) */
+  double tol;         /* target ||F - P X||_F / ||F||_F (0 = default 1e-10) */
+  void* stream;       /* cudaStream_t */
+  int32_t k_tile;     /* right-hand-side columns per CTA (0 = automatic) */
+  int32_t reserved;
+} bt_opts;
+
+/* Result report of bt_solve_ex (filled only when a non-NULL pointer is given;
+ * the call then synchronises its stream before returning). */
+typedef struct {
+  int32_t iters;      /* refinement passes performed after the first solve */
+  int32_t converged;  /* 1 if rel_res <= tol */
+  double rel_res;     /* final ||F - P X||_F / ||F||_F, measured in FP64 */
+  double rel_res0;    /* the same after the first (unrefined) solve */
+} bt_info;
+
+/*
+ * bt_factor -- Algorithm 2, stage 1 (Section 2.2, steps 1.1-1.3), all in FP64
+ * on the GPU:
+ *   1.1  per segment, the block-sweep factorisation of the interior rows and
+ *        the coupling responses U, V of eqs. sub1 / sub2;
+ *   1.2  the reduced (interface) system of eq. red1;
+ *   1.3  the stored block rows of the inverses needed by Algorithm 1 on it.
+ * N   block rows (>= 1); M block size (1..256); S segments, 1 <= S <= N and
+ *     N % S == 0 (the paper's L = N/p); interface rows are 1, L+1, ..., (S-1)L+1.
+ * A, B, C  device pointers as described above; they are only read, and may be
+ *     freed once this call returns.
+ * out receives a handle that owns all factor memory on the current device.
+ * The call synchronises `stream` once to read the pivot status:
+ *   BT_ERR_SINGULAR if any pivot block is singular or non-finite (no handle
+ *   is returned), BT_ERR_ARG for invalid sizes or NULL pointers,
+ *   BT_ERR_OOM / BT_ERR_CUDA on device failures.
+ */
+bt_status bt_factor(int64_t N, int64_t M, const double* A, const double* B, const double* C,
+                    int64_t S, void* stream, bt_handle* out);
+
+/*
+ * bt_solve -- Algorithm 2, stage 2 (Section 2.2, steps 2.1-2.3) in FP64:
+ *   2.1  per-segment sweeps of eq. sub3 (W),
+ *   2.2  Algorithm 1 on the reduced system eq. red1 (interface unknowns),
+ *   2.3  every row from eq. superposition.
+ * F  device [N][M][K] right-hand sides (read only); X device [N][M][K] output.
+ * X must not overlap F.  K >= 1.  Asynchronous on `stream`.
+ * Scratch memory is taken from a pool owned by the handle (grown on demand);
+ * concurrent calls on one handle must use the same stream.
+ */
+bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* stream);
+
+/*
+ * bt_solve_ex -- stage 2 with a selectable precision.  BT_PREC_F64 is
+ * bt_solve.  BT_PREC_TF32 / BT_PREC_BF16 run the panel products of steps
+ * 2.1-2.3 on tcgen05 tensor cores with FP32 accumulation against rounded
+ * copies of the factors, and recover FP64 accuracy by iterative refinement
+ * against the FP64 residual F - P X (not in the paper): X_0 = S~ F,
+ * X_{k+1} = X_k + S~ (F - P X_k), until ||F - P X||_F <= tol ||F||_F or
+ * max_it passes.  F, X, K as for bt_solve.  When `info` is non-NULL the call
+ * synchronises the stream and fills it; with info == NULL it is asynchronous
+ * and never returns BT_ERR_NOCONV.
+ */
+bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts,
+                      bt_info* info);
+
+/*
+ * bt_solve_adjoint -- gradients of a loss through X = P^{-1} F (not in the
+ * paper).  With G = dL/dX, solves P^T lambda = G by the same stage-2 machinery
+ * on the factors of P^T (built on first use and kept in the handle) and forms
+ *   dF = lambda,  dC_j = -lambda_j X_j^T,  dA_j = lambda_j X_{j-1}^T (j > 1),
+ *   dB_j = lambda_j X_{j+1}^T (j < N),  dA_1 = dB_N = 0,
+ * each summed over the K columns.  X: the solution [N][M][K]; G: [N][M][K];
+ * dF: [N][M][K]; dA, dB, dC: [N][M][M] (any of the four outputs may be NULL).
+ * All device pointers, FP64.  Asynchronous on `stream`, except that the first
+ * call on a handle factors P^T and synchronises once.
+ */
+bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF,
+                           double* dA, double* dB, double* dC, void* stream);
+
+/* Releases the handle and all its device memory (synchronises the device). */
+void bt_destroy(bt_handle h);
+
+/* Static description of a status code. */
+const char* bt_strerror(bt_status s);
+
+/* Detail of the calling thread's most recent failure ("" if none). */
+const char* bt_last_error(void);
+
+/*
+ * bt_handle_query -- sizes of a factored handle.
+ * out[0] = N, out[1] = M, out[2] = S, out[3] = depth of the dichotomy tree,
+ * out[4] = 1 if the matrix has A_j = B_j = I and tridiagonal C_j (a stencil
+ * operator), else 0, out[5] = device bytes held by the handle.
+ */
+bt_status bt_handle_query(bt_handle h, int64_t out[6]);
+
+/*
+ * bt_factor_export -- copies one FP64 array of the factorisation into a
+ * caller-owned device buffer (diagnostics and step-wise verification).
+ *   what = 0: U  [N][M][M]   coupling response of eq. sub1 on interior rows
+ *   what = 1: V  [N][M][M]   coupling response of eq. sub2 on interior rows
+ *   what = 2: At [S][M][M]   reduced system of eq. red1, sub-diagonal blocks
+ *   what = 3: Ct [S][M][M]   reduced system, diagonal blocks
+ *   what = 4: Bt [S][M][M]   reduced system, super-diagonal blocks
+ * Rows that are interfaces hold zeros in U and V.  Synchronous.
+ */
+bt_status bt_factor_export(bt_handle h, int32_t what, double* dst);
+
+/*
+ * bt_solve_stages -- runs only the first `stages` steps of bt_solve's FP64
+ * pipeline (diagnostics and step-wise verification):
+ *   stages = 1: X holds W of eq. sub3 on interior rows (step 2.1);
+ *   stages = 2: additionally X holds X~ of eq. red1 on interface rows (step 2.2);
+ *   stages = 3: the full solution (step 2.3), identical to bt_solve.
+ * Rows not yet written are left untouched.  Asynchronous on `stream`.
+ */
+bt_status bt_solve_stages(bt_handle h, const double* F, int64_t K, double* X, int32_t stages,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BT_H_ */

@@ -1,0 +1,11 @@
+"""Block-tridiagonal dichotomy solver for GB300 (sm_103a).
+
+Terekhov, "A fast parallel algorithm for solving block-tridiagonal systems of
+linear equations including the domain decomposition method" (arXiv:1108.4181):
+Algorithm 2 with segments mapped to CTAs.  The compute path is the C-ABI
+library ``libbt.so`` (declared in ``include/bt.h``); this package only
+marshals arguments to it.
+"""
+
+from ._lib import BtError, load  # noqa: F401
+from .solver import Factorization, factor  # noqa: F401

@@ -1,0 +1,210 @@
+// C-ABI entry points: argument validation, handle lifetime, dispatch.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bt_internal.cuh"
+
+namespace bt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bt_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BT_ERR_OOM : BT_ERR_CUDA;
+}
+
+bt_status DevArena::alloc(void** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 16;
+  cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("device allocation of ") + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+    return BT_ERR_OOM;
+  }
+  blocks.push_back(*p);
+  bytes += n;
+  return BT_OK;
+}
+
+void DevArena::release() {
+  for (void* p : blocks) cudaFree(p);
+  blocks.clear();
+  bytes = 0;
+}
+
+static void destroy_handle(bt_handle_s* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->adj) destroy_handle(h->adj);
+  h->arena.release();
+  if (h->scratch) cudaFree(h->scratch);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+static bt_status check_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3) {
+    set_error("this library is built for sm_103a (GB300); the current device is sm_" +
+              std::to_string(prop.major) + std::to_string(prop.minor));
+    return BT_ERR_CUDA;
+  }
+  return BT_OK;
+}
+
+bt_status make_handle(int64_t N, int64_t M, const double* A, const double* B, const double* C, int64_t S,
+                      cudaStream_t st, bt_handle_s** out) {
+  *out = nullptr;
+  bt_handle_s* h = new (std::nothrow) bt_handle_s();
+  if (!h) {
+    set_error("bt_factor: host allocation failed");
+    return BT_ERR_OOM;
+  }
+  cudaGetDevice(&h->device);
+  h->N = N;
+  h->M = M;
+  h->S = S;
+  h->L = N / S;
+  bt_status s = factor_f64(h, A, B, C, st);
+  if (s != BT_OK) {
+    destroy_handle(h);
+    return s;
+  }
+  *out = h;
+  return BT_OK;
+}
+
+}  // namespace bt
+
+using namespace bt;
+
+extern "C" {
+
+const char* bt_strerror(bt_status s) {
+  switch (s) {
+    case BT_OK: return "ok";
+    case BT_ERR_ARG: return "invalid argument";
+    case BT_ERR_SINGULAR: return "singular or non-finite pivot block";
+    case BT_ERR_CUDA: return "CUDA error";
+    case BT_ERR_NOCONV: return "iterative refinement did not converge";
+    case BT_ERR_TIMEOUT: return "device-side wait timed out";
+    case BT_ERR_OOM: return "out of device memory";
+    case BT_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+const char* bt_last_error(void) { return g_last_error.c_str(); }
+
+bt_status bt_factor(int64_t N, int64_t M, const double* A, const double* B, const double* C, int64_t S,
+                    void* stream, bt_handle* out) {
+  if (!out) {
+    set_error("bt_factor: out is NULL");
+    return BT_ERR_ARG;
+  }
+  *out = nullptr;
+  if (N < 1 || M < 1 || M > 1024 || S < 1 || S > N || N % S != 0) {
+    set_error("bt_factor: need N >= 1, 1 <= M <= 1024, 1 <= S <= N and N % S == 0");
+    return BT_ERR_ARG;
+  }
+  if (!A || !B || !C) {
+    set_error("bt_factor: A, B and C must be device pointers");
+    return BT_ERR_ARG;
+  }
+  BT_TRY(check_device());
+  return make_handle(N, M, A, B, C, S, (cudaStream_t)stream, out);
+}
+
+bt_status bt_solve_stages(bt_handle h, const double* F, int64_t K, double* X, int32_t stages, void* stream) {
+  if (!h || !F || !X || K < 1 || stages < 1 || stages > 3) {
+    set_error("bt_solve: need a handle, device F and X, K >= 1 (stages in 1..3)");
+    return BT_ERR_ARG;
+  }
+  const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
+  const char* f0 = reinterpret_cast<const char*>(F);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  if (f0 < x0 + bytes && x0 < f0 + bytes) {
+    set_error("bt_solve: X must not overlap F");
+    return BT_ERR_ARG;
+  }
+  return solve_f64(h, F, K, X, stages, (cudaStream_t)stream);
+}
+
+bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* stream) {
+  return bt_solve_stages(h, F, K, X, 3, stream);
+}
+
+bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts, bt_info* info) {
+  bt_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precision == BT_PREC_F64) {
+    BT_TRY(bt_solve_stages(h, F, K, X, 3, o.stream));
+    if (info) {
+      BT_CUDA(cudaStreamSynchronize((cudaStream_t)o.stream));
+      info->iters = 0;
+      info->converged = 1;
+      info->rel_res = -1.0;
+      info->rel_res0 = -1.0;
+    }
+    return BT_OK;
+  }
+  set_error("bt_solve_ex: this precision is not available in this build");
+  return BT_ERR_UNSUPPORTED;
+}
+
+bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF, double* dA,
+                           double* dB, double* dC, void* stream) {
+  (void)h; (void)X; (void)G; (void)K; (void)dF; (void)dA; (void)dB; (void)dC; (void)stream;
+  set_error("bt_solve_adjoint: not available in this build");
+  return BT_ERR_UNSUPPORTED;
+}
+
+void bt_destroy(bt_handle h) { destroy_handle(h); }
+
+bt_status bt_handle_query(bt_handle h, int64_t out[6]) {
+  if (!h || !out) {
+    set_error("bt_handle_query: NULL argument");
+    return BT_ERR_ARG;
+  }
+  out[0] = h->N;
+  out[1] = h->M;
+  out[2] = h->S;
+  out[3] = h->depth;
+  out[4] = h->stencil;
+  out[5] = (int64_t)(h->arena.bytes + h->scratch_bytes);
+  return BT_OK;
+}
+
+bt_status bt_factor_export(bt_handle h, int32_t what, double* dst) {
+  if (!h || !dst || what < 0 || what > 4) {
+    set_error("bt_factor_export: need a handle, a device buffer and what in 0..4");
+    return BT_ERR_ARG;
+  }
+  const size_t MM = (size_t)h->M * h->M;
+  const double* src = nullptr;
+  size_t n = 0;
+  switch (what) {
+    case 0: src = h->U; n = h->N * MM; break;
+    case 1: src = h->V; n = h->N * MM; break;
+    case 2: src = h->At; n = h->S * MM; break;
+    case 3: src = h->Ct; n = h->S * MM; break;
+    case 4: src = h->Bt; n = h->S * MM; break;
+  }
+  BT_CUDA(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice));
+  return BT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA translation units of libbt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bt.h"
+
+namespace bt {
+
+// ---------------------------------------------------------------------------
+// Error handling: status codes only cross the ABI; details go to a
+// thread-local string read by bt_last_error().
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+bt_status cuda_fail(cudaError_t e, const char* what);
+
+#define BT_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::bt::cuda_fail(e_, #call);  \
+  } while (0)
+
+#define BT_TRY(call)                        \
+  do {                                      \
+    bt_status s_ = (call);                  \
+    if (s_ != BT_OK) return s_;             \
+  } while (0)
+
+// A node of the dichotomy tree over the S interface unknowns (Algorithm 1 on
+// the reduced system): sub-range [l, r], middle unknown m, tree level.
+struct TreeNode {
+  int l, r, m, level;
+};
+
+// Dichotomy tree with the split m = l + (r - l) / 2, breadth first.
+std::vector<TreeNode> build_tree(int S, int* depth_out);
+
+// Device memory owned by a handle: a list of allocations freed together.
+struct DevArena {
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  bt_status alloc(void** p, size_t n);
+  void release();
+};
+
+}  // namespace bt
+
+// Everything a handle owns.  Block arrays are FP64, row-major M x M blocks.
+struct bt_handle_s {
+  int device = 0;
+  int64_t N = 0, M = 0, S = 0, L = 0;
+  int depth = 0;
+  int stencil = 0;  // A_j = B_j = I, C_j tridiagonal
+
+  bt::DevArena arena;
+
+  // Copies of the operator (A[0] and B[N-1] zeroed): the residual and the
+  // adjoint need P after the caller's buffers are gone.
+  double* A = nullptr;
+  double* B = nullptr;
+  double* C = nullptr;
+
+  // Segment factors, indexed by global block row (interface rows unused):
+  // D_i^{-1}, E_i = D_i^{-1} A_i, G_i = D_i^{-1} B_i (Gamma), and the coupling
+  // responses U_i, V_i of eqs. sub1 / sub2.
+  double* Dinv = nullptr;
+  double* E = nullptr;
+  double* G = nullptr;
+  double* U = nullptr;
+  double* V = nullptr;
+
+  // Reduced system of eq. red1, [S][M][M].
+  double* At = nullptr;
+  double* Ct = nullptr;
+  double* Bt = nullptr;
+
+  // Dichotomy tree: R[level][j] = block (m, j) of the inverse of the node's
+  // sub-matrix for the node containing j at that level; HL / HR indexed by
+  // the node's middle unknown m.
+  double* R = nullptr;
+  double* HL = nullptr;
+  double* HR = nullptr;
+  std::vector<bt::TreeNode> nodes;     // breadth-first, grouped by level
+  std::vector<int> level_off;          // nodes of level l: [level_off[l], level_off[l+1])
+  int* d_nodes = nullptr;              // device copy: (l, r, m) per node
+  int* d_mid_level = nullptr;          // level at which interface s is the middle unknown
+
+  // Solve scratch (grown on demand): series terms c[level][s] (M x K each).
+  double* scratch = nullptr;
+  size_t scratch_bytes = 0;
+
+  // Factors of P^T, built on the first adjoint call.
+  bt_handle_s* adj = nullptr;
+};
+
+namespace bt {
+
+// Factorisation (Algorithm 2 stage 1) into an allocated handle.
+bt_status factor_f64(bt_handle_s* h, const double* A, const double* B, const double* C,
+                     cudaStream_t st);
+
+// FP64 stage-2 pipeline; `stages` in 1..3 (see bt_solve_stages).
+bt_status solve_f64(bt_handle_s* h, const double* F, int64_t K, double* X, int stages,
+                    cudaStream_t st);
+
+// Grows the handle's scratch pool to at least `bytes`.
+bt_status ensure_scratch(bt_handle_s* h, size_t bytes, cudaStream_t st);
+
+}  // namespace bt
