@@ -36,6 +36,10 @@ class BtInfo(ctypes.Structure):
                 ("rel_res0", ctypes.c_double)]
 
 
+class BtKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _i64), ("total_ms", ctypes.c_double)]
+
+
 SIGNATURES = {
     "bt_factor": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _i64, _vp, ctypes.POINTER(_vp)]),
     "bt_solve": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
@@ -47,6 +51,8 @@ SIGNATURES = {
     "bt_handle_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "bt_factor_export": (ctypes.c_int, [_vp, _i32, _vp]),
     "bt_solve_stages": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
+    "bt_profile_enable": (ctypes.c_int, [_vp, _i32]),
+    "bt_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(BtKernelStat), _i32, ctypes.POINTER(_i32)]),
 }
 
 _LIB = None

@@ -53,9 +53,26 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every CUDA source and link libbt.so; returns the library path."""
+    """Compile every CUDA source and link libbt.so; returns the library path.
+
+    Concurrent callers (one per rank) serialise on a lock file; the first
+    builds, the others find the library up to date."""
     if not force and up_to_date():
         return LIB
+    import fcntl
+
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build_locked(verbose, extra_flags)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra_flags) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     flags = NVCC_FLAGS + list(extra_flags or [])

@@ -36,6 +36,47 @@ void DevArena::release() {
   bytes = 0;
 }
 
+cudaEvent_t Profiler::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Profiler::collect() {
+  for (const Rec& r : recs) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    size_t k = 0;
+    while (k < names.size() && names[k] != r.name) ++k;
+    if (k == names.size()) {
+      names.push_back(r.name);
+      launches.push_back(0);
+      total_ms.push_back(0.0);
+    }
+    launches[k] += 1;
+    total_ms[k] += ms;
+    pool.push_back(r.a);
+    pool.push_back(r.b);
+  }
+  recs.clear();
+}
+
+void Profiler::destroy() {
+  for (const Rec& r : recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  recs.clear();
+  for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
+
 static void destroy_handle(bt_handle_s* h) {
   if (!h) return;
   int prev = 0;
@@ -43,6 +84,7 @@ static void destroy_handle(bt_handle_s* h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   if (h->adj) destroy_handle(h->adj);
+  h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
   cudaSetDevice(prev);
@@ -204,6 +246,35 @@ bt_status bt_factor_export(bt_handle h, int32_t what, double* dst) {
     case 4: src = h->Bt; n = h->S * MM; break;
   }
   BT_CUDA(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice));
+  return BT_OK;
+}
+
+bt_status bt_profile_enable(bt_handle h, int32_t enable) {
+  if (!h) {
+    set_error("bt_profile_enable: NULL handle");
+    return BT_ERR_ARG;
+  }
+  h->prof.on = enable != 0;
+  return BT_OK;
+}
+
+bt_status bt_profile_read(bt_handle h, bt_kernel_stat* out, int32_t cap, int32_t* n) {
+  if (!h || !n || (cap > 0 && !out)) {
+    set_error("bt_profile_read: NULL argument");
+    return BT_ERR_ARG;
+  }
+  h->prof.collect();
+  const int32_t cnt = (int32_t)h->prof.names.size();
+  for (int32_t k = 0; k < cnt && k < cap; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, h->prof.names[k].c_str(), sizeof(out[k].name) - 1);
+    out[k].launches = h->prof.launches[k];
+    out[k].total_ms = h->prof.total_ms[k];
+  }
+  *n = cnt;
+  h->prof.names.clear();
+  h->prof.launches.clear();
+  h->prof.total_ms.clear();
   return BT_OK;
 }
 

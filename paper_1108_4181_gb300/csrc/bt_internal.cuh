@@ -39,6 +39,23 @@ struct TreeNode {
 // Dichotomy tree with the split m = l + (r - l) / 2, breadth first.
 std::vector<TreeNode> build_tree(int S, int* depth_out);
 
+// Per-kernel CUDA-event timing, enabled per handle (bt_profile_enable).
+struct Profiler {
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  bool on = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::string> names;
+  std::vector<int64_t> launches;
+  std::vector<double> total_ms;
+  cudaEvent_t get();
+  void collect();   // synchronises pending records into the totals
+  void destroy();
+};
+
 // Device memory owned by a handle: a list of allocations freed together.
 struct DevArena {
   std::vector<void*> blocks;
@@ -95,7 +112,27 @@ struct bt_handle_s {
 
   // Factors of P^T, built on the first adjoint call.
   bt_handle_s* adj = nullptr;
+
+  bt::Profiler prof;
 };
+
+namespace bt {
+// Records an event pair around one kernel launch when profiling is on.
+struct ProfScope {
+  Profiler* p;
+  cudaStream_t st;
+  ProfScope(bt_handle_s* h, cudaStream_t s, const char* name) : p(h->prof.on ? &h->prof : nullptr), st(s) {
+    if (p) {
+      Profiler::Rec r{name, p->get(), p->get()};
+      cudaEventRecord(r.a, st);
+      p->recs.push_back(r);
+    }
+  }
+  ~ProfScope() {
+    if (p) cudaEventRecord(p->recs.back().b, st);
+  }
+};
+}  // namespace bt
 
 namespace bt {
 

@@ -234,14 +234,19 @@ bt_status launch_all(bt_handle_s* h, F64Args a, const double* F, double* X, int 
       BT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   }
   if (a.L > 1) {
+    ProfScope ps(h, st, "f64_sweep");
     k_sweep<CW><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm2, st>>>(a, F, X);
     BT_CUDA(cudaGetLastError());
   }
   if (stages < 2) return BT_OK;
-  k_iface<CW><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm3, st>>>(a, F, X);
+  {
+    ProfScope ps(h, st, "f64_iface");
+    k_iface<CW><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm3, st>>>(a, F, X);
+  }
   BT_CUDA(cudaGetLastError());
   for (int lev = 0; lev < h->depth; ++lev) {
     const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
+    ProfScope ps(h, st, "f64_dichotomy");
     k_dichotomy<CW><<<dim3(nn, (unsigned)ntiles), threads, sm2, st>>>(a, lev, n0, X);
     BT_CUDA(cudaGetLastError());
   }
@@ -251,7 +256,10 @@ bt_status launch_all(bt_handle_s* h, F64Args a, const double* F, double* X, int 
   int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(rows, (4 * 152 + a.S * ntiles - 1) / (a.S * ntiles)));
   const int rows_per_cta = (int)((rows + chunks - 1) / chunks);
   chunks = (rows + rows_per_cta - 1) / rows_per_cta;
-  k_correct<CW><<<dim3((unsigned)a.S, (unsigned)ntiles, (unsigned)chunks), threads, sm2, st>>>(a, X, rows_per_cta);
+  {
+    ProfScope ps(h, st, "f64_correct");
+    k_correct<CW><<<dim3((unsigned)a.S, (unsigned)ntiles, (unsigned)chunks), threads, sm2, st>>>(a, X, rows_per_cta);
+  }
   BT_CUDA(cudaGetLastError());
   return BT_OK;
 }

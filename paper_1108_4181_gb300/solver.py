@@ -120,6 +120,18 @@ class Factorization:
         _lib.check(_lib.load().bt_factor_export(self._h, code, _ptr(dst)), "bt_factor_export")
         return dst
 
+    def profile(self, enable: bool):
+        """Turn per-kernel CUDA-event timing of later launches on or off."""
+        _lib.check(_lib.load().bt_profile_enable(self._h, 1 if enable else 0), "bt_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last read."""
+        cap = 64
+        buf = (_lib.BtKernelStat * cap)()
+        n = ctypes.c_int32()
+        _lib.check(_lib.load().bt_profile_read(self._h, buf, cap, ctypes.byref(n)), "bt_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, cap))}
+
     def adjoint(self, X: torch.Tensor, G: torch.Tensor, want=("F", "A", "B", "C"),
                 stream: Optional[torch.cuda.Stream] = None):
         """(dF, dA, dB, dC) for upstream gradient G = dL/dX at the solution X."""
