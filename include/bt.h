@@ -49,7 +49,8 @@ typedef enum {
 typedef enum {
   BT_PREC_F64 = 0,   /* every product in FP64 */
   BT_PREC_TF32 = 1,  /* panel products on tensor cores in TF32, FP32 accumulation */
-  BT_PREC_BF16 = 2   /* panel products on tensor cores in BF16, FP32 accumulation */
+  BT_PREC_BF16 = 2,  /* panel products on tensor cores in BF16, FP32 accumulation */
+  BT_PREC_F32 = 3    /* panel products on the CUDA cores in FP32 */
 } bt_precision;
 
 /* Options of bt_solve_ex.  Zero-initialised options mean: FP64, defaults. */
@@ -107,7 +108,8 @@ bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* str
  * bt_solve_ex -- stage 2 with a selectable precision.  BT_PREC_F64 is
  * bt_solve.  BT_PREC_TF32 / BT_PREC_BF16 run the panel products of steps
  * 2.1-2.3 on tcgen05 tensor cores with FP32 accumulation against rounded
- * copies of the factors, and recover FP64 accuracy by iterative refinement
+ * copies of the factors (BT_PREC_F32: FP32 on the CUDA cores), and recover
+ * FP64 accuracy by iterative refinement
  * against the FP64 residual F - P X (not in the paper): X_0 = S~ F,
  * X_{k+1} = X_k + S~ (F - P X_k), until ||F - P X||_F <= tol ||F||_F or
  * max_it passes.  F, X, K as for bt_solve.  When `info` is non-NULL the call
@@ -170,6 +172,24 @@ bt_status bt_factor_export(bt_handle h, int32_t what, double* dst);
  */
 bt_status bt_solve_stages(bt_handle h, const double* F, int64_t K, double* X, int32_t stages,
                           void* stream);
+
+/*
+ * Per-kernel timing (diagnostics for the benchmark; not in the paper).
+ * bt_profile_enable(h, 1) makes every later launch on this handle record a
+ * CUDA event pair on its stream around each kernel; 0 stops recording.
+ * bt_profile_read synchronises the recorded events, writes up to `cap`
+ * per-kernel totals (launch count and summed device time in milliseconds,
+ * grouped by kernel name) to `out`, sets *n to the number of kernel names and
+ * clears the totals.  Timing adds two event records per launch.
+ */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} bt_kernel_stat;
+
+bt_status bt_profile_enable(bt_handle h, int32_t enable);
+bt_status bt_profile_read(bt_handle h, bt_kernel_stat* out, int32_t cap, int32_t* n);
 
 #ifdef __cplusplus
 }

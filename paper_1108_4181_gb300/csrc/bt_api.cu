@@ -87,6 +87,8 @@ static void destroy_handle(bt_handle_s* h) {
   h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
+  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->ir_state})
+    if (q) cudaFree(q);
   cudaSetDevice(prev);
   delete h;
 }
@@ -203,8 +205,22 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
     }
     return BT_OK;
   }
-  set_error("bt_solve_ex: this precision is not available in this build");
-  return BT_ERR_UNSUPPORTED;
+  if (!h || !F || !X || K < 1) {
+    set_error("bt_solve_ex: need a handle, device F and X, K >= 1");
+    return BT_ERR_ARG;
+  }
+  if (o.precision < 0 || o.precision > 3) {
+    set_error("bt_solve_ex: unknown precision");
+    return BT_ERR_ARG;
+  }
+  const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
+  const char* f0 = reinterpret_cast<const char*>(F);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  if (f0 < x0 + bytes && x0 < f0 + bytes) {
+    set_error("bt_solve_ex: X must not overlap F");
+    return BT_ERR_ARG;
+  }
+  return solve_refined(h, F, K, X, o, info);
 }
 
 bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF, double* dA,

@@ -66,6 +66,15 @@ struct DevArena {
 
 }  // namespace bt
 
+// Rounded copies of the factors used by the low-precision solves (same
+// row-major block layout as the FP64 arrays; AK / BK are the coupling blocks
+// A_{k_s}, B_{k_s} of the interface rows, [S][M][M]).
+struct LowFactors {
+  float *Dinv = nullptr, *E = nullptr, *G = nullptr, *U = nullptr, *V = nullptr;
+  float *AK = nullptr, *BK = nullptr, *R = nullptr, *HL = nullptr, *HR = nullptr;
+  bool ready = false;
+};
+
 // Everything a handle owns.  Block arrays are FP64, row-major M x M blocks.
 struct bt_handle_s {
   int device = 0;
@@ -90,6 +99,12 @@ struct bt_handle_s {
   double* U = nullptr;
   double* V = nullptr;
 
+  // Coupling blocks of the interface rows, A_{k_s} and B_{k_s}, [S][M][M].
+  double* AK = nullptr;
+  double* BK = nullptr;
+  // Diagonals of C_j ([N][M][3]: sub, main, super) when the operator is a stencil.
+  double* Cdiag = nullptr;
+
   // Reduced system of eq. red1, [S][M][M].
   double* At = nullptr;
   double* Ct = nullptr;
@@ -112,6 +127,16 @@ struct bt_handle_s {
 
   // Factors of P^T, built on the first adjoint call.
   bt_handle_s* adj = nullptr;
+
+  LowFactors f32;
+
+  // Refinement buffers (grown on demand): residual panel, work panel,
+  // series terms and the device-side refinement state.
+  void* lp_r = nullptr;
+  void* lp_d = nullptr;
+  void* lp_c = nullptr;
+  size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0;
+  void* ir_state = nullptr;
 
   bt::Profiler prof;
 };
@@ -146,5 +171,19 @@ bt_status solve_f64(bt_handle_s* h, const double* F, int64_t K, double* X, int s
 
 // Grows the handle's scratch pool to at least `bytes`.
 bt_status ensure_scratch(bt_handle_s* h, size_t bytes, cudaStream_t st);
+
+// FP32 stage-2 pipeline on the CUDA cores: r -> work panel d (y, W, X~), then
+// X = (accumulate ? X : 0) + solution.  Returns at once when *done != 0.
+bt_status solve_simt_f32(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, double* X, int accumulate,
+                         const int* done, cudaStream_t st);
+// Only the interface steps (F~, series terms, dichotomy) of the FP32 pipeline.
+bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, const int* done,
+                                   cudaStream_t st);
+
+// Builds h->f32 from the FP64 factors (once per handle).
+bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st);
+
+// Mixed-precision solve with iterative refinement (bt_solve_ex).
+bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info);
 
 }  // namespace bt

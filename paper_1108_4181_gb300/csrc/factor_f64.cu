@@ -204,6 +204,29 @@ __global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst,
     dst[i] = src[i];
 }
 
+// dst[s] = src[s * L] for s < S (blocks of MM doubles).
+__global__ void k_gather_blocks(const double* __restrict__ src, double* __restrict__ dst, int64_t S, int64_t L,
+                                size_t MM) {
+  const size_t n = (size_t)S * MM;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = e / MM, o = e % MM;
+    dst[e] = src[s * L * MM + o];
+  }
+}
+
+// Cdiag[j][m] = (C_j[m][m-1], C_j[m][m], C_j[m][m+1]), zero outside the block.
+__global__ void k_tridiag(const double* __restrict__ C, double* __restrict__ Cd, int64_t N, int M) {
+  const size_t n = (size_t)N * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = e / M;
+    const int m = (int)(e % M);
+    const double* Cj = C + j * (size_t)M * M + (size_t)m * M;
+    Cd[3 * e + 0] = m > 0 ? Cj[m - 1] : 0.0;
+    Cd[3 * e + 1] = Cj[m];
+    Cd[3 * e + 2] = m + 1 < M ? Cj[m + 1] : 0.0;
+  }
+}
+
 __global__ void k_set_identity(double* I, int M) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * M; e += gridDim.x * blockDim.x)
     I[e] = (e / M == e % M) ? 1.0 : 0.0;
@@ -515,6 +538,14 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
 
   // stencil detection (A_j = B_j = I, tridiagonal C_j) for the residual
   k_detect_stencil<<<1024, 256, 0, st>>>(h->A, h->B, h->C, N, M, dstatus + 1);
+  BT_CUDA(cudaGetLastError());
+  // interface coupling blocks and the tridiagonal part of C
+  BT_TRY(ar.alloc((void**)&h->AK, S * MM * sizeof(double)));
+  BT_TRY(ar.alloc((void**)&h->BK, S * MM * sizeof(double)));
+  BT_TRY(ar.alloc((void**)&h->Cdiag, (size_t)N * M * 3 * sizeof(double)));
+  k_gather_blocks<<<256, 256, 0, st>>>(h->A, h->AK, S, L, MM);
+  k_gather_blocks<<<256, 256, 0, st>>>(h->B, h->BK, S, L, MM);
+  k_tridiag<<<256, 256, 0, st>>>(h->C, h->Cdiag, N, M);
   BT_CUDA(cudaGetLastError());
 
   // tree tables for the solve kernels

@@ -1,0 +1,277 @@
+// Mixed-precision solve with iterative refinement (not in the paper).
+//
+//   X_0 = S~ F,   X_{k+1} = X_k + S~ (F - P X_k)
+//
+// S~ is Algorithm 2's stage 2 run with rounded factors (FP32 on the CUDA cores,
+// or BF16 / TF32 on the tensor cores with FP32 accumulation); the residual
+// F - P X is formed in FP64 from the operator kept in the handle.  The loop is
+// unrolled on the host with a device-side stop flag: after every residual a
+// one-thread kernel compares ||r||_F^2 with tol^2 ||F||_F^2, and once the flag
+// is set every later kernel of the sequence returns at once, so the whole
+// refinement is enqueued without a host round trip.
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "bt_internal.cuh"
+
+namespace bt {
+
+namespace {
+
+constexpr int kMaxPasses = 64;
+
+struct IrState {
+  double fn2;               // ||F||_F^2
+  double rn2[kMaxPasses];   // ||F - P X_k||_F^2
+  int done;                 // 1 converged, 2 stalled
+  int last;                 // index of the last residual computed
+  int solves;               // stage-2 solves performed
+  int pad;
+};
+
+template <typename T>
+__device__ __forceinline__ T to_lp(double v);
+template <>
+__device__ __forceinline__ float to_lp<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+__device__ __forceinline__ void block_add(double v, double* target) {
+  __shared__ double red[32];
+  __syncthreads();  // red[] may still be read by a previous call
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x / 32) ? red[l] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (l == 0 && v != 0.0) atomicAdd(target, v);
+  }
+}
+
+// r = F - P X for A_j = B_j = I and tridiagonal C_j (FP64 arithmetic, rounded
+// to the solve precision on store).  first != 0: X = 0, r = F, and ||F||^2 is
+// accumulated as well.
+template <typename TR>
+__global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict__ F, const double* __restrict__ X,
+                                                      const double* __restrict__ Cd, TR* __restrict__ r,
+                                                      int64_t N, int M, int64_t K, int first, int pass,
+                                                      IrState* st) {
+  if (st->done) return;
+  const size_t MK = (size_t)M * K, n = (size_t)N * MK;
+  double acc = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = F[e];
+    if (!first) {
+      const size_t j = e / MK;
+      const size_t rem = e % MK;
+      const int m = (int)(rem / K);
+      const double* cd = Cd + 3 * (j * M + m);
+      double cx = cd[1] * X[e];
+      if (m > 0) cx += cd[0] * X[e - K];
+      if (m + 1 < M) cx += cd[2] * X[e + K];
+      v -= cx;
+      if (j > 0) v += X[e - MK];
+      if (j + 1 < (size_t)N) v += X[e + MK];
+    }
+    r[e] = to_lp<TR>(v);
+    acc += v * v;
+  }
+  block_add(acc, first ? &st->fn2 : &st->rn2[pass]);
+  if (first) block_add(acc, &st->rn2[0]);
+}
+
+// r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
+// One CTA per (block row, column tile); a thread owns row m and CW columns.
+template <typename TR, int CW>
+__global__ void k_resid_dense(const double* __restrict__ F, const double* __restrict__ X,
+                              const double* __restrict__ A, const double* __restrict__ B,
+                              const double* __restrict__ C, TR* __restrict__ r, int64_t N, int M, int64_t K,
+                              int pass, IrState* st) {
+  if (st->done) return;
+  extern __shared__ double sm[];
+  const int CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const int64_t j = blockIdx.x, col0 = (int64_t)blockIdx.y * kt, col = col0 + c0;
+  const size_t MM = (size_t)M * M, MK = (size_t)M * K;
+  double* xm = sm;
+  double* x0 = sm + M * kt;
+  double* xp = sm + 2 * M * kt;
+  for (int e = t; e < M * kt; e += blockDim.x) {
+    const int rr = e / kt, cc = e % kt;
+    const int64_t cl = col0 + cc;
+    const bool ok = cl < K;
+    x0[e] = ok ? X[j * MK + (size_t)rr * K + cl] : 0.0;
+    xm[e] = (ok && j > 0) ? X[(j - 1) * MK + (size_t)rr * K + cl] : 0.0;
+    xp[e] = (ok && j + 1 < N) ? X[(j + 1) * MK + (size_t)rr * K + cl] : 0.0;
+  }
+  __syncthreads();
+  double acc[CW];
+  double part = 0.0;
+  if (m < M) {
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = (col + c < K) ? F[j * MK + (size_t)m * K + col + c] : 0.0;
+    const double* Ar = A + j * MM + (size_t)m * M;
+    const double* Br = B + j * MM + (size_t)m * M;
+    const double* Cr = C + j * MM + (size_t)m * M;
+    for (int k = 0; k < M; ++k) {
+      const double a = __ldg(Ar + k), b = __ldg(Br + k), cc = __ldg(Cr + k);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        acc[c] = fma(a, xm[k * kt + c0 + c], acc[c]);
+        acc[c] = fma(b, xp[k * kt + c0 + c], acc[c]);
+        acc[c] = fma(-cc, x0[k * kt + c0 + c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (col + c < K) {
+        r[j * MK + (size_t)m * K + col + c] = to_lp<TR>(acc[c]);
+        part += acc[c] * acc[c];
+      }
+  }
+  block_add(part, &st->rn2[pass]);
+}
+
+__global__ void k_ir_check(IrState* st, int pass, double tol2) {
+  if (st->done) return;
+  st->last = pass;
+  if (pass == 0) return;
+  const double r2 = st->rn2[pass];
+  if (r2 <= tol2 * st->fn2) {
+    st->done = 1;
+  } else if (pass >= 3 && r2 >= 0.9 * st->rn2[pass - 1] && st->rn2[pass - 1] >= 0.9 * st->rn2[pass - 2]) {
+    st->done = 2;  // two passes without a 10 % reduction: stalled
+  }
+}
+
+__global__ void k_count_solve(IrState* st) {
+  if (!st->done) st->solves += 1;
+}
+
+template <typename Tin>
+__global__ void k_cast(const double* __restrict__ src, Tin* __restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (Tin)src[e];
+}
+
+bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
+  if (need <= *have) return BT_OK;
+  if (*p) {
+    BT_CUDA(cudaStreamSynchronize(st));
+    BT_CUDA(cudaFree(*p));
+    *p = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(p, need);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("refinement buffer allocation failed: ") + cudaGetErrorString(e));
+    return BT_ERR_OOM;
+  }
+  *have = need;
+  return BT_OK;
+}
+
+template <typename TR>
+bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int first, int pass,
+                          IrState* st, cudaStream_t s) {
+  const int M = (int)h->M;
+  ProfScope ps(h, s, "residual");
+  if (first || h->stencil) {
+    const size_t n = (size_t)h->N * M * K;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+    k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st);
+  } else {
+    constexpr int CW = 4;
+    const int CG = std::max(1, std::min(1024 / M, std::max(1, 128 / M)));
+    const int kt = CW * CG;
+    const int64_t ntiles = (K + kt - 1) / kt;
+    const size_t smem = 3 * (size_t)M * kt * sizeof(double);
+    if (smem > 48 * 1024)
+      BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_resid_dense<TR, CW><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(F, X, h->A, h->B, h->C, r,
+                                                                                       h->N, M, K, pass, st);
+  }
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+}  // namespace
+
+bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st) {
+  LowFactors& f = h->f32;
+  if (f.ready) return BT_OK;
+  const size_t MM = (size_t)h->M * h->M, NB = (size_t)h->N * MM, SB = (size_t)h->S * MM;
+  DevArena& ar = h->arena;
+  struct Item {
+    float** dst;
+    const double* src;
+    size_t n;
+  } items[] = {{&f.Dinv, h->Dinv, NB}, {&f.E, h->E, NB},   {&f.G, h->G, NB},   {&f.U, h->U, NB},
+               {&f.V, h->V, NB},       {&f.AK, h->AK, SB}, {&f.BK, h->BK, SB}, {&f.R, h->R, (size_t)h->depth * SB},
+               {&f.HL, h->HL, SB},     {&f.HR, h->HR, SB}};
+  for (auto& it : items) {
+    BT_TRY(ar.alloc((void**)it.dst, it.n * sizeof(float)));
+    k_cast<float><<<1024, 256, 0, st>>>(it.src, *it.dst, it.n);
+  }
+  BT_CUDA(cudaGetLastError());
+  f.ready = true;
+  return BT_OK;
+}
+
+bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info) {
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : 12;
+  const double tol = o.tol > 0 ? o.tol : 1e-10;
+  if (o.precision != 3) {
+    set_error("bt_solve_ex: this precision is not available in this build");
+    return BT_ERR_UNSUPPORTED;
+  }
+  const size_t panel = (size_t)h->N * h->M * K * sizeof(float);
+  const size_t cbytes = (size_t)h->depth * h->S * h->M * K * sizeof(float);
+  BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
+  BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
+  BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));
+  if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
+  BT_TRY(make_f32_factors(h, s));
+  IrState* st = reinterpret_cast<IrState*>(h->ir_state);
+  float* r = reinterpret_cast<float*>(h->lp_r);
+  float* d = reinterpret_cast<float*>(h->lp_d);
+  float* c = reinterpret_cast<float*>(h->lp_c);
+  const int* done = &st->done;
+  BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), s));
+  const double tol2 = tol * tol;
+  BT_TRY(launch_residual<float>(h, F, X, r, K, 1, 0, st, s));
+  k_ir_check<<<1, 1, 0, s>>>(st, 0, tol2);
+  BT_TRY(solve_simt_f32(h, r, K, d, c, X, 0, done, s));
+  for (int pass = 1; pass <= max_it + 1; ++pass) {
+    BT_TRY(launch_residual<float>(h, F, X, r, K, 0, pass, st, s));
+    k_ir_check<<<1, 1, 0, s>>>(st, pass, tol2);
+    if (pass <= max_it) {
+      k_count_solve<<<1, 1, 0, s>>>(st);
+      BT_TRY(solve_simt_f32(h, r, K, d, c, X, 1, done, s));
+    }
+  }
+  BT_CUDA(cudaGetLastError());
+  if (info) {
+    IrState hs;
+    BT_CUDA(cudaMemcpyAsync(&hs, st, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+    BT_CUDA(cudaStreamSynchronize(s));
+    info->iters = hs.solves;
+    info->converged = hs.done == 1 ? 1 : 0;
+    info->rel_res = hs.fn2 > 0 ? std::sqrt(hs.rn2[hs.last] / hs.fn2) : 0.0;
+    info->rel_res0 = hs.fn2 > 0 ? std::sqrt(hs.rn2[1] / hs.fn2) : 0.0;
+    if (!info->converged) {
+      set_error("bt_solve_ex: refinement stopped at relative residual " + std::to_string(info->rel_res));
+      return BT_ERR_NOCONV;
+    }
+  }
+  return BT_OK;
+}
+
+}  // namespace bt

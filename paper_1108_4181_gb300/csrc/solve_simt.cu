@@ -1,0 +1,423 @@
+// Algorithm 2, stage 2 (Section 2.2, steps 2.1-2.3) on the CUDA cores, for
+// FP64 (the plain path) and FP32 (the SIMT low-precision solve used inside
+// iterative refinement, and for the interface steps of the tensor-core path).
+//
+// On GB300 the FP64 pipe issues about 2 fused multiply-adds per clock per SM
+// (1.2 TFLOP/s for the chip), so the FP64 kernels are bound by FP64 issue, not
+// by memory: a thread owns one row m of an M x kt output tile and CW of its
+// columns, keeps CW independent accumulators, streams its block row from
+// global memory (L1-resident within the loop) and reads the panel from shared
+// memory as a broadcast.  Panels use the caller's layout (row-major
+// (N*M) x K); blocks are row-major M x M.
+//
+// Kernels, one per step, launched back to back on one stream:
+//   k_sweep      eq. sub3 per segment and column tile (step 2.1):
+//                y_i = Dinv_i F_i + E_i y_{i-1}, then W_i = y_i + G_i W_{i+1};
+//                W is written into the work panel's interior rows.
+//   k_iface      eq. red1 right-hand side F~_s = F_K + A_K W_{K-1} + B_K W_{K+1}
+//                and the series terms c[l][s] = R[l][s] F~_s for every tree
+//                level l at which interface s lies inside a node (step 2.2; the
+//                dichotomy evaluation is a sum of a series over distributed
+//                data, Section 1).
+//   k_dichotomy  one launch per tree level (Algorithm 1, step 2.2):
+//                X~_m = sum_{j in [l,r]} c[level][j] + HL_m X~_{l-1} + HR_m X~_{r+1},
+//                written into the work panel's interface row k_m.
+//   k_correct    eq. superposition (step 2.3): X_i = W_i + U_i X~_s + V_i X~_{s+1}.
+// Every kernel returns at once when the refinement flag `done` is set.
+
+#include <algorithm>
+
+#include "bt_internal.cuh"
+
+namespace bt {
+
+namespace {
+
+template <typename T>
+struct SimtArgs {
+  int64_t N, S, L, K;
+  int M;
+  const T *Dinv, *E, *G, *U, *V, *AK, *BK, *R, *HL, *HR;
+  const int* nodes;
+  const int* mid_level;
+  T* c;  // [depth][S][M][K]
+  const int* done;
+};
+
+template <typename T>
+__device__ __forceinline__ bool finished(const SimtArgs<T>& p) {
+  return p.done != nullptr && *(volatile const int*)p.done != 0;
+}
+
+template <typename T, int CW>
+__device__ __forceinline__ void acc_blk(T (&acc)[CW], const T* __restrict__ blk, int M, int m, const T* pan,
+                                        int kt, int c0) {
+  const T* row = blk + (size_t)m * M;
+#pragma unroll 4
+  for (int k = 0; k < M; ++k) {
+    const T a = __ldg(row + k);
+    const T* q = pan + k * kt + c0;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = fma(a, q[c], acc[c]);
+  }
+}
+
+// Stage an M x kt tile of a panel (row block at `src`, leading dimension K)
+// into shared memory; columns at or beyond K read as zero.
+template <typename T>
+__device__ __forceinline__ void load_tile(T* dst, const T* __restrict__ src, int M, int64_t K, int64_t col0,
+                                          int kt) {
+  for (int e = threadIdx.x; e < M * kt; e += blockDim.x) {
+    const int r = e / kt, c = e % kt;
+    const int64_t col = col0 + c;
+    dst[e] = col < K ? src[(size_t)r * K + col] : T(0);
+  }
+}
+
+template <typename T, typename U, int CW>
+__device__ __forceinline__ void load_own(T (&acc)[CW], const U* __restrict__ src, int m, int64_t K, int64_t col) {
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = (col + c < K) ? T(src[(size_t)m * K + col + c]) : T(0);
+}
+
+template <typename T, typename U, int CW>
+__device__ __forceinline__ void store_own(const T (&acc)[CW], U* __restrict__ dst, int m, int64_t K, int64_t col) {
+#pragma unroll
+  for (int c = 0; c < CW; ++c)
+    if (col + c < K) dst[(size_t)m * K + col + c] = U(acc[c]);
+}
+
+template <typename T, int CW>
+__global__ void k_sweep(SimtArgs<T> p, const T* __restrict__ Fin, T* __restrict__ Wk) {
+  if (finished(p)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int M = p.M, CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const bool active = m < M;
+  T* pf = sm;
+  T* py = sm + M * kt;
+  const int64_t s = blockIdx.x, col0 = (int64_t)blockIdx.y * kt, col = col0 + c0;
+  const int64_t a = s * p.L + 1, b = s * p.L + p.L;
+  const size_t MM = (size_t)M * M, MK = (size_t)M * p.K;
+  // forward elimination: y_i = Dinv_i F_i + E_i y_{i-1}, y_{a-1} = W_{k_s} = 0
+  for (int64_t i = a; i < b; ++i) {
+    load_tile(pf, Fin + i * MK, M, p.K, col0, kt);
+    __syncthreads();
+    T acc[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = T(0);
+    if (active) {
+      acc_blk<T, CW>(acc, p.Dinv + i * MM, M, m, pf, kt, c0);
+      if (i > a) acc_blk<T, CW>(acc, p.E + i * MM, M, m, py, kt, c0);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) py[m * kt + c0 + c] = acc[c];
+      store_own<T, T, CW>(acc, Wk + i * MK, m, p.K, col);
+    }
+  }
+  __syncthreads();
+  // back substitution: W_{b-1} = y_{b-1}, W_i = y_i + G_i W_{i+1}, W_{k_s+L} = 0
+  for (int64_t i = b - 2; i >= a; --i) {
+    T acc[CW];
+    if (active) {
+      load_own<T, T, CW>(acc, Wk + i * MK, m, p.K, col);
+      acc_blk<T, CW>(acc, p.G + i * MM, M, m, py, kt, c0);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) py[m * kt + c0 + c] = acc[c];
+      store_own<T, T, CW>(acc, Wk + i * MK, m, p.K, col);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int CW>
+__global__ void k_iface(SimtArgs<T> p, const T* __restrict__ Fin, const T* __restrict__ Wk) {
+  if (finished(p)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int M = p.M, CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const bool active = m < M;
+  T* pa = sm;
+  T* pb = sm + M * kt;
+  T* pt = sm + 2 * M * kt;
+  const int64_t s = blockIdx.x, col0 = (int64_t)blockIdx.y * kt, col = col0 + c0;
+  const int64_t Kr = s * p.L;
+  const size_t MM = (size_t)M * M, MK = (size_t)M * p.K;
+  const bool hasL = s > 0 && p.L > 1;         // W_{K-1}: last interior row of segment s-1
+  const bool hasR = Kr + 1 < p.N && p.L > 1;  // W_{K+1}: first interior row of segment s
+  if (hasL) load_tile(pa, Wk + (Kr - 1) * MK, M, p.K, col0, kt);
+  if (hasR) load_tile(pb, Wk + (Kr + 1) * MK, M, p.K, col0, kt);
+  __syncthreads();
+  T acc[CW];
+  if (active) {
+    load_own<T, T, CW>(acc, Fin + Kr * MK, m, p.K, col);
+    if (hasL) acc_blk<T, CW>(acc, p.AK + s * MM, M, m, pa, kt, c0);
+    if (hasR) acc_blk<T, CW>(acc, p.BK + s * MM, M, m, pb, kt, c0);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) pt[m * kt + c0 + c] = acc[c];
+  }
+  __syncthreads();
+  if (!active) return;
+  const int top = p.mid_level[s];
+  for (int lev = 0; lev <= top; ++lev) {
+    T cacc[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) cacc[c] = T(0);
+    acc_blk<T, CW>(cacc, p.R + ((size_t)lev * p.S + s) * MM, M, m, pt, kt, c0);
+    store_own<T, T, CW>(cacc, p.c + ((size_t)lev * p.S + s) * MK, m, p.K, col);
+  }
+}
+
+template <typename T, int CW>
+__global__ void k_dichotomy(SimtArgs<T> p, int lev, int node_off, T* __restrict__ Wk) {
+  if (finished(p)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int M = p.M, CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const bool active = m < M;
+  T* pl = sm;
+  T* pr = sm + M * kt;
+  const int q = node_off + blockIdx.x;
+  const int l = p.nodes[3 * q], r = p.nodes[3 * q + 1], mid = p.nodes[3 * q + 2];
+  const int64_t col0 = (int64_t)blockIdx.y * kt, col = col0 + c0;
+  const size_t MM = (size_t)M * M, MK = (size_t)M * p.K;
+  const bool hl = l > 0, hr = r < p.S - 1;
+  if (hl) load_tile(pl, Wk + (int64_t)(l - 1) * p.L * MK, M, p.K, col0, kt);
+  if (hr) load_tile(pr, Wk + (int64_t)(r + 1) * p.L * MK, M, p.K, col0, kt);
+  __syncthreads();
+  if (!active) return;
+  T acc[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = T(0);
+  for (int j = l; j <= r; ++j) {
+    const T* cj = p.c + ((size_t)lev * p.S + j) * MK + (size_t)m * p.K + col;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (col + c < p.K) acc[c] += cj[c];
+  }
+  if (hl) acc_blk<T, CW>(acc, p.HL + (size_t)mid * MM, M, m, pl, kt, c0);
+  if (hr) acc_blk<T, CW>(acc, p.HR + (size_t)mid * MM, M, m, pr, kt, c0);
+  store_own<T, T, CW>(acc, Wk + (int64_t)mid * p.L * MK, m, p.K, col);
+}
+
+// X_i = W_i + U_i X~_s + V_i X~_{s+1} on interior rows.  In place (Xout aliases
+// the work panel, FP64 path) or into a separate FP64 panel, optionally added
+// to its previous contents (refinement); in the separate case the interface
+// rows receive X~_s as well.
+template <typename T, int CW>
+__global__ void k_correct(SimtArgs<T> p, const T* __restrict__ Wk, double* __restrict__ Xout, int rows_per_cta,
+                          int separate, int accumulate) {
+  if (finished(p)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int M = p.M, CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const bool active = m < M;
+  T* p0 = sm;
+  T* p1 = sm + M * kt;
+  const int64_t s = blockIdx.x, col0 = (int64_t)blockIdx.y * kt, col = col0 + c0;
+  const size_t MM = (size_t)M * M, MK = (size_t)M * p.K;
+  const bool has_next = s + 1 < p.S;  // X~_S is the fictitious X_{N+1} = 0
+  load_tile(p0, Wk + s * p.L * MK, M, p.K, col0, kt);
+  if (has_next) load_tile(p1, Wk + (s + 1) * p.L * MK, M, p.K, col0, kt);
+  __syncthreads();
+  if (!active) return;
+  if (separate && blockIdx.z == 0) {
+    T v[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) v[c] = p0[m * kt + c0 + c];
+    double* xr = Xout + s * p.L * MK;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (col + c < p.K) {
+        double* o = xr + (size_t)m * p.K + col + c;
+        *o = (accumulate ? *o : 0.0) + (double)v[c];
+      }
+  }
+  const int64_t a = s * p.L + 1 + (int64_t)blockIdx.z * rows_per_cta;
+  const int64_t b = std::min<int64_t>(a + rows_per_cta, s * p.L + p.L);
+  for (int64_t i = a; i < b; ++i) {
+    T acc[CW];
+    load_own<T, T, CW>(acc, Wk + i * MK, m, p.K, col);
+    acc_blk<T, CW>(acc, p.U + i * MM, M, m, p0, kt, c0);
+    if (has_next) acc_blk<T, CW>(acc, p.V + i * MM, M, m, p1, kt, c0);
+    double* xr = Xout + i * MK;
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (col + c < p.K) {
+        double* o = xr + (size_t)m * p.K + col + c;
+        *o = ((separate && accumulate) ? *o : 0.0) + (double)acc[c];
+      }
+  }
+}
+
+struct Plan {
+  int CW, CG;
+};
+
+template <typename T>
+Plan pick_plan(int M, int64_t K) {
+  Plan pl;
+  pl.CW = K >= 4 ? 4 : (K >= 2 ? 2 : 1);
+  int CG = (int)std::min<int64_t>((K + pl.CW - 1) / pl.CW, std::max(1, 128 / M));
+  pl.CG = std::max(1, std::min(CG, 1024 / M));
+  return pl;
+}
+
+template <typename T, int CW>
+bt_status launch_all(bt_handle_s* h, const SimtArgs<T>& a, const T* Fin, T* Wk, double* Xout, int CG, int stages,
+                     int separate, int accumulate, cudaStream_t st, const char* tag) {
+  const int M = a.M, kt = CW * CG, threads = M * CG;
+  const int64_t ntiles = (a.K + kt - 1) / kt;
+  if (ntiles > 65535) {
+    set_error("bt_solve: too many right-hand-side tiles for one launch");
+    return BT_ERR_UNSUPPORTED;
+  }
+  const size_t sm2 = 2 * (size_t)M * kt * sizeof(T), sm3 = 3 * (size_t)M * kt * sizeof(T);
+  if (sm3 > 48 * 1024) {
+    for (const void* f : {(const void*)k_sweep<T, CW>, (const void*)k_iface<T, CW>, (const void*)k_dichotomy<T, CW>,
+                          (const void*)k_correct<T, CW>})
+      BT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+  }
+  const bool f64 = sizeof(T) == 8;
+  if (a.L > 1) {
+    ProfScope ps(h, st, f64 ? "f64_sweep" : "f32_sweep");
+    k_sweep<T, CW><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm2, st>>>(a, Fin, Wk);
+  }
+  BT_CUDA(cudaGetLastError());
+  if (stages < 2) return BT_OK;
+  {
+    ProfScope ps(h, st, f64 ? "f64_iface" : "f32_iface");
+    k_iface<T, CW><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm3, st>>>(a, Fin, Wk);
+  }
+  BT_CUDA(cudaGetLastError());
+  for (int lev = 0; lev < h->depth; ++lev) {
+    const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
+    ProfScope ps(h, st, f64 ? "f64_dichotomy" : "f32_dichotomy");
+    k_dichotomy<T, CW><<<dim3(nn, (unsigned)ntiles), threads, sm2, st>>>(a, lev, n0, Wk);
+  }
+  BT_CUDA(cudaGetLastError());
+  if (stages < 3 || (a.L < 2 && !separate)) return BT_OK;
+  // enough CTAs to cover the GPU several times over
+  const int64_t rows = std::max<int64_t>(1, a.L - 1);
+  int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(rows, (4 * 152 + a.S * ntiles - 1) / (a.S * ntiles)));
+  const int rows_per_cta = (int)((rows + chunks - 1) / chunks);
+  chunks = (rows + rows_per_cta - 1) / rows_per_cta;
+  {
+    ProfScope ps(h, st, f64 ? "f64_correct" : "f32_correct");
+    k_correct<T, CW><<<dim3((unsigned)a.S, (unsigned)ntiles, (unsigned)chunks), threads, sm2, st>>>(
+        a, Wk, Xout, rows_per_cta, separate, accumulate);
+  }
+  BT_CUDA(cudaGetLastError());
+  (void)tag;
+  return BT_OK;
+}
+
+template <typename T>
+bt_status run(bt_handle_s* h, const SimtArgs<T>& a, const T* Fin, T* Wk, double* Xout, int stages, int separate,
+              int accumulate, cudaStream_t st) {
+  const Plan pl = pick_plan<T>(a.M, a.K);
+  switch (pl.CW) {
+    case 4: return launch_all<T, 4>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
+    case 2: return launch_all<T, 2>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
+    default: return launch_all<T, 1>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
+  }
+}
+
+}  // namespace
+
+bt_status ensure_scratch(bt_handle_s* h, size_t bytes, cudaStream_t st) {
+  if (bytes <= h->scratch_bytes) return BT_OK;
+  if (h->scratch) {
+    BT_CUDA(cudaStreamSynchronize(st));
+    BT_CUDA(cudaFree(h->scratch));
+    h->scratch = nullptr;
+    h->scratch_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc((void**)&h->scratch, bytes);
+  if (e != cudaSuccess) {
+    h->scratch = nullptr;
+    set_error(std::string("bt_solve: scratch allocation failed: ") + cudaGetErrorString(e));
+    return BT_ERR_OOM;
+  }
+  h->scratch_bytes = bytes;
+  return BT_OK;
+}
+
+bt_status solve_f64(bt_handle_s* h, const double* F, int64_t K, double* X, int stages, cudaStream_t st) {
+  const int M = (int)h->M;
+  BT_TRY(ensure_scratch(h, (size_t)h->depth * h->S * M * K * sizeof(double), st));
+  SimtArgs<double> a;
+  a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = M;
+  a.Dinv = h->Dinv; a.E = h->E; a.G = h->G; a.U = h->U; a.V = h->V;
+  a.AK = h->AK; a.BK = h->BK; a.R = h->R; a.HL = h->HL; a.HR = h->HR;
+  a.nodes = h->d_nodes; a.mid_level = h->d_mid_level;
+  a.c = reinterpret_cast<double*>(h->scratch);
+  a.done = nullptr;
+  return run<double>(h, a, F, X, X, stages, 0, 0, st);
+}
+
+bt_status solve_simt_f32(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, double* X, int accumulate,
+                         const int* done, cudaStream_t st) {
+  const LowFactors& f = h->f32;
+  SimtArgs<float> a;
+  a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = (int)h->M;
+  a.Dinv = f.Dinv; a.E = f.E; a.G = f.G; a.U = f.U; a.V = f.V;
+  a.AK = f.AK; a.BK = f.BK; a.R = f.R; a.HL = f.HL; a.HR = f.HR;
+  a.nodes = h->d_nodes; a.mid_level = h->d_mid_level;
+  a.c = c;
+  a.done = done;
+  return run<float>(h, a, r, d, X, 3, 1, accumulate, st);
+}
+
+bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, const int* done,
+                                   cudaStream_t st) {
+  // steps 2.2 only (the interface right-hand side and the dichotomy); the
+  // tensor-core kernels do the sweeps and the correction.
+  const LowFactors& f = h->f32;
+  SimtArgs<float> a;
+  a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = (int)h->M;
+  a.Dinv = f.Dinv; a.E = f.E; a.G = f.G; a.U = f.U; a.V = f.V;
+  a.AK = f.AK; a.BK = f.BK; a.R = f.R; a.HL = f.HL; a.HR = f.HR;
+  a.nodes = h->d_nodes; a.mid_level = h->d_mid_level;
+  a.c = c;
+  a.done = done;
+  const Plan pl = pick_plan<float>(a.M, K);
+  const int CW = pl.CW, CG = pl.CG, M = a.M, kt = CW * CG, threads = M * CG;
+  const int64_t ntiles = (K + kt - 1) / kt;
+  const size_t sm2 = 2 * (size_t)M * kt * sizeof(float), sm3 = 3 * (size_t)M * kt * sizeof(float);
+  auto go = [&](auto cw) -> bt_status {
+    constexpr int W = decltype(cw)::value;
+    if (sm3 > 48 * 1024) {
+      BT_CUDA(cudaFuncSetAttribute(k_iface<float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+      BT_CUDA(cudaFuncSetAttribute(k_dichotomy<float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    }
+    {
+      ProfScope ps(h, st, "f32_iface");
+      k_iface<float, W><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm3, st>>>(a, r, d);
+    }
+    BT_CUDA(cudaGetLastError());
+    for (int lev = 0; lev < h->depth; ++lev) {
+      const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
+      ProfScope ps(h, st, "f32_dichotomy");
+      k_dichotomy<float, W><<<dim3(nn, (unsigned)ntiles), threads, sm2, st>>>(a, lev, n0, d);
+    }
+    BT_CUDA(cudaGetLastError());
+    return BT_OK;
+  };
+  switch (CW) {
+    case 4: return go(std::integral_constant<int, 4>());
+    case 2: return go(std::integral_constant<int, 2>());
+    default: return go(std::integral_constant<int, 1>());
+  }
+}
+
+}  // namespace bt

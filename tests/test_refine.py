@@ -1,0 +1,88 @@
+"""Mixed-precision solve with FP64-residual iterative refinement vs the CPU oracle (GPU only).
+
+Bars: the refined solution reaches the requested relative residual
+||F - P X||_F / ||F||_F (measured by the oracle in FP64, independently of the
+device's own report) and its error against the FP64 oracle is <= 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+PRECISIONS = ["f32"]
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1108_4181_gb300 as bt
+
+    return bt
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("N,M,K,S", [(64, 4, 1, 8), (64, 8, 5, 8), (96, 33, 7, 12), (128, 64, 20, 16)])
+def test_refined_dense_random(bt, prec, N, M, K, S):
+    A, B, C = gen.dominant_blocks(N, M, seed=N + M)
+    F = gen.uniform_rhs(N, M, K, seed=K)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        assert fac.stencil == 0
+        X, info = fac.solve(_t(F), precision=prec, tol=1e-12, return_info=True)
+    X = X.cpu().numpy()
+    assert info["converged"] and info["rel_res"] <= 1e-12
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_refined_poisson_stencil(bt, prec):
+    N, M, K, S = 64, 32, 6, 8
+    A, B, C = gen.poisson_system(N, M)
+    X_exact, F = gen.poisson_manufactured(N, M, K, seed=11)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        assert fac.stencil == 1
+        X, info = fac.solve(_t(F), precision=prec, tol=1e-12, return_info=True)
+    X = X.cpu().numpy()
+    assert info["converged"]
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_refined_acoustic_full_size(bt, prec):
+    w = gen.config2()
+    cols = [0, 100, 511]
+    with bt.factor(_t(w.A), _t(w.B), _t(w.C), w.S) as fac:
+        X, info = fac.solve(_t(w.F), precision=prec, tol=1e-12, return_info=True)
+        X = X.cpu().numpy()
+    assert info["converged"] and info["rel_res"] <= 1e-12
+    Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
+    assert oracle.rel_err(X[:, :, cols], Xr) <= 1e-10
+    assert oracle.rel_res(w.A, w.B, w.C, X[:, :, cols], w.F[:, :, cols]) <= 1e-11
+
+
+def test_nonconvergence_is_reported(bt):
+    A, B, C = gen.dominant_blocks(32, 4, seed=2)
+    F = gen.uniform_rhs(32, 4, 3, seed=3)
+    with bt.factor(_t(A), _t(B), _t(C), 4) as fac:
+        with pytest.raises(bt.BtError) as ei:
+            fac.solve(_t(F), precision="f32", tol=1e-300, max_it=1, return_info=True)
+        assert ei.value.name == "BT_ERR_NOCONV"
+
+
+def test_refined_zero_rhs(bt):
+    A, B, C = gen.dominant_blocks(16, 3, seed=2)
+    with bt.factor(_t(A), _t(B), _t(C), 4) as fac:
+        X = fac.solve(torch.zeros((16, 3, 2), dtype=torch.float64, device=DEV), precision="f32")
+    assert float(X.abs().max()) == 0.0
