@@ -129,6 +129,9 @@ struct bt_handle_s {
   bt_handle_s* adj = nullptr;
 
   LowFactors f32;
+  // Tensor-core factor copies [5][N][M][M] (Dinv, E, G, U, V) in BF16 / FP32.
+  void* tc_fac_bf16 = nullptr;
+  void* tc_fac_tf32 = nullptr;
 
   // Refinement buffers (grown on demand): residual panel, work panel,
   // series terms and the device-side refinement state.
@@ -179,6 +182,25 @@ bt_status solve_simt_f32(bt_handle_s* h, const float* r, int64_t K, float* d, fl
 // Only the interface steps (F~, series terms, dichotomy) of the FP32 pipeline.
 bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, const int* done,
                                    cudaStream_t st);
+
+// Buffers of one tensor-core solve: factor copies, block-transposed residual
+// and work panels (leading dimension Kp, a multiple of the column tile), and
+// the FP32 series terms [depth][S][M][Kp].
+struct TcBuffers {
+  const void* fac;
+  void* r;
+  void* w;
+  float* c;
+  int64_t Kp;
+};
+
+// Column tile of the tensor-core kernels for a precision and block size (0: unsupported).
+int tc_col_tile(int precision, int M);
+// Builds the tensor-core factor copies for `precision` (once per handle).
+bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st);
+// One tensor-core stage-2 solve: r -> w (y, W, X~), then X (+)= solution.
+bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,
+                   const int* done, int* status, cudaStream_t st);
 
 // Builds h->f32 from the FP64 factors (once per handle).
 bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st);

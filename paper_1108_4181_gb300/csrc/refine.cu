@@ -28,8 +28,8 @@ struct IrState {
   double rn2[kMaxPasses];   // ||F - P X_k||_F^2
   int done;                 // 1 converged, 2 stalled
   int last;                 // index of the last residual computed
-  int solves;               // stage-2 solves performed
-  int pad;
+  int solves;               // refinement solves performed after the first
+  int kstatus;              // non-zero: a tensor-core kernel gave up a bounded wait
 };
 
 template <typename T>
@@ -53,9 +53,27 @@ __device__ __forceinline__ void block_add(double v, double* target) {
   }
 }
 
-// r = F - P X for A_j = B_j = I and tridiagonal C_j (FP64 arithmetic, rounded
-// to the solve precision on store).  first != 0: X = 0, r = F, and ||F||^2 is
-// accumulated as well.
+// One residual entry of the stencil operator (A_j = B_j = I, tridiagonal C_j):
+// r = F_j + X_{j-1} + X_{j+1} - C_j X_j at (j, m, n), FP64.
+__device__ __forceinline__ double stencil_res(const double* __restrict__ F, const double* __restrict__ X,
+                                              const double* __restrict__ Cd, int64_t N, int M, int64_t K, int64_t j,
+                                              int m, int64_t n, int first) {
+  const size_t MK = (size_t)M * K;
+  const size_t e = j * MK + (size_t)m * K + n;
+  double v = F[e];
+  if (!first) {
+    const double* cd = Cd + 3 * (j * M + m);
+    double cx = cd[1] * X[e];
+    if (m > 0) cx += cd[0] * X[e - K];
+    if (m + 1 < M) cx += cd[2] * X[e + K];
+    v -= cx;
+    if (j > 0) v += X[e - MK];
+    if (j + 1 < N) v += X[e + MK];
+  }
+  return v;
+}
+
+// Row-major residual panel (leading dimension K): grid-stride over entries.
 template <typename TR>
 __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict__ F, const double* __restrict__ X,
                                                       const double* __restrict__ Cd, TR* __restrict__ r,
@@ -65,19 +83,9 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
   const size_t MK = (size_t)M * K, n = (size_t)N * MK;
   double acc = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double v = F[e];
-    if (!first) {
-      const size_t j = e / MK;
-      const size_t rem = e % MK;
-      const int m = (int)(rem / K);
-      const double* cd = Cd + 3 * (j * M + m);
-      double cx = cd[1] * X[e];
-      if (m > 0) cx += cd[0] * X[e - K];
-      if (m + 1 < M) cx += cd[2] * X[e + K];
-      v -= cx;
-      if (j > 0) v += X[e - MK];
-      if (j + 1 < (size_t)N) v += X[e + MK];
-    }
+    const int64_t j = e / MK;
+    const size_t rem = e % MK;
+    const double v = stencil_res(F, X, Cd, N, M, K, j, (int)(rem / K), rem % K, first);
     r[e] = to_lp<TR>(v);
     acc += v * v;
   }
@@ -85,13 +93,51 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
   if (first) block_add(acc, &st->rn2[0]);
 }
 
+// Block-transposed residual panel (element (m, n) of block j at (j*Kp + n)*M + m),
+// through a 32 x 32 shared-memory tile so that both the FP64 reads (along n)
+// and the stores (along m) are coalesced.  Columns K..Kp-1 are written as zero.
+template <typename TR>
+__global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restrict__ F, const double* __restrict__ X,
+                                                        const double* __restrict__ Cd, TR* __restrict__ r,
+                                                        int64_t N, int M, int64_t K, int64_t Kp, int first,
+                                                        int pass, IrState* st) {
+  if (st->done) return;
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int64_t n0 = (int64_t)blockIdx.x * 32, j = blockIdx.z;
+  const int m0 = blockIdx.y * 32;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int m = m0 + ty + 8 * q;
+    const int64_t n = n0 + tx;
+    double v = 0.0;
+    if (m < M && n < K) {
+      v = stencil_res(F, X, Cd, N, M, K, j, m, n, first);
+      acc += v * v;
+    }
+    tile[ty + 8 * q][tx] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t n = n0 + ty + 8 * q;
+    const int m = m0 + tx;
+    if (m < M && n < Kp) r[((size_t)j * Kp + n) * M + m] = to_lp<TR>(tile[tx][ty + 8 * q]);
+  }
+  block_add(acc, first ? &st->fn2 : &st->rn2[pass]);
+  if (first) block_add(acc, &st->rn2[0]);
+}
+
 // r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
 // One CTA per (block row, column tile); a thread owns row m and CW columns.
-template <typename TR, int CW>
+// Output row-major (TRANS = false, leading dimension ldr) or block-transposed
+// (TRANS = true, leading dimension ldr = Kp; columns K..Kp-1 written as zero).
+template <typename TR, int CW, bool TRANS>
 __global__ void k_resid_dense(const double* __restrict__ F, const double* __restrict__ X,
                               const double* __restrict__ A, const double* __restrict__ B,
                               const double* __restrict__ C, TR* __restrict__ r, int64_t N, int M, int64_t K,
-                              int pass, IrState* st) {
+                              int64_t ldr, int pass, IrState* st) {
   if (st->done) return;
   extern __shared__ double sm[];
   const int CG = blockDim.x / M, kt = CW * CG;
@@ -128,11 +174,15 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
       }
     }
 #pragma unroll
-    for (int c = 0; c < CW; ++c)
-      if (col + c < K) {
-        r[j * MK + (size_t)m * K + col + c] = to_lp<TR>(acc[c]);
-        part += acc[c] * acc[c];
+    for (int c = 0; c < CW; ++c) {
+      const bool in = col + c < K;
+      if (in) part += acc[c] * acc[c];
+      if (TRANS) {
+        if (col + c < ldr) r[((size_t)j * ldr + col + c) * M + m] = to_lp<TR>(in ? acc[c] : 0.0);
+      } else if (in) {
+        r[j * (size_t)M * ldr + (size_t)m * ldr + col + c] = to_lp<TR>(acc[c]);
       }
+    }
   }
   block_add(part, &st->rn2[pass]);
 }
@@ -142,7 +192,9 @@ __global__ void k_ir_check(IrState* st, int pass, double tol2) {
   st->last = pass;
   if (pass == 0) return;
   const double r2 = st->rn2[pass];
-  if (r2 <= tol2 * st->fn2) {
+  if (st->kstatus != 0) {
+    st->done = 3;  // a tensor-core kernel gave up: stop, report
+  } else if (r2 <= tol2 * st->fn2) {
     st->done = 1;
   } else if (pass >= 3 && r2 >= 0.9 * st->rn2[pass - 1] && st->rn2[pass - 1] >= 0.9 * st->rn2[pass - 2]) {
     st->done = 2;  // two passes without a 10 % reduction: stalled
@@ -177,25 +229,44 @@ bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
   return BT_OK;
 }
 
+// Residual into the solve's panel: row-major (ld = K) for the SIMT solve,
+// block-transposed (ld = Kp) for the tensor-core solve.
 template <typename TR>
-bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int first, int pass,
-                          IrState* st, cudaStream_t s) {
+bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
+                          int first, int pass, IrState* st, cudaStream_t s) {
   const int M = (int)h->M;
   ProfScope ps(h, s, "residual");
   if (first || h->stencil) {
-    const size_t n = (size_t)h->N * M * K;
-    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
-    k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st);
+    if (trans) {
+      if (h->N > 65535) {
+        set_error("residual: N > 65535 is not supported by the transposed residual kernel");
+        return BT_ERR_UNSUPPORTED;
+      }
+      dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)h->N);
+      k_resid_stencil_t<TR><<<grid, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, st);
+    } else {
+      const size_t n = (size_t)h->N * M * K;
+      const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+      k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st);
+    }
   } else {
     constexpr int CW = 4;
     const int CG = std::max(1, std::min(1024 / M, std::max(1, 128 / M)));
     const int kt = CW * CG;
-    const int64_t ntiles = (K + kt - 1) / kt;
+    const int64_t ncols = trans ? Kp : K;
+    const int64_t ntiles = (ncols + kt - 1) / kt;
     const size_t smem = 3 * (size_t)M * kt * sizeof(double);
-    if (smem > 48 * 1024)
-      BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_resid_dense<TR, CW><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(F, X, h->A, h->B, h->C, r,
-                                                                                       h->N, M, K, pass, st);
+    if (trans) {
+      if (smem > 48 * 1024)
+        BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_resid_dense<TR, CW, true><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
+          F, X, h->A, h->B, h->C, r, h->N, M, K, Kp, pass, st);
+    } else {
+      if (smem > 48 * 1024)
+        BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_resid_dense<TR, CW, false><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
+          F, X, h->A, h->B, h->C, r, h->N, M, K, K, pass, st);
+    }
   }
   BT_CUDA(cudaGetLastError());
   return BT_OK;
@@ -228,33 +299,58 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   cudaStream_t s = (cudaStream_t)o.stream;
   const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : 12;
   const double tol = o.tol > 0 ? o.tol : 1e-10;
-  if (o.precision != 3) {
-    set_error("bt_solve_ex: this precision is not available in this build");
-    return BT_ERR_UNSUPPORTED;
+  const int prec = o.precision;
+  const bool tcore = prec == BT_PREC_BF16 || prec == BT_PREC_TF32;
+  const int M = (int)h->M;
+  int64_t Kp = K;
+  size_t eb = sizeof(float);
+  if (tcore) {
+    const int nt = tc_col_tile(prec, M);
+    if (nt == 0) {
+      set_error("bt_solve_ex: the tensor-core precisions support block sizes M = 64 and M = 128");
+      return BT_ERR_UNSUPPORTED;
+    }
+    Kp = (K + nt - 1) / nt * nt;
+    eb = prec == BT_PREC_BF16 ? 2 : 4;
   }
-  const size_t panel = (size_t)h->N * h->M * K * sizeof(float);
-  const size_t cbytes = (size_t)h->depth * h->S * h->M * K * sizeof(float);
+  const size_t panel = (size_t)h->N * M * Kp * eb;
+  const size_t cbytes = (size_t)h->depth * h->S * M * Kp * sizeof(float);
   BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
   BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));
   if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
   BT_TRY(make_f32_factors(h, s));
+  if (tcore) BT_TRY(make_tc_factors(h, prec, s));
   IrState* st = reinterpret_cast<IrState*>(h->ir_state);
-  float* r = reinterpret_cast<float*>(h->lp_r);
-  float* d = reinterpret_cast<float*>(h->lp_d);
-  float* c = reinterpret_cast<float*>(h->lp_c);
   const int* done = &st->done;
   BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), s));
   const double tol2 = tol * tol;
-  BT_TRY(launch_residual<float>(h, F, X, r, K, 1, 0, st, s));
+
+  auto residual = [&](int first, int pass) -> bt_status {
+    if (prec == BT_PREC_BF16)
+      return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, first,
+                                            pass, st, s);
+    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, first, pass, st, s);
+  };
+  auto inner = [&](int accumulate) -> bt_status {
+    if (tcore) {
+      TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : h->tc_fac_tf32, h->lp_r, h->lp_d,
+                   reinterpret_cast<float*>(h->lp_c), Kp};
+      return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, s);
+    }
+    return solve_simt_f32(h, reinterpret_cast<float*>(h->lp_r), K, reinterpret_cast<float*>(h->lp_d),
+                          reinterpret_cast<float*>(h->lp_c), X, accumulate, done, s);
+  };
+
+  BT_TRY(residual(1, 0));
   k_ir_check<<<1, 1, 0, s>>>(st, 0, tol2);
-  BT_TRY(solve_simt_f32(h, r, K, d, c, X, 0, done, s));
+  BT_TRY(inner(0));
   for (int pass = 1; pass <= max_it + 1; ++pass) {
-    BT_TRY(launch_residual<float>(h, F, X, r, K, 0, pass, st, s));
+    BT_TRY(residual(0, pass));
     k_ir_check<<<1, 1, 0, s>>>(st, pass, tol2);
     if (pass <= max_it) {
       k_count_solve<<<1, 1, 0, s>>>(st);
-      BT_TRY(solve_simt_f32(h, r, K, d, c, X, 1, done, s));
+      BT_TRY(inner(1));
     }
   }
   BT_CUDA(cudaGetLastError());
@@ -266,6 +362,10 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     info->converged = hs.done == 1 ? 1 : 0;
     info->rel_res = hs.fn2 > 0 ? std::sqrt(hs.rn2[hs.last] / hs.fn2) : 0.0;
     info->rel_res0 = hs.fn2 > 0 ? std::sqrt(hs.rn2[1] / hs.fn2) : 0.0;
+    if (hs.kstatus != 0) {
+      set_error("bt_solve_ex: a tensor-core kernel gave up a bounded wait (code " + std::to_string(hs.kstatus) + ")");
+      return BT_ERR_TIMEOUT;
+    }
     if (!info->converged) {
       set_error("bt_solve_ex: refinement stopped at relative residual " + std::to_string(info->rel_res));
       return BT_ERR_NOCONV;

@@ -1,0 +1,815 @@
+// Algorithm 2, stage 2 on the tcgen05 tensor cores (BF16 or TF32 operands,
+// FP32 accumulation in TMEM), used as the inner solve of iterative refinement.
+//
+// Internal panels (residual r, work panel holding y, W and X~) are stored
+// block-transposed: block row j of a panel is a K x M matrix, element (m, n)
+// at (j * Kp + n) * M + m, Kp = K rounded up to the column tile.  A column
+// tile of a block row is then an NT x M matrix with M contiguous: the K-major
+// B operand of the MMA for both BF16 and TF32.  Factor blocks are row-major
+// M x M: the K-major A operand.  Both are moved by TMA with 128-byte swizzle.
+//
+//   k_tc_sweep    eq. sub3 per (segment, column tile), step 2.1:
+//                 forward  y_i = Dinv_i r_i + E_i y_{i-1},
+//                 backward W_i = y_i + G_i W_{i+1}.
+//                 Warp 0 streams factor slices and panel tiles with TMA into
+//                 rings, warp 1 issues the MMAs (one thread), warps 2-5 drain
+//                 the TMEM accumulator, write the next B operand into shared
+//                 memory and store the row with TMA.  Two accumulators let the
+//                 next row's MMA start while the previous one is drained.
+//   k_tc_iface / k_tc_dichotomy   step 2.2 on the CUDA cores in FP32 (a few
+//                 per cent of the flops: S (2 + depth) block products).
+//   k_tc_correct  eq. superposition, step 2.3: X_i (+)= W_i + U_i X~_s +
+//                 V_i X~_{s+1} with the FP64 solution updated in place.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "bt_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace bt {
+
+namespace {
+
+using namespace tc;
+
+// ------------------------------------------------------------------ traits
+template <typename E>
+struct ET;
+template <>
+struct ET<__nv_bfloat16> {
+  static constexpr uint32_t fmt = 1;
+  static constexpr CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  static __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct ET<float> {
+  static constexpr uint32_t fmt = 2;
+  static constexpr CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  static __device__ __forceinline__ float tof(float v) { return v; }
+  static __device__ __forceinline__ float from(float v) { return v; }
+};
+
+__host__ __device__ constexpr int pow2ceil(int v) {
+  int p = 32;
+  while (p < v) p *= 2;
+  return p;
+}
+
+template <typename E, int M_, int NT_, int NA_>
+struct Cfg {
+  static constexpr int M = M_, NT = NT_, NA = NA_;
+  static constexpr int eb = (int)sizeof(E);
+  static constexpr int CE = 128 / eb;      // elements in one 128-byte swizzle row
+  static constexpr int KS = 32 / eb;       // K of one MMA instruction
+  static constexpr int NCH = M / CE;       // 128-byte chunks per block row / per tile row
+  static constexpr int SLICE = M * 128;    // one A slice: M rows x 128 bytes
+  static constexpr int TCH = NT * 128;     // one tile chunk: NT rows x 128 bytes
+  static constexpr int TILE = NCH * TCH;   // one NT x M panel tile
+  static constexpr int TMEM_COLS = pow2ceil(2 * NT);
+  static constexpr uint32_t IDESC = instr_desc(ET<E>::fmt, 0, M, NT);
+  static_assert(M == 64 || M == 128, "tensor-core path supports M = 64 and M = 128");
+  static_assert(NT % 32 == 0 && NT <= 256, "column tile");
+  static_assert(TCH % 1024 == 0, "swizzle atoms");
+};
+
+// Byte offset of element (n, m) inside a K-major 128B-swizzled NT x M tile.
+template <class C>
+__device__ __forceinline__ uint32_t kmaj_off(int n, int m) {
+  constexpr int per16 = 16 / C::eb;
+  const int c = m / C::CE;
+  const int u = (m % C::CE) / per16;
+  return (uint32_t)(c * C::TCH + n * 128 + ((u ^ (n & 7)) << 4) + (m % per16) * C::eb);
+}
+
+// TMEM lane holding accumulator row `row` (cta_group::1): M = 128 uses all 128
+// lanes, M = 64 the first 16 lanes of each 32-lane quadrant.
+template <class C>
+__device__ __forceinline__ void epi_row(int warp, int lane, int* row, bool* has) {
+  const int q = warp & 3;
+  if (C::M == 128) {
+    *row = 32 * q + lane;
+    *has = true;
+  } else {
+    *row = 16 * q + (lane & 15);
+    *has = lane < 16;
+  }
+}
+
+__device__ __forceinline__ bool flag_set(const int* f) { return f != nullptr && *(volatile const int*)f != 0; }
+
+struct Bars {
+  uint64_t* fullA;
+  uint64_t* emptyA;
+  uint64_t* fullP;
+  uint64_t* emptyP;
+  uint64_t* mdone;
+  uint64_t* afree;
+  uint64_t* yrdy;
+  uint64_t* extra;  // [0] forward stores complete / B tiles loaded, [1] drain
+};
+
+template <class C>
+__device__ __forceinline__ Bars carve(uint64_t* b) {
+  Bars r;
+  r.fullA = b;
+  r.emptyA = b + C::NA;
+  r.fullP = b + 2 * C::NA;
+  r.emptyP = r.fullP + 2;
+  r.mdone = r.emptyP + 2;
+  r.afree = r.mdone + 2;
+  r.yrdy = r.afree + 2;
+  r.extra = r.yrdy + 2;
+  return r;
+}
+
+__host__ __device__ constexpr int kBars(int na) { return 2 * na + 12; }
+
+template <class C>
+__device__ __forceinline__ void init_bars(const Bars& b) {
+  for (int i = 0; i < C::NA; ++i) {
+    mbar_init(&b.fullA[i], 1);
+    mbar_init(&b.emptyA[i], 1);
+  }
+  for (int i = 0; i < 2; ++i) {
+    mbar_init(&b.fullP[i], 1);
+    mbar_init(&b.emptyP[i], 1);
+    mbar_init(&b.mdone[i], 1);
+    mbar_init(&b.afree[i], 4);
+    mbar_init(&b.yrdy[i], 1);
+    mbar_init(&b.extra[i], 1);
+  }
+  fence_mbar_init();
+}
+
+// Producer helper: one A slice into the ring (waits for the slot to drain).
+template <class C>
+__device__ __forceinline__ bool load_slice(uint8_t* sA, const Bars& b, uint32_t& ai, const CUtensorMap* tm, int x,
+                                           int y) {
+  const uint32_t slot = ai % C::NA, use = ai / C::NA;
+  if (use > 0 && !mbar_wait(&b.emptyA[slot], (use - 1) & 1)) return false;
+  mbar_arrive_expect_tx(&b.fullA[slot], C::SLICE);
+  tma_load_2d(sA + slot * C::SLICE, tm, x, y, &b.fullA[slot]);
+  ++ai;
+  return true;
+}
+
+// Producer helper: one panel tile (NCH boxes) into the P ring.
+template <class C>
+__device__ __forceinline__ bool load_tile(uint8_t* sP, const Bars& b, uint32_t& pi, const CUtensorMap* tm, int y) {
+  const uint32_t slot = pi % 2, use = pi / 2;
+  if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
+  mbar_arrive_expect_tx(&b.fullP[slot], C::TILE);
+  for (int c = 0; c < C::NCH; ++c) tma_load_2d(sP + slot * C::TILE + c * C::TCH, tm, c * C::CE, y, &b.fullP[slot]);
+  ++pi;
+  return true;
+}
+
+// MMA helper: D (+)= A_block * B_tile over the M-long contraction, streaming
+// the block's NCH slices from the ring; frees each slice when consumed.
+template <typename E, class C>
+__device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& ai, uint32_t dtmem, uint32_t btile,
+                                          bool& first) {
+  for (int c = 0; c < C::NCH; ++c) {
+    const uint32_t slot = ai % C::NA, use = ai / C::NA;
+    if (!mbar_wait(&b.fullA[slot], use & 1)) return false;
+    tc_fence_after();
+    const uint32_t abase = smem_u32(sA + slot * C::SLICE);
+#pragma unroll
+    for (int kq = 0; kq < C::CE / C::KS; ++kq) {
+      const uint64_t ad = smem_desc(abase + kq * 32, 16, 1024);
+      const uint64_t bd = smem_desc(btile + c * C::TCH + kq * 32, 16, 1024);
+      if (ET<E>::fmt == 1)
+        mma_f16(dtmem, ad, bd, C::IDESC, first ? 0u : 1u);
+      else
+        mma_tf32(dtmem, ad, bd, C::IDESC, first ? 0u : 1u);
+      first = false;
+    }
+    mma_commit(&b.emptyA[slot]);
+    ++ai;
+  }
+  return true;
+}
+
+// Drains NT accumulator columns of this thread's TMEM lane into v[].
+template <class C>
+__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[C::NT]) {
+#pragma unroll
+  for (int c0 = 0; c0 < C::NT; c0 += 32) {
+    float t[32];
+    tmem_ld32(taddr + c0, t);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[c0 + i] = t[i];
+  }
+}
+
+// Factor block types in the combined low-precision factor array [5][N][M][M].
+enum { FT_DINV = 0, FT_E = 1, FT_G = 2, FT_U = 3, FT_V = 4 };
+
+// ======================================================================
+// Sweep kernel
+// ======================================================================
+template <typename E, class C>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_sweep(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_r,
+               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, const int* done, int* status) {
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;
+  uint8_t* sP = sA + C::NA * C::SLICE;
+  uint8_t* sY = sP + 2 * C::TILE;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + 2 * C::TILE);
+  const Bars b = carve<C>(barmem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const int s = blockIdx.y;
+  const int a = s * L + 1;       // first interior row
+  const int nrow = L - 1;        // interior rows
+  const int T = nrow >= 2 ? 2 * nrow - 1 : nrow;
+
+  if (threadIdx.x == 0) init_bars<C>(b);
+  if (warp == 1) {
+    tmem_alloc(tslot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tm_fac);
+      prefetch_tmap(&tm_r);
+      prefetch_tmap(&tm_w);
+      uint32_t ai = 0, pi = 0;
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const bool fwd = t < nrow;
+        const int o = fwd ? t : nrow - 2 - (t - nrow);
+        const int i = a + o;
+        if (!fwd && t == nrow) ok = mbar_wait(&b.extra[0], 0);
+        if (ok) ok = load_tile<C>(sP, b, pi, fwd ? &tm_r : &tm_w, i * Kp + n0);
+        const int first_type = fwd ? FT_DINV : FT_G;
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M);
+        if (fwd && t > 0)
+          for (int c = 0; c < C::NCH && ok; ++c)
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M);
+      }
+      if (!ok) atomicExch(status, 1);
+      // no copy may still be landing when the CTA exits
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = (ai - 1 - q);
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+      for (uint32_t q = 0; q < 2 && q < pi; ++q) {
+        const uint32_t last = pi - 1 - q;
+        mbar_wait(&b.fullP[last % 2], (last / 2) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t ai = 0, pi = 0;
+      bool ok = true;
+      int issued = 0;
+      for (int t = 0; t < T && ok; ++t) {
+        const bool fwd = t < nrow;
+        const int bsel = t & 1;
+        const uint32_t dt = tmem + bsel * C::NT;
+        if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
+        tc_fence_after();
+        bool first = true;
+        uint32_t pslot = 0;
+        if (ok && fwd) {
+          pslot = pi % 2;
+          ok = mbar_wait(&b.fullP[pslot], (pi / 2) & 1);
+          tc_fence_after();
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::TILE), first);
+          if (ok && t > 0) {
+            ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
+            tc_fence_after();
+            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::TILE), first);
+          }
+        } else if (ok) {
+          ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
+          tc_fence_after();
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::TILE), first);
+        }
+        if (ok) {
+          mma_commit(&b.mdone[bsel]);
+          if (fwd) {
+            mma_commit(&b.emptyP[pslot]);
+            ++pi;
+          }
+          ++issued;
+        }
+      }
+      if (!ok) atomicExch(status, 2);
+      // every issued MMA has completed before TMEM is released
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    // epilogue: 128 threads, thread <-> accumulator row
+    int row;
+    bool has;
+    epi_row<C>(warp, lane, &row, &has);
+    const bool leader = (warp == 2 && lane == 0);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    uint32_t pe = (uint32_t)nrow;  // P tiles consumed here start after the forward ones
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const bool fwd = t < nrow;
+      const int o = fwd ? t : nrow - 2 - (t - nrow);
+      const int i = a + o;
+      const int bsel = t & 1;
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      tc_fence_after();
+      float v[C::NT];
+      if (ok) {
+        tmem_row<C>(tmem + lane_base + bsel * C::NT, v);
+      } else {
+#pragma unroll
+        for (int n = 0; n < C::NT; ++n) v[n] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      if (!fwd) {
+        const uint32_t ps = pe % 2;
+        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+        if (ok && has) {
+          const uint8_t* tile = sP + ps * C::TILE;
+#pragma unroll 8
+          for (int n = 0; n < C::NT; ++n) v[n] += ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
+        }
+        named_bar_sync(1, 128);
+        if (ok && leader) mbar_arrive(&b.emptyP[ps]);
+        ++pe;
+      }
+      if (leader) tma_store_wait_read<1>();
+      named_bar_sync(1, 128);
+      uint8_t* ybuf = sY + bsel * C::TILE;
+      if (ok && has) {
+#pragma unroll 8
+        for (int n = 0; n < C::NT; ++n) *reinterpret_cast<E*>(ybuf + kmaj_off<C>(n, row)) = ET<E>::from(v[n]);
+      }
+      fence_proxy_async_smem();
+      named_bar_sync(1, 128);
+      if (leader && ok) {
+        mbar_arrive(&b.yrdy[bsel]);
+        for (int c = 0; c < C::NCH; ++c) tma_store_2d(&tm_w, c * C::CE, i * Kp + n0, ybuf + c * C::TCH);
+        tma_store_commit();
+        if (t == nrow - 1) {
+          tma_store_wait<0>();
+          fence_proxy_async_all();
+          mbar_arrive(&b.extra[0]);
+        }
+      }
+    }
+    if (leader) tma_store_wait<0>();
+    if (!ok && leader) atomicExch(status, 3);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ======================================================================
+// Correction kernel: X_i (+)= W_i + U_i X~_s + V_i X~_{s+1}
+// ======================================================================
+template <typename E, class C>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w, int N, int L,
+                 int S, int Kp, int K, int rows_per_cta, double* __restrict__ X, int accumulate, const int* done,
+                 int* status) {
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;
+  uint8_t* sP = sA + C::NA * C::SLICE;
+  uint8_t* sB = sP + 2 * C::TILE;  // X~_s, X~_{s+1}
+  float* stage = reinterpret_cast<float*>(sB + 2 * C::TILE);
+  constexpr int SLD = C::NT + 1;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(stage + C::M * SLD + 64);
+  const Bars b = carve<C>(barmem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const int s = blockIdx.y;
+  const bool has_next = s + 1 < S;
+  const int r0 = s * L + 1 + blockIdx.z * rows_per_cta;
+  const int r1 = min(r0 + rows_per_cta, s * L + L);
+  const int T = max(0, r1 - r0);
+  const bool do_iface = blockIdx.z == 0;
+
+  if (threadIdx.x == 0) init_bars<C>(b);
+  if (warp == 1) {
+    tmem_alloc(tslot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tm_fac);
+      prefetch_tmap(&tm_w);
+      bool ok = true;
+      // X~_s and X~_{s+1}: the two B operands, loaded once
+      mbar_arrive_expect_tx(&b.extra[0], (has_next ? 2 : 1) * C::TILE);
+      for (int c = 0; c < C::NCH; ++c)
+        tma_load_2d(sB + c * C::TCH, &tm_w, c * C::CE, (s * L) * Kp + n0, &b.extra[0]);
+      if (has_next)
+        for (int c = 0; c < C::NCH; ++c)
+          tma_load_2d(sB + C::TILE + c * C::TCH, &tm_w, c * C::CE, ((s + 1) * L) * Kp + n0, &b.extra[0]);
+      uint32_t ai = 0, pi = 0;
+      for (int t = 0; t < T && ok; ++t) {
+        const int i = r0 + t;
+        ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0);
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M);
+        if (has_next)
+          for (int c = 0; c < C::NCH && ok; ++c)
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M);
+      }
+      if (!ok) atomicExch(status, 4);
+      mbar_wait(&b.extra[0], 0);
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = (ai - 1 - q);
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+      for (uint32_t q = 0; q < 2 && q < pi; ++q) {
+        const uint32_t last = pi - 1 - q;
+        mbar_wait(&b.fullP[last % 2], (last / 2) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(&b.extra[0], 0);
+      tc_fence_after();
+      uint32_t ai = 0;
+      for (int t = 0; t < T && ok; ++t) {
+        const int bsel = t & 1;
+        const uint32_t dt = tmem + bsel * C::NT;
+        if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
+        tc_fence_after();
+        bool first = true;
+        if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first);
+        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::TILE), first);
+        if (ok) mma_commit(&b.mdone[bsel]);
+      }
+      if (!ok) atomicExch(status, 5);
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    int row;
+    bool has;
+    epi_row<C>(warp, lane, &row, &has);
+    const int et = threadIdx.x - 64;  // 0..127
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const size_t MK = (size_t)C::M * K;
+    bool ok = mbar_wait(&b.extra[0], 0);
+    // cooperative, coalesced FP64 update of one M x NT block-row tile from `stage`
+    auto flush = [&](int irow) {
+      double* xb = X + (size_t)irow * MK + n0;
+      for (int e = et; e < C::M * C::NT; e += 128) {
+        const int rr = e / C::NT, cc = e % C::NT;
+        if (n0 + cc < K) {
+          double* o = xb + (size_t)rr * K + cc;
+          const double v = (double)stage[rr * SLD + cc];
+          *o = accumulate ? *o + v : v;
+        }
+      }
+    };
+    if (do_iface) {
+      // interface row k_s: X_K (+)= X~_s
+      if (ok && has)
+        for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = ET<E>::tof(*reinterpret_cast<const E*>(sB + kmaj_off<C>(n, row)));
+      named_bar_sync(1, 128);
+      if (ok) flush(s * L);
+      named_bar_sync(1, 128);
+    }
+    uint32_t pe = 0;
+    for (int t = 0; t < T; ++t) {
+      const int i = r0 + t;
+      const int bsel = t & 1;
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      tc_fence_after();
+      float v[C::NT];
+      if (ok) {
+        tmem_row<C>(tmem + lane_base + bsel * C::NT, v);
+      } else {
+#pragma unroll
+        for (int n = 0; n < C::NT; ++n) v[n] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      const uint32_t ps = pe % 2;
+      if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+      if (ok && has) {
+        const uint8_t* tile = sP + ps * C::TILE;
+#pragma unroll 8
+        for (int n = 0; n < C::NT; ++n) {
+          const float w = ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
+          stage[row * SLD + n] = v[n] + w;
+        }
+      }
+      named_bar_sync(1, 128);
+      if (ok && et == 0) mbar_arrive(&b.emptyP[ps]);
+      ++pe;
+      if (ok) flush(i);
+      named_bar_sync(1, 128);
+    }
+    if (!ok && et == 0) atomicExch(status, 6);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ======================================================================
+// Step 2.2 on the CUDA cores (FP32), block-transposed panels of type E
+// ======================================================================
+template <typename E>
+__device__ __forceinline__ const E* prow(const E* base, int j, int Kp, int M) {
+  return base + (size_t)j * Kp * M;
+}
+
+// F~_s = r_K + A_K W_{K-1} + B_K W_{K+1};  c[l][s] = R[l][s] F~_s  (FP32, c row-major [M][Kp])
+template <typename E, int CW>
+__global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, const float* __restrict__ AK,
+                           const float* __restrict__ BK, const float* __restrict__ R, const int* __restrict__ mid_level,
+                           float* __restrict__ cbuf, int N, int M, int S, int L, int Kp, const int* done) {
+  if (flag_set(done)) return;
+  extern __shared__ float fsm[];
+  const int CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const int s = blockIdx.x, col0 = blockIdx.y * kt;
+  const int Kr = s * L;
+  float* pa = fsm;
+  float* pb = fsm + M * kt;
+  float* pt = fsm + 2 * M * kt;
+  const bool hasL = s > 0 && L > 1, hasR = Kr + 1 < N && L > 1;
+  for (int e = t; e < M * kt; e += blockDim.x) {
+    const int mm = e % M, n = e / M;  // coalesced along m
+    pa[mm * kt + n] = hasL ? ET<E>::tof(prow(w, Kr - 1, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
+    pb[mm * kt + n] = hasR ? ET<E>::tof(prow(w, Kr + 1, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
+    pt[mm * kt + n] = ET<E>::tof(prow(r, Kr, Kp, M)[(size_t)(col0 + n) * M + mm]);
+  }
+  __syncthreads();
+  const size_t MM = (size_t)M * M;
+  float acc[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = pt[m * kt + c0 + c];
+  const float* arow = AK + s * MM + (size_t)m * M;
+  const float* brow = BK + s * MM + (size_t)m * M;
+  for (int k = 0; k < M; ++k) {
+    const float av = hasL ? __ldg(arow + k) : 0.f, bv = hasR ? __ldg(brow + k) : 0.f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = fmaf(av, pa[k * kt + c0 + c], fmaf(bv, pb[k * kt + c0 + c], acc[c]));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < CW; ++c) pt[m * kt + c0 + c] = acc[c];
+  __syncthreads();
+  const int top = mid_level[s];
+  for (int lev = 0; lev <= top; ++lev) {
+    float cc[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) cc[c] = 0.f;
+    const float* rr = R + ((size_t)lev * S + s) * MM + (size_t)m * M;
+    for (int k = 0; k < M; ++k) {
+      const float rv = __ldg(rr + k);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) cc[c] = fmaf(rv, pt[k * kt + c0 + c], cc[c]);
+    }
+    float* out = cbuf + ((size_t)lev * S + s) * M * Kp + (size_t)m * Kp + col0 + c0;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) out[c] = cc[c];
+  }
+}
+
+// X~_m = sum_{j in [l, r]} c[level][j] + HL_m X~_{l-1} + HR_m X~_{r+1}, written as E
+// into the work panel's interface row k_m.
+template <typename E, int CW>
+__global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf, const float* __restrict__ HL,
+                               const float* __restrict__ HR, const int* __restrict__ nodes, int lev, int node_off,
+                               int M, int S, int L, int Kp, const int* done) {
+  if (flag_set(done)) return;
+  extern __shared__ float fsm[];
+  const int CG = blockDim.x / M, kt = CW * CG;
+  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  const int q = node_off + blockIdx.x;
+  const int l = nodes[3 * q], r = nodes[3 * q + 1], mid = nodes[3 * q + 2];
+  const int col0 = blockIdx.y * kt;
+  float* pl = fsm;
+  float* pr = fsm + M * kt;
+  const bool hl = l > 0, hr = r < S - 1;
+  for (int e = t; e < M * kt; e += blockDim.x) {
+    const int mm = e % M, n = e / M;
+    pl[mm * kt + n] = hl ? ET<E>::tof(prow(w, (l - 1) * L, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
+    pr[mm * kt + n] = hr ? ET<E>::tof(prow(w, (r + 1) * L, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
+  }
+  __syncthreads();
+  const size_t MM = (size_t)M * M;
+  float acc[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) acc[c] = 0.f;
+  for (int j = l; j <= r; ++j) {
+    const float* cj = cbuf + ((size_t)lev * S + j) * M * Kp + (size_t)m * Kp + col0 + c0;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] += cj[c];
+  }
+  const float* hlr = HL + (size_t)mid * MM + (size_t)m * M;
+  const float* hrr = HR + (size_t)mid * MM + (size_t)m * M;
+  for (int k = 0; k < M; ++k) {
+    const float a1 = hl ? __ldg(hlr + k) : 0.f, a2 = hr ? __ldg(hrr + k) : 0.f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc[c] = fmaf(a1, pl[k * kt + c0 + c], fmaf(a2, pr[k * kt + c0 + c], acc[c]));
+  }
+  __syncthreads();
+  // transpose through shared memory for a coalesced store along m
+#pragma unroll
+  for (int c = 0; c < CW; ++c) pl[m * kt + c0 + c] = acc[c];
+  __syncthreads();
+  E* out = w + (size_t)mid * L * Kp * M;
+  for (int e = t; e < M * kt; e += blockDim.x) {
+    const int mm = e % M, n = e / M;
+    out[(size_t)(col0 + n) * M + mm] = ET<E>::from(pl[mm * kt + n]);
+  }
+}
+
+// ======================================================================
+// host side
+// ======================================================================
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bt_status make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int eb, uint64_t inner, uint64_t outer,
+                   uint32_t box_inner, uint32_t box_outer) {
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return BT_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * (uint64_t)eb};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return BT_ERR_CUDA;
+  }
+  return BT_OK;
+}
+
+template <typename E>
+__global__ void k_cast_factors(const double* __restrict__ D, const double* __restrict__ Ee,
+                               const double* __restrict__ G, const double* __restrict__ U,
+                               const double* __restrict__ V, E* __restrict__ out, size_t nb) {
+  const size_t n = 5 * nb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t w = e / nb, o = e % nb;
+    const double* src = w == 0 ? D : w == 1 ? Ee : w == 2 ? G : w == 3 ? U : V;
+    out[e] = ET<E>::from((float)src[o]);
+  }
+}
+
+template <typename E, class C>
+size_t sweep_smem() {
+  return 1024 + C::NA * C::SLICE + 4 * C::TILE + kBars(C::NA) * 8 + 16;
+}
+template <typename E, class C>
+size_t correct_smem() {
+  return 1024 + C::NA * C::SLICE + 4 * C::TILE + (size_t)C::M * (C::NT + 1) * 4 + 256 + kBars(C::NA) * 8 + 16;
+}
+
+template <typename E, class C>
+bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int accumulate, const int* done,
+                 int* status, cudaStream_t st) {
+  const int M = C::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
+  const int ntiles = Kp / C::NT;
+  CUtensorMap tm_fac, tm_r, tm_w;
+  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)5 * N * M, C::CE, M));
+  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)N * Kp, C::CE, C::NT));
+  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)N * Kp, C::CE, C::NT));
+  const E* r = reinterpret_cast<const E*>(tb.r);
+  E* w = reinterpret_cast<E*>(tb.w);
+  // step 2.1
+  if (L > 1) {
+    const size_t smem = sweep_smem<E, C>();
+    BT_CUDA(cudaFuncSetAttribute(k_tc_sweep<E, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(h, st, "tc_sweep");
+    k_tc_sweep<E, C><<<dim3(ntiles, S), 192, smem, st>>>(tm_fac, tm_r, tm_w, N, L, Kp, done, status);
+  }
+  BT_CUDA(cudaGetLastError());
+  // step 2.2 (FP32 on the CUDA cores)
+  {
+    constexpr int CW = 4;
+    const int CG = std::max(1, std::min(4, 256 / M));
+    const int kt = CW * CG;
+    const int nt2 = Kp / kt;
+    const LowFactors& f = h->f32;
+    const size_t sm3 = 3 * (size_t)M * kt * sizeof(float);
+    {
+      ProfScope ps(h, st, "tc_iface");
+      k_tc_iface<E, CW><<<dim3(S, nt2), M * CG, sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level, tb.c, N, M, S, L,
+                                                           Kp, done);
+    }
+    BT_CUDA(cudaGetLastError());
+    for (int lev = 0; lev < h->depth; ++lev) {
+      const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
+      ProfScope ps(h, st, "tc_dichotomy");
+      k_tc_dichotomy<E, CW><<<dim3(nn, nt2), M * CG, 2 * (size_t)M * kt * sizeof(float), st>>>(
+          w, tb.c, f.HL, f.HR, h->d_nodes, lev, n0, M, S, L, Kp, done);
+    }
+    BT_CUDA(cudaGetLastError());
+  }
+  // step 2.3
+  {
+    const int rows = std::max(1, L - 1);
+    int chunks = std::max(1, std::min(rows, (2 * 152 + S * ntiles - 1) / (S * ntiles)));
+    const int rpc = (rows + chunks - 1) / chunks;
+    chunks = (rows + rpc - 1) / rpc;
+    const size_t smem = correct_smem<E, C>();
+    BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(h, st, "tc_correct");
+    k_tc_correct<E, C><<<dim3(ntiles, S, chunks), 192, smem, st>>>(tm_fac, tm_w, N, L, S, Kp, (int)K,
+                                                                    L > 1 ? rpc : 0, X, accumulate, done, status);
+  }
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+using CfgB128 = Cfg<__nv_bfloat16, 128, 64, 6>;
+using CfgT128 = Cfg<float, 128, 32, 6>;
+using CfgB64 = Cfg<__nv_bfloat16, 64, 128, 8>;
+using CfgT64 = Cfg<float, 64, 64, 8>;
+
+}  // namespace
+
+int tc_col_tile(int precision, int M) {
+  if (M == 128) return precision == BT_PREC_BF16 ? CfgB128::NT : CfgT128::NT;
+  if (M == 64) return precision == BT_PREC_BF16 ? CfgB64::NT : CfgT64::NT;
+  return 0;
+}
+
+bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
+  void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : &h->tc_fac_tf32;
+  if (*slot) return BT_OK;
+  const size_t nb = (size_t)h->N * h->M * h->M;
+  const size_t eb = precision == BT_PREC_BF16 ? 2 : 4;
+  BT_TRY(h->arena.alloc(slot, 5 * nb * eb));
+  if (precision == BT_PREC_BF16)
+    k_cast_factors<__nv_bfloat16><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
+                                                        reinterpret_cast<__nv_bfloat16*>(*slot), nb);
+  else
+    k_cast_factors<float><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V, reinterpret_cast<float*>(*slot), nb);
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,
+                   const int* done, int* status, cudaStream_t st) {
+  const int M = (int)h->M;
+  if (precision == BT_PREC_BF16) {
+    if (M == 128) return run_tc<__nv_bfloat16, CfgB128>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 64) return run_tc<__nv_bfloat16, CfgB64>(h, tb, K, X, accumulate, done, status, st);
+  } else {
+    if (M == 128) return run_tc<float, CfgT128>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 64) return run_tc<float, CfgT64>(h, tb, K, X, accumulate, done, status, st);
+  }
+  set_error("the tensor-core solve supports block sizes M = 64 and M = 128");
+  return BT_ERR_UNSUPPORTED;
+}
+
+}  // namespace bt

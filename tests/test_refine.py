@@ -86,3 +86,63 @@ def test_refined_zero_rhs(bt):
     with bt.factor(_t(A), _t(B), _t(C), 4) as fac:
         X = fac.solve(torch.zeros((16, 3, 2), dtype=torch.float64, device=DEV), precision="f32")
     assert float(X.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# tensor-core inner solve (tcgen05, BF16 / TF32 operands, FP32 accumulation)
+# ---------------------------------------------------------------------------
+TC = ["bf16", "tf32"]
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("N,M,K,S", [
+    (64, 64, 20, 8),     # one column tile, ragged
+    (48, 128, 70, 6),    # M = 128, two column tiles with a ragged tail
+    (40, 64, 130, 20),   # L = 2: one interior row per segment
+    (32, 128, 33, 32),   # S = N: every row an interface (no sweep)
+    (96, 64, 1, 1),      # S = 1, single right-hand side
+])
+def test_tc_refined_dense(bt, prec, N, M, K, S):
+    A, B, C = gen.dominant_blocks(N, M, seed=N + M + K)
+    F = gen.uniform_rhs(N, M, K, seed=K + 1)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        X, info = fac.solve(_t(F), precision=prec, tol=1e-12, return_info=True)
+    X = X.cpu().numpy()
+    assert info["converged"] and info["rel_res"] <= 1e-12
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_tc_refined_stencil(bt, prec):
+    N, M, K, S = 64, 128, 40, 8
+    A, B, C = gen.acoustic_system(N, M)
+    F = gen.acoustic_rhs(N, M, K, seed=5)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        assert fac.stencil == 1
+        X, info = fac.solve(_t(F), precision=prec, tol=1e-12, return_info=True)
+    X = X.cpu().numpy()
+    assert info["converged"]
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_tc_refined_acoustic_full_size(bt, prec):
+    w = gen.config2()
+    cols = [0, 257, 511]
+    with bt.factor(_t(w.A), _t(w.B), _t(w.C), w.S) as fac:
+        X, info = fac.solve(_t(w.F), precision=prec, tol=1e-12, return_info=True)
+        X = X.cpu().numpy()
+    assert info["converged"] and info["rel_res"] <= 1e-12, info
+    Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
+    assert oracle.rel_err(X[:, :, cols], Xr) <= 1e-10
+
+
+def test_tc_unsupported_block_size(bt):
+    A, B, C = gen.dominant_blocks(16, 8, seed=1)
+    F = gen.uniform_rhs(16, 8, 2, seed=2)
+    with bt.factor(_t(A), _t(B), _t(C), 4) as fac:
+        with pytest.raises(bt.BtError) as ei:
+            fac.solve(_t(F), precision="bf16")
+        assert ei.value.name == "BT_ERR_UNSUPPORTED"
