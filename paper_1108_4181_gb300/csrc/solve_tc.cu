@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(192, 1)
       const int i = a + o;
       const int bsel = t & 1;
       if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       tc_fence_after();
       float v[C::NT];
       if (ok) {
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(192, 1)
       if (!fwd) {
         const uint32_t ps = pe % 2;
         if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+        ok = __all_sync(0xffffffffu, ok);
         if (ok && has) {
           const uint8_t* tile = sP + ps * C::TILE;
 #pragma unroll 8
@@ -485,6 +487,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const size_t MK = (size_t)C::M * K;
     bool ok = mbar_wait(&b.extra[0], 0);
+    ok = __all_sync(0xffffffffu, ok);
     // cooperative, coalesced FP64 update of one M x NT block-row tile from `stage`
     auto flush = [&](int irow) {
       double* xb = X + (size_t)irow * MK + n0;
@@ -510,6 +513,7 @@ __global__ void __launch_bounds__(192, 1)
       const int i = r0 + t;
       const int bsel = t & 1;
       if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       tc_fence_after();
       float v[C::NT];
       if (ok) {
@@ -523,6 +527,7 @@ __global__ void __launch_bounds__(192, 1)
       if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
       const uint32_t ps = pe % 2;
       if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+        ok = __all_sync(0xffffffffu, ok);
       if (ok && has) {
         const uint8_t* tile = sP + ps * C::TILE;
 #pragma unroll 8
