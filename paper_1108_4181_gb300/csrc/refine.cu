@@ -104,26 +104,33 @@ __global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restric
   if (st->done) return;
   __shared__ double tile[32][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int64_t n0 = (int64_t)blockIdx.x * 32, j = blockIdx.z;
-  const int m0 = blockIdx.y * 32;
+  const int64_t tn = (Kp + 31) / 32, tm = (M + 31) / 32;
+  const int64_t ntile = tn * tm * N;
   double acc = 0.0;
+  // grid-stride over 32 x 32 tiles; one partial sum per CTA
+  for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
+    const int64_t n0 = (q0 % tn) * 32;
+    const int m0 = (int)((q0 / tn) % tm) * 32;
+    const int64_t j = q0 / (tn * tm);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int m = m0 + ty + 8 * q;
-    const int64_t n = n0 + tx;
-    double v = 0.0;
-    if (m < M && n < K) {
-      v = stencil_res(F, X, Cd, N, M, K, j, m, n, first);
-      acc += v * v;
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + ty + 8 * q;
+      const int64_t n = n0 + tx;
+      double v = 0.0;
+      if (m < M && n < K) {
+        v = stencil_res(F, X, Cd, N, M, K, j, m, n, first);
+        acc += v * v;
+      }
+      tile[ty + 8 * q][tx] = v;
     }
-    tile[ty + 8 * q][tx] = v;
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t n = n0 + ty + 8 * q;
-    const int m = m0 + tx;
-    if (m < M && n < Kp) r[((size_t)j * Kp + n) * M + m] = to_lp<TR>(tile[tx][ty + 8 * q]);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t n = n0 + ty + 8 * q;
+      const int m = m0 + tx;
+      if (m < M && n < Kp) r[((size_t)j * Kp + n) * M + m] = to_lp<TR>(tile[tx][ty + 8 * q]);
+    }
+    __syncthreads();
   }
   block_add(acc, first ? &st->fn2 : &st->rn2[pass]);
   if (first) block_add(acc, &st->rn2[0]);
@@ -238,12 +245,9 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   ProfScope ps(h, s, "residual");
   if (first || h->stencil) {
     if (trans) {
-      if (h->N > 65535) {
-        set_error("residual: N > 65535 is not supported by the transposed residual kernel");
-        return BT_ERR_UNSUPPORTED;
-      }
-      dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)h->N);
-      k_resid_stencil_t<TR><<<grid, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, st);
+      const int64_t ntile = ((Kp + 31) / 32) * ((M + 31) / 32) * h->N;
+      const int blocks = (int)std::min<int64_t>(ntile, 152 * 8);
+      k_resid_stencil_t<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, st);
     } else {
       const size_t n = (size_t)h->N * M * K;
       const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);

@@ -390,21 +390,38 @@ __global__ void __launch_bounds__(192, 1)
 
 // ======================================================================
 // Correction kernel: X_i (+)= W_i + U_i X~_s + V_i X~_{s+1}
+//
+// The FP64 solution tile of every row is moved by TMA (XT = true: X has an
+// even leading dimension and a 16-byte aligned base): the producer loads the
+// W_i tile and the X_i tile into one stage of the P ring, the epilogue adds
+// the accumulator and W_i into the X tile in shared memory and stores it back
+// with TMA, so the FP64 read-modify-write streams asynchronously.  With
+// XT = false the epilogue updates X with plain coalesced loads and stores.
+// Chunk 0 of every segment also updates the interface row: X_K (+)= X~_s.
 // ======================================================================
-template <typename E, class C>
+template <class C>
+__device__ __forceinline__ uint32_t xt_off(int m, int n) {
+  // X tile: NT/16 boxes of [M rows][16 doubles], 128-byte swizzle
+  return (uint32_t)((n >> 4) * (C::M * 128) + m * 128 + ((((n & 15) >> 1) ^ (m & 7)) << 4) + (n & 1) * 8);
+}
+
+template <typename E, class C, bool XT>
 __global__ void __launch_bounds__(192, 1)
-    k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w, int N, int L,
-                 int S, int Kp, int K, int rows_per_cta, double* __restrict__ X, int accumulate, const int* done,
-                 int* status) {
+    k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
+                 const __grid_constant__ CUtensorMap tm_x, int N, int L, int S, int Kp, int K, int rows_per_cta,
+                 double* __restrict__ X, int accumulate, const int* done, int* status) {
   if (flag_set(done)) return;
+  constexpr int XB = C::NT / 16;                 // X boxes per tile
+  constexpr int XBYTES = XT ? XB * C::M * 128 : 0;
+  constexpr int PST = C::TILE + XBYTES;          // one P stage: W tile (+ X tile)
+  constexpr int SLD = C::NT + 1;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLICE;
-  uint8_t* sB = sP + 2 * C::TILE;  // X~_s, X~_{s+1}
+  uint8_t* sB = sP + 2 * PST;  // X~_s, X~_{s+1}
   float* stage = reinterpret_cast<float*>(sB + 2 * C::TILE);
-  constexpr int SLD = C::NT + 1;
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(stage + C::M * SLD + 64);
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(stage + (XT ? 0 : C::M * SLD) + 64);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
 
@@ -415,7 +432,10 @@ __global__ void __launch_bounds__(192, 1)
   const int r0 = s * L + 1 + blockIdx.z * rows_per_cta;
   const int r1 = min(r0 + rows_per_cta, s * L + L);
   const int T = max(0, r1 - r0);
+  const int pre = (XT && blockIdx.z == 0) ? 1 : 0;  // interface row through the P ring
   const bool do_iface = blockIdx.z == 0;
+  // X boxes that start inside the matrix (later ones are skipped, not clipped)
+  const int xboxes = XT ? max(0, min(XB, (K - n0 + 15) / 16)) : 0;
 
   if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
@@ -431,6 +451,7 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       prefetch_tmap(&tm_fac);
       prefetch_tmap(&tm_w);
+      if (XT) prefetch_tmap(&tm_x);
       bool ok = true;
       // X~_s and X~_{s+1}: the two B operands, loaded once
       mbar_arrive_expect_tx(&b.extra[0], (has_next ? 2 : 1) * C::TILE);
@@ -440,9 +461,23 @@ __global__ void __launch_bounds__(192, 1)
         for (int c = 0; c < C::NCH; ++c)
           tma_load_2d(sB + C::TILE + c * C::TCH, &tm_w, c * C::CE, ((s + 1) * L) * Kp + n0, &b.extra[0]);
       uint32_t ai = 0, pi = 0;
+      auto load_stage = [&](int irow, bool with_w) -> bool {
+        const uint32_t slot = pi % 2, use = pi / 2;
+        if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
+        const int xload = (XT && accumulate) ? xboxes : 0;
+        mbar_arrive_expect_tx(&b.fullP[slot], (with_w ? C::TILE : 0) + xload * C::M * 128);
+        uint8_t* st = sP + slot * PST;
+        if (with_w)
+          for (int c = 0; c < C::NCH; ++c) tma_load_2d(st + c * C::TCH, &tm_w, c * C::CE, irow * Kp + n0, &b.fullP[slot]);
+        for (int q = 0; q < xload; ++q)
+          tma_load_2d(st + C::TILE + q * C::M * 128, &tm_x, n0 + 16 * q, irow * C::M, &b.fullP[slot]);
+        ++pi;
+        return true;
+      };
+      if (pre) ok = load_stage(s * L, false);
       for (int t = 0; t < T && ok; ++t) {
         const int i = r0 + t;
-        ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0);
+        ok = load_stage(i, true);
         for (int c = 0; c < C::NCH && ok; ++c)
           ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M);
         if (has_next)
@@ -484,11 +519,36 @@ __global__ void __launch_bounds__(192, 1)
     bool has;
     epi_row<C>(warp, lane, &row, &has);
     const int et = threadIdx.x - 64;  // 0..127
+    const bool leader = et == 0;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const size_t MK = (size_t)C::M * K;
     bool ok = mbar_wait(&b.extra[0], 0);
     ok = __all_sync(0xffffffffu, ok);
-    // cooperative, coalesced FP64 update of one M x NT block-row tile from `stage`
+    uint32_t pe = 0;
+    // X tile of P stage `ps` (XT): this thread's row += v[] (or = v[]), then TMA store
+    auto xt_update = [&](uint32_t ps, const float (&v)[C::NT], int irow) {
+      uint8_t* xt = sP + ps * PST + C::TILE;
+      if (ok && has) {
+#pragma unroll 4
+        for (int n = 0; n < C::NT; n += 2) {
+          double2* p = reinterpret_cast<double2*>(xt + xt_off<C>(row, n));
+          double2 x = accumulate ? *p : make_double2(0.0, 0.0);
+          x.x += (double)v[n];
+          x.y += (double)v[n + 1];
+          *p = x;
+        }
+      }
+      fence_proxy_async_smem();
+      named_bar_sync(1, 128);
+      if (leader && ok) {
+        for (int q = 0; q < xboxes; ++q) tma_store_2d(&tm_x, n0 + 16 * q, irow * C::M, xt + q * C::M * 128);
+        tma_store_commit();
+        // the previous stage's store has finished reading: hand its slot back
+        tma_store_wait_read<1>();
+        if (pe > 0) mbar_arrive(&b.emptyP[(pe - 1) % 2]);
+      }
+    };
+    // SIMT path: cooperative, coalesced FP64 update of one tile from `stage`
     auto flush = [&](int irow) {
       double* xb = X + (size_t)irow * MK + n0;
       for (int e = et; e < C::M * C::NT; e += 128) {
@@ -502,13 +562,24 @@ __global__ void __launch_bounds__(192, 1)
     };
     if (do_iface) {
       // interface row k_s: X_K (+)= X~_s
-      if (ok && has)
-        for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = ET<E>::tof(*reinterpret_cast<const E*>(sB + kmaj_off<C>(n, row)));
-      named_bar_sync(1, 128);
-      if (ok) flush(s * L);
-      named_bar_sync(1, 128);
+      float v[C::NT];
+#pragma unroll
+      for (int n = 0; n < C::NT; ++n) v[n] = (ok && has) ? ET<E>::tof(*reinterpret_cast<const E*>(sB + kmaj_off<C>(n, row))) : 0.f;
+      if constexpr (XT) {
+        const uint32_t ps = pe % 2;
+        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        xt_update(ps, v, s * L);
+        ++pe;
+      } else {
+        if (has)
+#pragma unroll
+          for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = v[n];
+        named_bar_sync(1, 128);
+        if (ok) flush(s * L);
+        named_bar_sync(1, 128);
+      }
     }
-    uint32_t pe = 0;
     for (int t = 0; t < T; ++t) {
       const int i = r0 + t;
       const int bsel = t & 1;
@@ -527,22 +598,27 @@ __global__ void __launch_bounds__(192, 1)
       if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
       const uint32_t ps = pe % 2;
       if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
-        ok = __all_sync(0xffffffffu, ok);
+      ok = __all_sync(0xffffffffu, ok);
       if (ok && has) {
-        const uint8_t* tile = sP + ps * C::TILE;
+        const uint8_t* tile = sP + ps * PST;
 #pragma unroll 8
-        for (int n = 0; n < C::NT; ++n) {
-          const float w = ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
-          stage[row * SLD + n] = v[n] + w;
-        }
+        for (int n = 0; n < C::NT; ++n) v[n] += ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
       }
-      named_bar_sync(1, 128);
-      if (ok && et == 0) mbar_arrive(&b.emptyP[ps]);
+      if constexpr (XT) {
+        xt_update(ps, v, i);
+      } else {
+        if (ok && has)
+#pragma unroll 8
+          for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = v[n];
+        named_bar_sync(1, 128);
+        if (ok && leader) mbar_arrive(&b.emptyP[ps]);
+        if (ok) flush(i);
+        named_bar_sync(1, 128);
+      }
       ++pe;
-      if (ok) flush(i);
-      named_bar_sync(1, 128);
     }
-    if (!ok && et == 0) atomicExch(status, 6);
+    if (XT && leader) tma_store_wait<0>();
+    if (!ok && leader) atomicExch(status, 6);
   }
   tc_fence_before();
   __syncthreads();
@@ -697,6 +773,11 @@ bt_status make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int
   return BT_OK;
 }
 
+bt_status make_map_f64(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                       uint32_t box_outer) {
+  return make_map(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, inner, outer, box_inner, box_outer);
+}
+
 template <typename E>
 __global__ void k_cast_factors(const double* __restrict__ D, const double* __restrict__ Ee,
                                const double* __restrict__ G, const double* __restrict__ U,
@@ -709,42 +790,54 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
   }
 }
 
-template <typename E, class C>
+template <class C>
 size_t sweep_smem() {
   return 1024 + C::NA * C::SLICE + 4 * C::TILE + kBars(C::NA) * 8 + 16;
 }
-template <typename E, class C>
+template <class C, bool XT>
 size_t correct_smem() {
-  return 1024 + C::NA * C::SLICE + 4 * C::TILE + (size_t)C::M * (C::NT + 1) * 4 + 256 + kBars(C::NA) * 8 + 16;
+  const size_t xbytes = XT ? (size_t)(C::NT / 16) * C::M * 128 : 0;
+  return 1024 + C::NA * C::SLICE + 2 * (C::TILE + xbytes) + 2 * C::TILE +
+         (XT ? 0 : (size_t)C::M * (C::NT + 1) * 4) + 256 + kBars(C::NA) * 8 + 16;
 }
 
-template <typename E, class C>
+// CS: configuration of the sweep kernel, CC: of the correction kernel.
+template <typename E, class CS, class CC>
 bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int accumulate, const int* done,
                  int* status, cudaStream_t st) {
-  const int M = C::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
-  const int ntiles = Kp / C::NT;
-  CUtensorMap tm_fac, tm_r, tm_w;
-  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)5 * N * M, C::CE, M));
-  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)N * Kp, C::CE, C::NT));
-  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, C::eb, (uint64_t)M, (uint64_t)N * Kp, C::CE, C::NT));
+  const int M = CS::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
+  CUtensorMap tm_fac, tm_r, tm_w, tm_wc, tm_x;
+  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)5 * N * M, CS::CE, M));
+  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)N * Kp, CS::CE, CS::NT));
+  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)N * Kp, CS::CE, CS::NT));
+  BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)N * Kp, CC::CE, CC::NT));
+  // FP64 solution tiles by TMA need an even leading dimension and a 16-byte aligned base
+  const bool xt = (K % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  if (xt) {
+    BT_TRY(make_map_f64(&tm_x, X, (uint64_t)K, (uint64_t)N * M, 16, M));
+  } else {
+    std::memset(&tm_x, 0, sizeof(tm_x));
+  }
   const E* r = reinterpret_cast<const E*>(tb.r);
   E* w = reinterpret_cast<E*>(tb.w);
   // step 2.1
   if (L > 1) {
-    const size_t smem = sweep_smem<E, C>();
-    BT_CUDA(cudaFuncSetAttribute(k_tc_sweep<E, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = sweep_smem<CS>();
+    BT_CUDA(cudaFuncSetAttribute(k_tc_sweep<E, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(h, st, "tc_sweep");
-    k_tc_sweep<E, C><<<dim3(ntiles, S), 192, smem, st>>>(tm_fac, tm_r, tm_w, N, L, Kp, done, status);
+    k_tc_sweep<E, CS><<<dim3(Kp / CS::NT, S), 192, smem, st>>>(tm_fac, tm_r, tm_w, N, L, Kp, done, status);
   }
   BT_CUDA(cudaGetLastError());
   // step 2.2 (FP32 on the CUDA cores)
   {
-    constexpr int CW = 4;
-    const int CG = std::max(1, std::min(4, 256 / M));
+    constexpr int CW = 8;
+    const int CG = 4;
     const int kt = CW * CG;
     const int nt2 = Kp / kt;
     const LowFactors& f = h->f32;
     const size_t sm3 = 3 * (size_t)M * kt * sizeof(float);
+    BT_CUDA(cudaFuncSetAttribute(k_tc_iface<E, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    BT_CUDA(cudaFuncSetAttribute(k_tc_dichotomy<E, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     {
       ProfScope ps(h, st, "tc_iface");
       k_tc_iface<E, CW><<<dim3(S, nt2), M * CG, sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level, tb.c, N, M, S, L,
@@ -761,31 +854,44 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   }
   // step 2.3
   {
+    const int ntiles = Kp / CC::NT;
     const int rows = std::max(1, L - 1);
     int chunks = std::max(1, std::min(rows, (2 * 152 + S * ntiles - 1) / (S * ntiles)));
     const int rpc = (rows + chunks - 1) / chunks;
     chunks = (rows + rpc - 1) / rpc;
-    const size_t smem = correct_smem<E, C>();
-    BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(h, st, "tc_correct");
-    k_tc_correct<E, C><<<dim3(ntiles, S, chunks), 192, smem, st>>>(tm_fac, tm_w, N, L, S, Kp, (int)K,
-                                                                    L > 1 ? rpc : 0, X, accumulate, done, status);
+    if (xt) {
+      const size_t smem = correct_smem<CC, true>();
+      BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tc_correct<E, CC, true><<<dim3(ntiles, S, chunks), 192, smem, st>>>(
+          tm_fac, tm_wc, tm_x, N, L, S, Kp, (int)K, L > 1 ? rpc : 0, X, accumulate, done, status);
+    } else {
+      const size_t smem = correct_smem<CC, false>();
+      BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tc_correct<E, CC, false><<<dim3(ntiles, S, chunks), 192, smem, st>>>(
+          tm_fac, tm_wc, tm_x, N, L, S, Kp, (int)K, L > 1 ? rpc : 0, X, accumulate, done, status);
+    }
   }
   BT_CUDA(cudaGetLastError());
   return BT_OK;
 }
 
-using CfgB128 = Cfg<__nv_bfloat16, 128, 64, 6>;
-using CfgT128 = Cfg<float, 128, 32, 6>;
-using CfgB64 = Cfg<__nv_bfloat16, 64, 128, 8>;
-using CfgT64 = Cfg<float, 64, 64, 8>;
+// sweep / correction configurations per (operand type, block size)
+using SwB128 = Cfg<__nv_bfloat16, 128, 64, 6>;
+using CoB128 = Cfg<__nv_bfloat16, 128, 32, 4>;
+using SwT128 = Cfg<float, 128, 32, 6>;
+using CoT128 = Cfg<float, 128, 32, 4>;
+using SwB64 = Cfg<__nv_bfloat16, 64, 128, 8>;
+using CoB64 = Cfg<__nv_bfloat16, 64, 64, 4>;
+using SwT64 = Cfg<float, 64, 64, 8>;
+using CoT64 = Cfg<float, 64, 64, 4>;
 
 }  // namespace
 
 int tc_col_tile(int precision, int M) {
-  if (M == 128) return precision == BT_PREC_BF16 ? CfgB128::NT : CfgT128::NT;
-  if (M == 64) return precision == BT_PREC_BF16 ? CfgB64::NT : CfgT64::NT;
-  return 0;
+  (void)precision;
+  // internal panels are padded to a multiple of every column tile in use
+  return (M == 128 || M == 64) ? 128 : 0;
 }
 
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
@@ -807,11 +913,11 @@ bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K
                    const int* done, int* status, cudaStream_t st) {
   const int M = (int)h->M;
   if (precision == BT_PREC_BF16) {
-    if (M == 128) return run_tc<__nv_bfloat16, CfgB128>(h, tb, K, X, accumulate, done, status, st);
-    if (M == 64) return run_tc<__nv_bfloat16, CfgB64>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 128) return run_tc<__nv_bfloat16, SwB128, CoB128>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 64) return run_tc<__nv_bfloat16, SwB64, CoB64>(h, tb, K, X, accumulate, done, status, st);
   } else {
-    if (M == 128) return run_tc<float, CfgT128>(h, tb, K, X, accumulate, done, status, st);
-    if (M == 64) return run_tc<float, CfgT64>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 128) return run_tc<float, SwT128, CoT128>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 64) return run_tc<float, SwT64, CoT64>(h, tb, K, X, accumulate, done, status, st);
   }
   set_error("the tensor-core solve supports block sizes M = 64 and M = 128");
   return BT_ERR_UNSUPPORTED;
