@@ -133,6 +133,32 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
 bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF,
                            double* dA, double* dB, double* dC, void* stream);
 
+/*
+ * bt_solve_noalloc -- the FP64 solve of bt_solve, for callers that cannot
+ * allocate device memory at solve time.  The paper has no counterpart: it is a
+ * service of this library.  Some callers cannot call cudaMalloc once they are
+ * running: a host whose device memory is owned by another allocator (a
+ * framework's caching pool or a fixed arena), or a latency-bound loop that
+ * must not take the device-wide synchronisation cudaMalloc and cudaFree may
+ * imply.  bt_solve grows a scratch buffer in the handle on first use;
+ * this entry point instead uses a scratch array of BT_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   - F, K, X, stream: as for bt_solve (the caller owns inputs and outputs).
+ *   - The scratch needed is depth * S * M * K * 8 bytes (depth from
+ *     bt_handle_query); larger requests return BT_ERR_ARG and do nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) for that device; make that first call before any
+ *     stream capture.  The device of the handle must be current.
+ *   - All calls share the one array per device: calls whose work overlaps on
+ *     the GPU (other streams, other threads) race on it and give wrong results.
+ *     The array keeps the previous call's contents; this solve overwrites
+ *     every entry it reads, so nothing needs clearing.
+ *   - No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+#define BT_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+bt_status bt_solve_noalloc(bt_handle h, const double* F, int64_t K, double* X, void* stream);
+
 /* Releases the handle and all its device memory (synchronises the device). */
 void bt_destroy(bt_handle h);
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "bt_handle_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "bt_factor_export": (ctypes.c_int, [_vp, _i32, _vp]),
     "bt_solve_stages": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
+    "bt_solve_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "bt_profile_enable": (ctypes.c_int, [_vp, _i32]),
     "bt_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(BtKernelStat), _i32, ctypes.POINTER(_i32)]),
 }

@@ -186,6 +186,21 @@ bt_status bt_solve_stages(bt_handle h, const double* F, int64_t K, double* X, in
   return solve_f64(h, F, K, X, stages, (cudaStream_t)stream);
 }
 
+bt_status bt_solve_noalloc(bt_handle h, const double* F, int64_t K, double* X, void* stream) {
+  if (!h || !F || !X || K < 1) {
+    set_error("bt_solve_noalloc: need a handle, device F and X, K >= 1");
+    return BT_ERR_ARG;
+  }
+  const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
+  const char* f0 = reinterpret_cast<const char*>(F);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  if (f0 < x0 + bytes && x0 < f0 + bytes) {
+    set_error("bt_solve_noalloc: X must not overlap F");
+    return BT_ERR_ARG;
+  }
+  return solve_f64_noalloc(h, F, K, X, (cudaStream_t)stream);
+}
+
 bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* stream) {
   return bt_solve_stages(h, F, K, X, 3, stream);
 }

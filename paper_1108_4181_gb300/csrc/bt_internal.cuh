@@ -172,6 +172,9 @@ bt_status factor_f64(bt_handle_s* h, const double* A, const double* B, const dou
 bt_status solve_f64(bt_handle_s* h, const double* F, int64_t K, double* X, int stages,
                     cudaStream_t st);
 
+// FP64 stage-2 pipeline with its scratch in the library's fixed array (no allocation).
+bt_status solve_f64_noalloc(bt_handle_s* h, const double* F, int64_t K, double* X, cudaStream_t st);
+
 // Grows the handle's scratch pool to at least `bytes`.
 bt_status ensure_scratch(bt_handle_s* h, size_t bytes, cudaStream_t st);
 

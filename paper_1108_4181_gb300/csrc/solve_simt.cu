@@ -26,6 +26,8 @@
 // Every kernel returns at once when the refinement flag `done` is set.
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "bt_internal.cuh"
 
@@ -418,6 +420,59 @@ bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, fl
     case 2: return go(std::integral_constant<int, 2>());
     default: return go(std::integral_constant<int, 1>());
   }
+}
+
+}  // namespace bt
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 solve (bt_solve_noalloc): the series-term scratch of
+// the FP64 pipeline lives in a fixed array compiled into the library instead
+// of the handle's grow-on-demand pool.  Host code must not take the array's
+// name as a device address: its device address is looked up once per device
+// with cudaGetSymbolAddress and handed to the kernels.
+// ---------------------------------------------------------------------------
+namespace bt {
+
+static __device__ __align__(256) double g_noalloc_scratch[BT_NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+bt_status solve_f64_noalloc(bt_handle_s* h, const double* F, int64_t K, double* X, cudaStream_t st) {
+  const size_t need = (size_t)h->depth * h->S * h->M * K * sizeof(double);
+  if (need > (size_t)BT_NOALLOC_SCRATCH_BYTES) {
+    set_error("bt_solve_noalloc: needs " + std::to_string(need) + " bytes of scratch (depth*S*M*K*8), more than " +
+              "the " + std::to_string((size_t)BT_NOALLOC_SCRATCH_BYTES) + " bytes compiled into the library");
+    return BT_ERR_ARG;
+  }
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device || dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("bt_solve_noalloc: the handle's device must be current (and below device index 64)");
+    return BT_ERR_ARG;
+  }
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "bt_solve_noalloc: cudaGetSymbolAddress");
+      g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  SimtArgs<double> a;
+  a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = (int)h->M;
+  a.Dinv = h->Dinv; a.E = h->E; a.G = h->G; a.U = h->U; a.V = h->V;
+  a.AK = h->AK; a.BK = h->BK; a.R = h->R; a.HL = h->HL; a.HR = h->HR;
+  a.nodes = h->d_nodes; a.mid_level = h->d_mid_level;
+  a.c = scratch;
+  a.done = nullptr;
+  return run<double>(h, a, F, X, X, 3, 0, 0, st);
 }
 
 }  // namespace bt
