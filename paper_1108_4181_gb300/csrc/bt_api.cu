@@ -87,7 +87,7 @@ static void destroy_handle(bt_handle_s* h) {
   h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
-  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->ir_state})
+  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->ir_state, h->adj_lam})
     if (q) cudaFree(q);
   cudaSetDevice(prev);
   delete h;
@@ -240,9 +240,24 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
 
 bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF, double* dA,
                            double* dB, double* dC, void* stream) {
-  (void)h; (void)X; (void)G; (void)K; (void)dF; (void)dA; (void)dB; (void)dC; (void)stream;
-  set_error("bt_solve_adjoint: not available in this build");
-  return BT_ERR_UNSUPPORTED;
+  if (!h || !X || !G || K < 1) {
+    set_error("bt_solve_adjoint: need a handle, device X and G, K >= 1");
+    return BT_ERR_ARG;
+  }
+  if (h->N > 65535) {
+    set_error("bt_solve_adjoint: N > 65535 is not supported");
+    return BT_ERR_UNSUPPORTED;
+  }
+  const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
+  if (dF) {
+    const char* g0 = reinterpret_cast<const char*>(G);
+    const char* f0 = reinterpret_cast<const char*>(dF);
+    if (g0 < f0 + bytes && f0 < g0 + bytes) {
+      set_error("bt_solve_adjoint: dF must not overlap G");
+      return BT_ERR_ARG;
+    }
+  }
+  return solve_adjoint(h, X, G, K, dF, dA, dB, dC, (cudaStream_t)stream);
 }
 
 void bt_destroy(bt_handle h) { destroy_handle(h); }

@@ -125,8 +125,11 @@ struct bt_handle_s {
   double* scratch = nullptr;
   size_t scratch_bytes = 0;
 
-  // Factors of P^T, built on the first adjoint call.
+  // Factors of P^T, built on the first adjoint call, and the lambda buffer
+  // used when the caller does not ask for dF.
   bt_handle_s* adj = nullptr;
+  void* adj_lam = nullptr;
+  size_t adj_lam_bytes = 0;
 
   LowFactors f32;
   // Tensor-core factor copies [5][N][M][M] (Dinv, E, G, U, V) in BF16 / FP32.
@@ -204,6 +207,10 @@ bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st);
 // One tensor-core stage-2 solve: r -> w (y, W, X~), then X (+)= solution.
 bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,
                    const int* done, int* status, cudaStream_t st);
+
+// Adjoint solve and gradient contractions (bt_solve_adjoint).
+bt_status solve_adjoint(bt_handle_s* h, const double* X, const double* G, int64_t K, double* dF, double* dA,
+                        double* dB, double* dC, cudaStream_t st);
 
 // Builds h->f32 from the FP64 factors (once per handle).
 bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st);
