@@ -254,7 +254,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32+f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}[precision],
+        "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32+f64", "tf32": "tf32+f64", "bf16": "bf16+f64", "bf16x3": "bf16x3+f64"}[precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": precision, "tol": args.tol,
                    "l2": "inputs larger than L2 (F, X 2.1 GB each)", "pre_s": pre_s,
@@ -292,7 +292,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["f64", "f32", "tf32", "bf16"], default="f64")
+    ap.add_argument("--precision", choices=["f64", "f32", "tf32", "bf16", "bf16x3"], default="f64")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -50,7 +50,9 @@ typedef enum {
   BT_PREC_F64 = 0,   /* every product in FP64 */
   BT_PREC_TF32 = 1,  /* panel products on tensor cores in TF32, FP32 accumulation */
   BT_PREC_BF16 = 2,  /* panel products on tensor cores in BF16, FP32 accumulation */
-  BT_PREC_F32 = 3    /* panel products on the CUDA cores in FP32 */
+  BT_PREC_F32 = 3,   /* panel products on the CUDA cores in FP32 */
+  BT_PREC_BF16X3 = 4 /* tensor cores, every operand split into two BF16 terms (hi + lo),
+                        three MMAs per product: about 2^-17 relative operand precision */
 } bt_precision;
 
 /* Options of bt_solve_ex.  Zero-initialised options mean: FP64, defaults. */

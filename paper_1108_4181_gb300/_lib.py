@@ -18,7 +18,7 @@ STATUS_NAMES = {
     0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_SINGULAR", 3: "BT_ERR_CUDA", 4: "BT_ERR_NOCONV",
     5: "BT_ERR_TIMEOUT", 6: "BT_ERR_OOM", 7: "BT_ERR_UNSUPPORTED",
 }
-PREC = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3}
+PREC = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3, "bf16x3": 4}
 
 # Every symbol declared in include/bt.h, with (restype, argtypes).
 _vp = ctypes.c_void_p

@@ -224,7 +224,7 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
     set_error("bt_solve_ex: need a handle, device F and X, K >= 1");
     return BT_ERR_ARG;
   }
-  if (o.precision < 0 || o.precision > 3) {
+  if (o.precision < 0 || o.precision > 4) {
     set_error("bt_solve_ex: unknown precision");
     return BT_ERR_ARG;
   }

@@ -135,6 +135,7 @@ struct bt_handle_s {
   // Tensor-core factor copies [5][N][M][M] (Dinv, E, G, U, V) in BF16 / FP32.
   void* tc_fac_bf16 = nullptr;
   void* tc_fac_tf32 = nullptr;
+  void* tc_fac_bf16x3 = nullptr;  // [2][5][N][M][M]: rounded values and their remainders
 
   // Refinement buffers (grown on demand): residual panel, work panel,
   // series terms and the device-side refinement state.
@@ -202,6 +203,8 @@ struct TcBuffers {
 
 // Column tile of the tensor-core kernels for a precision and block size (0: unsupported).
 int tc_col_tile(int precision, int M);
+// Operand planes of a tensor-core precision (2 for the split BF16 precision).
+int tc_planes(int precision);
 // Builds the tensor-core factor copies for `precision` (once per handle).
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st);
 // One tensor-core stage-2 solve: r -> w (y, W, X~), then X (+)= solution.

@@ -58,19 +58,44 @@ __device__ __forceinline__ void block_add(double v, double* target) {
 __device__ __forceinline__ double stencil_res(const double* __restrict__ F, const double* __restrict__ X,
                                               const double* __restrict__ Cd, int64_t N, int M, int64_t K, int64_t j,
                                               int m, int64_t n, int first) {
+  // FP64 instructions are the scarce resource on this GPU (about 1/60 of the
+  // FP32 rate): five fused operations per entry, no separate products.
   const size_t MK = (size_t)M * K;
   const size_t e = j * MK + (size_t)m * K + n;
   double v = F[e];
   if (!first) {
     const double* cd = Cd + 3 * (j * M + m);
-    double cx = cd[1] * X[e];
-    if (m > 0) cx += cd[0] * X[e - K];
-    if (m + 1 < M) cx += cd[2] * X[e + K];
-    v -= cx;
+    v = fma(-cd[1], X[e], v);
+    if (m > 0) v = fma(-cd[0], X[e - K], v);
+    if (m + 1 < M) v = fma(-cd[2], X[e + K], v);
     if (j > 0) v += X[e - MK];
     if (j + 1 < N) v += X[e + MK];
   }
   return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Stores v at r[idx]; with two planes (sp = 2) the rounded value goes to plane 0
+// and the rounding remainder to plane 1 (r[idx + plane]).
+__device__ __forceinline__ void put_planes(__nv_bfloat16* r, size_t idx, size_t plane, int sp, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  r[idx] = hi;
+  if (sp == 2) r[idx + plane] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+__device__ __forceinline__ void put_planes(float* r, size_t idx, size_t plane, int sp, float v) {
+  if (sp == 2) {
+    const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+    r[idx] = hi;
+    r[idx + plane] = v - hi;
+  } else {
+    r[idx] = v;
+  }
 }
 
 // Row-major residual panel (leading dimension K): grid-stride over entries.
@@ -100,35 +125,38 @@ template <typename TR>
 __global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restrict__ F, const double* __restrict__ X,
                                                         const double* __restrict__ Cd, TR* __restrict__ r,
                                                         int64_t N, int M, int64_t K, int64_t Kp, int first,
-                                                        int pass, IrState* st) {
+                                                        int pass, int sp, IrState* st) {
+  const size_t plane = (size_t)N * Kp * M;
   if (st->done) return;
-  __shared__ double tile[32][33];
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   const int64_t tn = (Kp + 31) / 32, tm = (M + 31) / 32;
   const int64_t ntile = tn * tm * N;
   double acc = 0.0;
-  // grid-stride over 32 x 32 tiles; one partial sum per CTA
+  // grid-stride over 32 x 32 tiles; one partial sum per CTA.  The entry is
+  // rounded to FP32 once (the only FP64 conversion); the stored value and the
+  // squared norm are formed from the FP32 copy on the FP32 pipe.
+  __shared__ float ftile[32][33];
   for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
     const int64_t n0 = (q0 % tn) * 32;
     const int m0 = (int)((q0 / tn) % tm) * 32;
     const int64_t j = q0 / (tn * tm);
+    float part = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int m = m0 + ty + 8 * q;
       const int64_t n = n0 + tx;
-      double v = 0.0;
-      if (m < M && n < K) {
-        v = stencil_res(F, X, Cd, N, M, K, j, m, n, first);
-        acc += v * v;
-      }
-      tile[ty + 8 * q][tx] = v;
+      float v = 0.f;
+      if (m < M && n < K) v = __double2float_rn(stencil_res(F, X, Cd, N, M, K, j, m, n, first));
+      part = fmaf(v, v, part);
+      ftile[ty + 8 * q][tx] = v;
     }
+    acc += (double)part;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t n = n0 + ty + 8 * q;
       const int m = m0 + tx;
-      if (m < M && n < Kp) r[((size_t)j * Kp + n) * M + m] = to_lp<TR>(tile[tx][ty + 8 * q]);
+      if (m < M && n < Kp) put_planes(r, ((size_t)j * Kp + n) * M + m, plane, sp, ftile[tx][ty + 8 * q]);
     }
     __syncthreads();
   }
@@ -144,7 +172,7 @@ template <typename TR, int CW, bool TRANS>
 __global__ void k_resid_dense(const double* __restrict__ F, const double* __restrict__ X,
                               const double* __restrict__ A, const double* __restrict__ B,
                               const double* __restrict__ C, TR* __restrict__ r, int64_t N, int M, int64_t K,
-                              int64_t ldr, int pass, IrState* st) {
+                              int64_t ldr, int pass, int sp, IrState* st) {
   if (st->done) return;
   extern __shared__ double sm[];
   const int CG = blockDim.x / M, kt = CW * CG;
@@ -185,7 +213,9 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
       const bool in = col + c < K;
       if (in) part += acc[c] * acc[c];
       if (TRANS) {
-        if (col + c < ldr) r[((size_t)j * ldr + col + c) * M + m] = to_lp<TR>(in ? acc[c] : 0.0);
+        if (col + c < ldr)
+          put_planes(r, ((size_t)j * ldr + col + c) * M + m, (size_t)N * ldr * M, sp,
+                     in ? __double2float_rn(acc[c]) : 0.f);
       } else if (in) {
         r[j * (size_t)M * ldr + (size_t)m * ldr + col + c] = to_lp<TR>(acc[c]);
       }
@@ -240,14 +270,14 @@ bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
 // block-transposed (ld = Kp) for the tensor-core solve.
 template <typename TR>
 bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
-                          int first, int pass, IrState* st, cudaStream_t s) {
+                          int sp, int first, int pass, IrState* st, cudaStream_t s) {
   const int M = (int)h->M;
   ProfScope ps(h, s, "residual");
   if (first || h->stencil) {
     if (trans) {
       const int64_t ntile = ((Kp + 31) / 32) * ((M + 31) / 32) * h->N;
       const int blocks = (int)std::min<int64_t>(ntile, 152 * 8);
-      k_resid_stencil_t<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, st);
+      k_resid_stencil_t<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
     } else {
       const size_t n = (size_t)h->N * M * K;
       const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
@@ -264,12 +294,12 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
       if (smem > 48 * 1024)
         BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_resid_dense<TR, CW, true><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
-          F, X, h->A, h->B, h->C, r, h->N, M, K, Kp, pass, st);
+          F, X, h->A, h->B, h->C, r, h->N, M, K, Kp, pass, sp, st);
     } else {
       if (smem > 48 * 1024)
         BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_resid_dense<TR, CW, false><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
-          F, X, h->A, h->B, h->C, r, h->N, M, K, K, pass, st);
+          F, X, h->A, h->B, h->C, r, h->N, M, K, K, pass, 1, st);
     }
   }
   BT_CUDA(cudaGetLastError());
@@ -304,7 +334,8 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : 12;
   const double tol = o.tol > 0 ? o.tol : 1e-10;
   const int prec = o.precision;
-  const bool tcore = prec == BT_PREC_BF16 || prec == BT_PREC_TF32;
+  const bool tcore = prec == BT_PREC_BF16 || prec == BT_PREC_TF32 || prec == BT_PREC_BF16X3;
+  const int sp = tcore ? tc_planes(prec) : 1;
   const int M = (int)h->M;
   int64_t Kp = K;
   size_t eb = sizeof(float);
@@ -315,9 +346,9 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       return BT_ERR_UNSUPPORTED;
     }
     Kp = (K + nt - 1) / nt * nt;
-    eb = prec == BT_PREC_BF16 ? 2 : 4;
+    eb = prec == BT_PREC_TF32 ? 4 : 2;
   }
-  const size_t panel = (size_t)h->N * M * Kp * eb;
+  const size_t panel = (size_t)sp * h->N * M * Kp * eb;
   const size_t cbytes = (size_t)h->depth * h->S * M * Kp * sizeof(float);
   BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
@@ -331,14 +362,15 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   const double tol2 = tol * tol;
 
   auto residual = [&](int first, int pass) -> bt_status {
-    if (prec == BT_PREC_BF16)
-      return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, first,
-                                            pass, st, s);
-    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, first, pass, st, s);
+    if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
+      return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
+                                            first, pass, st, s);
+    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, pass, st, s);
   };
   auto inner = [&](int accumulate) -> bt_status {
     if (tcore) {
-      TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : h->tc_fac_tf32, h->lp_r, h->lp_d,
+      TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : prec == BT_PREC_TF32 ? h->tc_fac_tf32 : h->tc_fac_bf16x3,
+                   h->lp_r, h->lp_d,
                    reinterpret_cast<float*>(h->lp_c), Kp};
       return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, s);
     }

@@ -8,6 +8,12 @@
 // B operand of the MMA for both BF16 and TF32.  Factor blocks are row-major
 // M x M: the K-major A operand.  Both are moved by TMA with 128-byte swizzle.
 //
+// Split operands (SP = 2): every factor and panel value v is stored as two
+// planes hi = round(v), lo = round(v - hi), and each product is formed as
+// Ahi Bhi + Ahi Blo + Alo Bhi (three MMAs, FP32 accumulation), which carries
+// about twice the operand precision (BF16: ~2^-17 instead of 2^-9) and cuts
+// the number of refinement passes.
+//
 //   k_tc_sweep    eq. sub3 per (segment, column tile), step 2.1:
 //                 forward  y_i = Dinv_i r_i + E_i y_{i-1},
 //                 backward W_i = y_i + G_i W_{i+1}.
@@ -46,6 +52,11 @@ struct ET<__nv_bfloat16> {
   static constexpr CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   static __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
   static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+  // v = hi + lo with hi, lo representable
+  static __device__ __forceinline__ void split(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
 };
 template <>
 struct ET<float> {
@@ -53,6 +64,10 @@ struct ET<float> {
   static constexpr CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   static __device__ __forceinline__ float tof(float v) { return v; }
   static __device__ __forceinline__ float from(float v) { return v; }
+  static __device__ __forceinline__ void split(float v, float& hi, float& lo) {
+    hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);  // exactly a TF32 value
+    lo = v - hi;
+  }
 };
 
 __host__ __device__ constexpr int pow2ceil(int v) {
@@ -61,21 +76,24 @@ __host__ __device__ constexpr int pow2ceil(int v) {
   return p;
 }
 
-template <typename E, int M_, int NT_, int NA_>
+template <typename E, int M_, int NT_, int NA_, int SP_>
 struct Cfg {
-  static constexpr int M = M_, NT = NT_, NA = NA_;
+  static constexpr int M = M_, NT = NT_, NA = NA_, SP = SP_;
   static constexpr int eb = (int)sizeof(E);
   static constexpr int CE = 128 / eb;      // elements in one 128-byte swizzle row
   static constexpr int KS = 32 / eb;       // K of one MMA instruction
   static constexpr int NCH = M / CE;       // 128-byte chunks per block row / per tile row
-  static constexpr int SLICE = M * 128;    // one A slice: M rows x 128 bytes
+  static constexpr int SLICE = M * 128;    // one A slice of one plane: M rows x 128 bytes
+  static constexpr int SLOT = SP * SLICE;  // one ring slot: the slice of every plane
   static constexpr int TCH = NT * 128;     // one tile chunk: NT rows x 128 bytes
-  static constexpr int TILE = NCH * TCH;   // one NT x M panel tile
+  static constexpr int TILE = NCH * TCH;   // one NT x M panel tile of one plane
+  static constexpr int PT = SP * TILE;     // a panel tile with all its planes
   static constexpr int TMEM_COLS = pow2ceil(2 * NT);
   static constexpr uint32_t IDESC = instr_desc(ET<E>::fmt, 0, M, NT);
   static_assert(M == 64 || M == 128, "tensor-core path supports M = 64 and M = 128");
   static_assert(NT % 32 == 0 && NT <= 256, "column tile");
   static_assert(TCH % 1024 == 0, "swizzle atoms");
+  static_assert(SP == 1 || SP == 2, "one or two planes");
 };
 
 // Byte offset of element (n, m) inside a K-major 128B-swizzled NT x M tile.
@@ -85,6 +103,28 @@ __device__ __forceinline__ uint32_t kmaj_off(int n, int m) {
   const int c = m / C::CE;
   const int u = (m % C::CE) / per16;
   return (uint32_t)(c * C::TCH + n * 128 + ((u ^ (n & 7)) << 4) + (m % per16) * C::eb);
+}
+
+// Value (n, m) of a panel tile with all its planes.
+template <typename E, class C>
+__device__ __forceinline__ float tile_get(const uint8_t* tile, int n, int m) {
+  const uint32_t o = kmaj_off<C>(n, m);
+  float v = ET<E>::tof(*reinterpret_cast<const E*>(tile + o));
+  if (C::SP == 2) v += ET<E>::tof(*reinterpret_cast<const E*>(tile + C::TILE + o));
+  return v;
+}
+
+template <typename E, class C>
+__device__ __forceinline__ void tile_put(uint8_t* tile, int n, int m, float v) {
+  const uint32_t o = kmaj_off<C>(n, m);
+  if (C::SP == 2) {
+    E hi, lo;
+    ET<E>::split(v, hi, lo);
+    *reinterpret_cast<E*>(tile + o) = hi;
+    *reinterpret_cast<E*>(tile + C::TILE + o) = lo;
+  } else {
+    *reinterpret_cast<E*>(tile + o) = ET<E>::from(v);
+  }
 }
 
 // TMEM lane holding accumulator row `row` (cta_group::1): M = 128 uses all 128
@@ -147,31 +187,47 @@ __device__ __forceinline__ void init_bars(const Bars& b) {
   fence_mbar_init();
 }
 
-// Producer helper: one A slice into the ring (waits for the slot to drain).
+// Producer helper: one A slice (every plane) into the ring; waits for the slot.
+// fplane: tensor-map rows between factor planes.
 template <class C>
 __device__ __forceinline__ bool load_slice(uint8_t* sA, const Bars& b, uint32_t& ai, const CUtensorMap* tm, int x,
-                                           int y) {
+                                           int y, int fplane) {
   const uint32_t slot = ai % C::NA, use = ai / C::NA;
   if (use > 0 && !mbar_wait(&b.emptyA[slot], (use - 1) & 1)) return false;
-  mbar_arrive_expect_tx(&b.fullA[slot], C::SLICE);
-  tma_load_2d(sA + slot * C::SLICE, tm, x, y, &b.fullA[slot]);
+  mbar_arrive_expect_tx(&b.fullA[slot], C::SLOT);
+#pragma unroll
+  for (int p = 0; p < C::SP; ++p) tma_load_2d(sA + slot * C::SLOT + p * C::SLICE, tm, x, y + p * fplane, &b.fullA[slot]);
   ++ai;
   return true;
 }
 
-// Producer helper: one panel tile (NCH boxes) into the P ring.
+// Producer helper: one panel tile (every plane, NCH boxes each) into the P ring.
+// pplane: tensor-map rows between panel planes.
 template <class C>
-__device__ __forceinline__ bool load_tile(uint8_t* sP, const Bars& b, uint32_t& pi, const CUtensorMap* tm, int y) {
+__device__ __forceinline__ bool load_tile(uint8_t* sP, const Bars& b, uint32_t& pi, const CUtensorMap* tm, int y,
+                                          int pplane) {
   const uint32_t slot = pi % 2, use = pi / 2;
   if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
-  mbar_arrive_expect_tx(&b.fullP[slot], C::TILE);
-  for (int c = 0; c < C::NCH; ++c) tma_load_2d(sP + slot * C::TILE + c * C::TCH, tm, c * C::CE, y, &b.fullP[slot]);
+  mbar_arrive_expect_tx(&b.fullP[slot], C::PT);
+#pragma unroll
+  for (int p = 0; p < C::SP; ++p)
+    for (int c = 0; c < C::NCH; ++c)
+      tma_load_2d(sP + slot * C::PT + p * C::TILE + c * C::TCH, tm, c * C::CE, y + p * pplane, &b.fullP[slot]);
   ++pi;
   return true;
 }
 
+template <typename E>
+__device__ __forceinline__ void mma1(uint32_t d, uint64_t a, uint64_t bdesc, uint32_t idesc, bool acc) {
+  if (ET<E>::fmt == 1)
+    mma_f16(d, a, bdesc, idesc, acc ? 1u : 0u);
+  else
+    mma_tf32(d, a, bdesc, idesc, acc ? 1u : 0u);
+}
+
 // MMA helper: D (+)= A_block * B_tile over the M-long contraction, streaming
-// the block's NCH slices from the ring; frees each slice when consumed.
+// the block's NCH slices from the ring; frees each slot when consumed.  With
+// two planes: D += Ahi Bhi + Ahi Blo + Alo Bhi.
 template <typename E, class C>
 __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& ai, uint32_t dtmem, uint32_t btile,
                                           bool& first) {
@@ -179,16 +235,16 @@ __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& 
     const uint32_t slot = ai % C::NA, use = ai / C::NA;
     if (!mbar_wait(&b.fullA[slot], use & 1)) return false;
     tc_fence_after();
-    const uint32_t abase = smem_u32(sA + slot * C::SLICE);
+    const uint32_t ahi = smem_u32(sA + slot * C::SLOT);
 #pragma unroll
     for (int kq = 0; kq < C::CE / C::KS; ++kq) {
-      const uint64_t ad = smem_desc(abase + kq * 32, 16, 1024);
-      const uint64_t bd = smem_desc(btile + c * C::TCH + kq * 32, 16, 1024);
-      if (ET<E>::fmt == 1)
-        mma_f16(dtmem, ad, bd, C::IDESC, first ? 0u : 1u);
-      else
-        mma_tf32(dtmem, ad, bd, C::IDESC, first ? 0u : 1u);
+      const uint32_t boff = btile + c * C::TCH + kq * 32;
+      mma1<E>(dtmem, smem_desc(ahi + kq * 32, 16, 1024), smem_desc(boff, 16, 1024), C::IDESC, !first);
       first = false;
+      if (C::SP == 2) {
+        mma1<E>(dtmem, smem_desc(ahi + kq * 32, 16, 1024), smem_desc(boff + C::TILE, 16, 1024), C::IDESC, true);
+        mma1<E>(dtmem, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), smem_desc(boff, 16, 1024), C::IDESC, true);
+      }
     }
     mma_commit(&b.emptyA[slot]);
     ++ai;
@@ -209,7 +265,7 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[C::NT]) {
   }
 }
 
-// Factor block types in the combined low-precision factor array [5][N][M][M].
+// Factor block types in the combined low-precision factor array [SP][5][N][M][M].
 enum { FT_DINV = 0, FT_E = 1, FT_G = 2, FT_U = 3, FT_V = 4 };
 
 // ======================================================================
@@ -223,9 +279,9 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
-  uint8_t* sP = sA + C::NA * C::SLICE;
-  uint8_t* sY = sP + 2 * C::TILE;
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + 2 * C::TILE);
+  uint8_t* sP = sA + C::NA * C::SLOT;
+  uint8_t* sY = sP + 2 * C::PT;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + 2 * C::PT);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
 
@@ -235,6 +291,8 @@ __global__ void __launch_bounds__(192, 1)
   const int a = s * L + 1;       // first interior row
   const int nrow = L - 1;        // interior rows
   const int T = nrow >= 2 ? 2 * nrow - 1 : nrow;
+  const int fplane = 5 * N * C::M;  // tensor-map rows per factor plane
+  const int pplane = N * Kp;        // tensor-map rows per panel plane
 
   if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
@@ -258,13 +316,13 @@ __global__ void __launch_bounds__(192, 1)
         const int o = fwd ? t : nrow - 2 - (t - nrow);
         const int i = a + o;
         if (!fwd && t == nrow) ok = mbar_wait(&b.extra[0], 0);
-        if (ok) ok = load_tile<C>(sP, b, pi, fwd ? &tm_r : &tm_w, i * Kp + n0);
+        if (ok) ok = load_tile<C>(sP, b, pi, fwd ? &tm_r : &tm_w, i * Kp + n0, pplane);
         const int first_type = fwd ? FT_DINV : FT_G;
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane);
         if (fwd && t > 0)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane);
       }
       if (!ok) atomicExch(status, 1);
       // no copy may still be landing when the CTA exits
@@ -281,7 +339,6 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       uint32_t ai = 0, pi = 0;
       bool ok = true;
-      int issued = 0;
       for (int t = 0; t < T && ok; ++t) {
         const bool fwd = t < nrow;
         const int bsel = t & 1;
@@ -294,16 +351,16 @@ __global__ void __launch_bounds__(192, 1)
           pslot = pi % 2;
           ok = mbar_wait(&b.fullP[pslot], (pi / 2) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::TILE), first);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::PT), first);
           if (ok && t > 0) {
             ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
             tc_fence_after();
-            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::TILE), first);
+            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first);
           }
         } else if (ok) {
           ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::TILE), first);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first);
         }
         if (ok) {
           mma_commit(&b.mdone[bsel]);
@@ -311,7 +368,6 @@ __global__ void __launch_bounds__(192, 1)
             mma_commit(&b.emptyP[pslot]);
             ++pi;
           }
-          ++issued;
         }
       }
       if (!ok) atomicExch(status, 2);
@@ -351,9 +407,9 @@ __global__ void __launch_bounds__(192, 1)
         if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
         ok = __all_sync(0xffffffffu, ok);
         if (ok && has) {
-          const uint8_t* tile = sP + ps * C::TILE;
+          const uint8_t* tile = sP + ps * C::PT;
 #pragma unroll 8
-          for (int n = 0; n < C::NT; ++n) v[n] += ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
+          for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
         }
         named_bar_sync(1, 128);
         if (ok && leader) mbar_arrive(&b.emptyP[ps]);
@@ -361,16 +417,18 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (leader) tma_store_wait_read<1>();
       named_bar_sync(1, 128);
-      uint8_t* ybuf = sY + bsel * C::TILE;
+      uint8_t* ybuf = sY + bsel * C::PT;
       if (ok && has) {
 #pragma unroll 8
-        for (int n = 0; n < C::NT; ++n) *reinterpret_cast<E*>(ybuf + kmaj_off<C>(n, row)) = ET<E>::from(v[n]);
+        for (int n = 0; n < C::NT; ++n) tile_put<E, C>(ybuf, n, row, v[n]);
       }
       fence_proxy_async_smem();
       named_bar_sync(1, 128);
       if (leader && ok) {
         mbar_arrive(&b.yrdy[bsel]);
-        for (int c = 0; c < C::NCH; ++c) tma_store_2d(&tm_w, c * C::CE, i * Kp + n0, ybuf + c * C::TCH);
+        for (int p = 0; p < C::SP; ++p)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_store_2d(&tm_w, c * C::CE, p * pplane + i * Kp + n0, ybuf + p * C::TILE + c * C::TCH);
         tma_store_commit();
         if (t == nrow - 1) {
           tma_store_wait<0>();
@@ -413,14 +471,14 @@ __global__ void __launch_bounds__(192, 1)
   if (flag_set(done)) return;
   constexpr int XB = C::NT / 16;                 // X boxes per tile
   constexpr int XBYTES = XT ? XB * C::M * 128 : 0;
-  constexpr int PST = C::TILE + XBYTES;          // one P stage: W tile (+ X tile)
+  constexpr int PST = C::PT + XBYTES;            // one P stage: W tile planes (+ X tile)
   constexpr int SLD = C::NT + 1;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
-  uint8_t* sP = sA + C::NA * C::SLICE;
-  uint8_t* sB = sP + 2 * PST;  // X~_s, X~_{s+1}
-  float* stage = reinterpret_cast<float*>(sB + 2 * C::TILE);
+  uint8_t* sP = sA + C::NA * C::SLOT;
+  uint8_t* sB = sP + 2 * PST;  // X~_s, X~_{s+1} (all planes each)
+  float* stage = reinterpret_cast<float*>(sB + 2 * C::PT);
   uint64_t* barmem = reinterpret_cast<uint64_t*>(stage + (XT ? 0 : C::M * SLD) + 64);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
@@ -434,6 +492,8 @@ __global__ void __launch_bounds__(192, 1)
   const int T = max(0, r1 - r0);
   const int pre = (XT && blockIdx.z == 0) ? 1 : 0;  // interface row through the P ring
   const bool do_iface = blockIdx.z == 0;
+  const int fplane = 5 * N * C::M;
+  const int pplane = N * Kp;
   // X boxes that start inside the matrix (later ones are skipped, not clipped)
   const int xboxes = XT ? max(0, min(XB, (K - n0 + 15) / 16)) : 0;
 
@@ -454,23 +514,26 @@ __global__ void __launch_bounds__(192, 1)
       if (XT) prefetch_tmap(&tm_x);
       bool ok = true;
       // X~_s and X~_{s+1}: the two B operands, loaded once
-      mbar_arrive_expect_tx(&b.extra[0], (has_next ? 2 : 1) * C::TILE);
-      for (int c = 0; c < C::NCH; ++c)
-        tma_load_2d(sB + c * C::TCH, &tm_w, c * C::CE, (s * L) * Kp + n0, &b.extra[0]);
-      if (has_next)
-        for (int c = 0; c < C::NCH; ++c)
-          tma_load_2d(sB + C::TILE + c * C::TCH, &tm_w, c * C::CE, ((s + 1) * L) * Kp + n0, &b.extra[0]);
+      mbar_arrive_expect_tx(&b.extra[0], (has_next ? 2 : 1) * C::PT);
+      for (int q = 0; q < (has_next ? 2 : 1); ++q)
+        for (int p = 0; p < C::SP; ++p)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_load_2d(sB + q * C::PT + p * C::TILE + c * C::TCH, &tm_w, c * C::CE,
+                        p * pplane + ((s + q) * L) * Kp + n0, &b.extra[0]);
       uint32_t ai = 0, pi = 0;
       auto load_stage = [&](int irow, bool with_w) -> bool {
         const uint32_t slot = pi % 2, use = pi / 2;
         if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
         const int xload = (XT && accumulate) ? xboxes : 0;
-        mbar_arrive_expect_tx(&b.fullP[slot], (with_w ? C::TILE : 0) + xload * C::M * 128);
+        mbar_arrive_expect_tx(&b.fullP[slot], (with_w ? C::PT : 0) + xload * C::M * 128);
         uint8_t* st = sP + slot * PST;
         if (with_w)
-          for (int c = 0; c < C::NCH; ++c) tma_load_2d(st + c * C::TCH, &tm_w, c * C::CE, irow * Kp + n0, &b.fullP[slot]);
+          for (int p = 0; p < C::SP; ++p)
+            for (int c = 0; c < C::NCH; ++c)
+              tma_load_2d(st + p * C::TILE + c * C::TCH, &tm_w, c * C::CE, p * pplane + irow * Kp + n0,
+                          &b.fullP[slot]);
         for (int q = 0; q < xload; ++q)
-          tma_load_2d(st + C::TILE + q * C::M * 128, &tm_x, n0 + 16 * q, irow * C::M, &b.fullP[slot]);
+          tma_load_2d(st + C::PT + q * C::M * 128, &tm_x, n0 + 16 * q, irow * C::M, &b.fullP[slot]);
         ++pi;
         return true;
       };
@@ -479,10 +542,10 @@ __global__ void __launch_bounds__(192, 1)
         const int i = r0 + t;
         ok = load_stage(i, true);
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane);
         if (has_next)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane);
       }
       if (!ok) atomicExch(status, 4);
       mbar_wait(&b.extra[0], 0);
@@ -507,7 +570,7 @@ __global__ void __launch_bounds__(192, 1)
         tc_fence_after();
         bool first = true;
         if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first);
-        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::TILE), first);
+        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::PT), first);
         if (ok) mma_commit(&b.mdone[bsel]);
       }
       if (!ok) atomicExch(status, 5);
@@ -527,7 +590,7 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t pe = 0;
     // X tile of P stage `ps` (XT): this thread's row += v[] (or = v[]), then TMA store
     auto xt_update = [&](uint32_t ps, const float (&v)[C::NT], int irow) {
-      uint8_t* xt = sP + ps * PST + C::TILE;
+      uint8_t* xt = sP + ps * PST + C::PT;
       if (ok && has) {
 #pragma unroll 4
         for (int n = 0; n < C::NT; n += 2) {
@@ -564,7 +627,7 @@ __global__ void __launch_bounds__(192, 1)
       // interface row k_s: X_K (+)= X~_s
       float v[C::NT];
 #pragma unroll
-      for (int n = 0; n < C::NT; ++n) v[n] = (ok && has) ? ET<E>::tof(*reinterpret_cast<const E*>(sB + kmaj_off<C>(n, row))) : 0.f;
+      for (int n = 0; n < C::NT; ++n) v[n] = (ok && has) ? tile_get<E, C>(sB, n, row) : 0.f;
       if constexpr (XT) {
         const uint32_t ps = pe % 2;
         if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
@@ -602,7 +665,7 @@ __global__ void __launch_bounds__(192, 1)
       if (ok && has) {
         const uint8_t* tile = sP + ps * PST;
 #pragma unroll 8
-        for (int n = 0; n < C::NT; ++n) v[n] += ET<E>::tof(*reinterpret_cast<const E*>(tile + kmaj_off<C>(n, row)));
+        for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
       }
       if constexpr (XT) {
         xt_update(ps, v, i);
@@ -627,15 +690,18 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ======================================================================
-// Step 2.2 on the CUDA cores (FP32), block-transposed panels of type E
+// Step 2.2 on the CUDA cores (FP32), block-transposed panels of type E with
+// SP planes (plane stride `ps` elements)
 // ======================================================================
-template <typename E>
-__device__ __forceinline__ const E* prow(const E* base, int j, int Kp, int M) {
-  return base + (size_t)j * Kp * M;
+template <typename E, int SP>
+__device__ __forceinline__ float pget(const E* base, size_t idx, size_t ps) {
+  float v = ET<E>::tof(base[idx]);
+  if (SP == 2) v += ET<E>::tof(base[idx + ps]);
+  return v;
 }
 
 // F~_s = r_K + A_K W_{K-1} + B_K W_{K+1};  c[l][s] = R[l][s] F~_s  (FP32, c row-major [M][Kp])
-template <typename E, int CW>
+template <typename E, int SP, int CW>
 __global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, const float* __restrict__ AK,
                            const float* __restrict__ BK, const float* __restrict__ R, const int* __restrict__ mid_level,
                            float* __restrict__ cbuf, int N, int M, int S, int L, int Kp, const int* done) {
@@ -645,15 +711,17 @@ __global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, con
   const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
   const int s = blockIdx.x, col0 = blockIdx.y * kt;
   const int Kr = s * L;
+  const size_t ps = (size_t)N * Kp * M;
   float* pa = fsm;
   float* pb = fsm + M * kt;
   float* pt = fsm + 2 * M * kt;
   const bool hasL = s > 0 && L > 1, hasR = Kr + 1 < N && L > 1;
   for (int e = t; e < M * kt; e += blockDim.x) {
     const int mm = e % M, n = e / M;  // coalesced along m
-    pa[mm * kt + n] = hasL ? ET<E>::tof(prow(w, Kr - 1, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
-    pb[mm * kt + n] = hasR ? ET<E>::tof(prow(w, Kr + 1, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
-    pt[mm * kt + n] = ET<E>::tof(prow(r, Kr, Kp, M)[(size_t)(col0 + n) * M + mm]);
+    const size_t off = (size_t)(col0 + n) * M + mm;
+    pa[mm * kt + n] = hasL ? pget<E, SP>(w, (size_t)(Kr - 1) * Kp * M + off, ps) : 0.f;
+    pb[mm * kt + n] = hasR ? pget<E, SP>(w, (size_t)(Kr + 1) * Kp * M + off, ps) : 0.f;
+    pt[mm * kt + n] = pget<E, SP>(r, (size_t)Kr * Kp * M + off, ps);
   }
   __syncthreads();
   const size_t MM = (size_t)M * M;
@@ -688,12 +756,12 @@ __global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, con
   }
 }
 
-// X~_m = sum_{j in [l, r]} c[level][j] + HL_m X~_{l-1} + HR_m X~_{r+1}, written as E
-// into the work panel's interface row k_m.
-template <typename E, int CW>
+// X~_m = sum_{j in [l, r]} c[level][j] + HL_m X~_{l-1} + HR_m X~_{r+1}, written
+// into the work panel's interface row k_m (all planes).
+template <typename E, int SP, int CW>
 __global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf, const float* __restrict__ HL,
                                const float* __restrict__ HR, const int* __restrict__ nodes, int lev, int node_off,
-                               int M, int S, int L, int Kp, const int* done) {
+                               int N, int M, int S, int L, int Kp, const int* done) {
   if (flag_set(done)) return;
   extern __shared__ float fsm[];
   const int CG = blockDim.x / M, kt = CW * CG;
@@ -701,13 +769,15 @@ __global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf
   const int q = node_off + blockIdx.x;
   const int l = nodes[3 * q], r = nodes[3 * q + 1], mid = nodes[3 * q + 2];
   const int col0 = blockIdx.y * kt;
+  const size_t ps = (size_t)N * Kp * M;
   float* pl = fsm;
   float* pr = fsm + M * kt;
   const bool hl = l > 0, hr = r < S - 1;
   for (int e = t; e < M * kt; e += blockDim.x) {
     const int mm = e % M, n = e / M;
-    pl[mm * kt + n] = hl ? ET<E>::tof(prow(w, (l - 1) * L, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
-    pr[mm * kt + n] = hr ? ET<E>::tof(prow(w, (r + 1) * L, Kp, M)[(size_t)(col0 + n) * M + mm]) : 0.f;
+    const size_t off = (size_t)(col0 + n) * M + mm;
+    pl[mm * kt + n] = hl ? pget<E, SP>(w, (size_t)(l - 1) * L * Kp * M + off, ps) : 0.f;
+    pr[mm * kt + n] = hr ? pget<E, SP>(w, (size_t)(r + 1) * L * Kp * M + off, ps) : 0.f;
   }
   __syncthreads();
   const size_t MM = (size_t)M * M;
@@ -734,7 +804,16 @@ __global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf
   E* out = w + (size_t)mid * L * Kp * M;
   for (int e = t; e < M * kt; e += blockDim.x) {
     const int mm = e % M, n = e / M;
-    out[(size_t)(col0 + n) * M + mm] = ET<E>::from(pl[mm * kt + n]);
+    const size_t off = (size_t)(col0 + n) * M + mm;
+    const float v = pl[mm * kt + n];
+    if (SP == 2) {
+      E hi, lo;
+      ET<E>::split(v, hi, lo);
+      out[off] = hi;
+      out[off + ps] = lo;
+    } else {
+      out[off] = ET<E>::from(v);
+    }
   }
 }
 
@@ -778,7 +857,9 @@ bt_status make_map_f64(CUtensorMap* m, const void* base, uint64_t inner, uint64_
   return make_map(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, inner, outer, box_inner, box_outer);
 }
 
-template <typename E>
+// [SP][5][N][M][M] rounded factor copies (Dinv, E, G, U, V); plane 1 holds the
+// rounding remainder of plane 0.
+template <typename E, int SP>
 __global__ void k_cast_factors(const double* __restrict__ D, const double* __restrict__ Ee,
                                const double* __restrict__ G, const double* __restrict__ U,
                                const double* __restrict__ V, E* __restrict__ out, size_t nb) {
@@ -786,31 +867,44 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const size_t w = e / nb, o = e % nb;
     const double* src = w == 0 ? D : w == 1 ? Ee : w == 2 ? G : w == 3 ? U : V;
-    out[e] = ET<E>::from((float)src[o]);
+    const double x = src[o];
+    if (SP == 2) {
+      E hi, lo;
+      // remainder taken against the FP64 value, then rounded
+      ET<E>::split((float)x, hi, lo);
+      const double r = x - (double)ET<E>::tof(hi);
+      lo = ET<E>::from((float)r);
+      out[e] = hi;
+      out[e + n] = lo;
+    } else {
+      out[e] = ET<E>::from((float)x);
+    }
   }
 }
 
 template <class C>
 size_t sweep_smem() {
-  return 1024 + C::NA * C::SLICE + 4 * C::TILE + kBars(C::NA) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + 4 * C::PT + kBars(C::NA) * 8 + 16;
 }
 template <class C, bool XT>
 size_t correct_smem() {
   const size_t xbytes = XT ? (size_t)(C::NT / 16) * C::M * 128 : 0;
-  return 1024 + C::NA * C::SLICE + 2 * (C::TILE + xbytes) + 2 * C::TILE +
-         (XT ? 0 : (size_t)C::M * (C::NT + 1) * 4) + 256 + kBars(C::NA) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + 2 * (C::PT + xbytes) + 2 * C::PT + (XT ? 0 : (size_t)C::M * (C::NT + 1) * 4) +
+         256 + kBars(C::NA) * 8 + 16;
 }
 
 // CS: configuration of the sweep kernel, CC: of the correction kernel.
 template <typename E, class CS, class CC>
 bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int accumulate, const int* done,
                  int* status, cudaStream_t st) {
+  constexpr int SP = CS::SP;
+  static_assert(CS::SP == CC::SP, "one plane count per precision");
   const int M = CS::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
   CUtensorMap tm_fac, tm_r, tm_w, tm_wc, tm_x;
-  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)5 * N * M, CS::CE, M));
-  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)N * Kp, CS::CE, CS::NT));
-  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)N * Kp, CS::CE, CS::NT));
-  BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)N * Kp, CC::CE, CC::NT));
+  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M));
+  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
+  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
+  BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CC::CE, CC::NT));
   // FP64 solution tiles by TMA need an even leading dimension and a 16-byte aligned base
   const bool xt = (K % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   if (xt) {
@@ -836,19 +930,19 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     const int nt2 = Kp / kt;
     const LowFactors& f = h->f32;
     const size_t sm3 = 3 * (size_t)M * kt * sizeof(float);
-    BT_CUDA(cudaFuncSetAttribute(k_tc_iface<E, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    BT_CUDA(cudaFuncSetAttribute(k_tc_dichotomy<E, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    BT_CUDA(cudaFuncSetAttribute(k_tc_iface<E, SP, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    BT_CUDA(cudaFuncSetAttribute(k_tc_dichotomy<E, SP, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     {
       ProfScope ps(h, st, "tc_iface");
-      k_tc_iface<E, CW><<<dim3(S, nt2), M * CG, sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level, tb.c, N, M, S, L,
-                                                           Kp, done);
+      k_tc_iface<E, SP, CW><<<dim3(S, nt2), M * CG, sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level, tb.c, N, M, S,
+                                                               L, Kp, done);
     }
     BT_CUDA(cudaGetLastError());
     for (int lev = 0; lev < h->depth; ++lev) {
       const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
       ProfScope ps(h, st, "tc_dichotomy");
-      k_tc_dichotomy<E, CW><<<dim3(nn, nt2), M * CG, 2 * (size_t)M * kt * sizeof(float), st>>>(
-          w, tb.c, f.HL, f.HR, h->d_nodes, lev, n0, M, S, L, Kp, done);
+      k_tc_dichotomy<E, SP, CW><<<dim3(nn, nt2), M * CG, 2 * (size_t)M * kt * sizeof(float), st>>>(
+          w, tb.c, f.HL, f.HR, h->d_nodes, lev, n0, N, M, S, L, Kp, done);
     }
     BT_CUDA(cudaGetLastError());
   }
@@ -876,15 +970,19 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   return BT_OK;
 }
 
-// sweep / correction configurations per (operand type, block size)
-using SwB128 = Cfg<__nv_bfloat16, 128, 64, 6>;
-using CoB128 = Cfg<__nv_bfloat16, 128, 32, 4>;
-using SwT128 = Cfg<float, 128, 32, 6>;
-using CoT128 = Cfg<float, 128, 32, 4>;
-using SwB64 = Cfg<__nv_bfloat16, 64, 128, 8>;
-using CoB64 = Cfg<__nv_bfloat16, 64, 64, 4>;
-using SwT64 = Cfg<float, 64, 64, 8>;
-using CoT64 = Cfg<float, 64, 64, 4>;
+// sweep / correction configurations per (operand type, block size, planes)
+using SwB128 = Cfg<__nv_bfloat16, 128, 64, 6, 1>;
+using CoB128 = Cfg<__nv_bfloat16, 128, 32, 4, 1>;
+using SwT128 = Cfg<float, 128, 32, 6, 1>;
+using CoT128 = Cfg<float, 128, 32, 4, 1>;
+using SwB64 = Cfg<__nv_bfloat16, 64, 128, 8, 1>;
+using CoB64 = Cfg<__nv_bfloat16, 64, 64, 4, 1>;
+using SwT64 = Cfg<float, 64, 64, 8, 1>;
+using CoT64 = Cfg<float, 64, 64, 4, 1>;
+using SwX128 = Cfg<__nv_bfloat16, 128, 32, 4, 2>;
+using CoX128 = Cfg<__nv_bfloat16, 128, 32, 3, 2>;
+using SwX64 = Cfg<__nv_bfloat16, 64, 64, 8, 2>;
+using CoX64 = Cfg<__nv_bfloat16, 64, 64, 4, 2>;
 
 }  // namespace
 
@@ -894,17 +992,24 @@ int tc_col_tile(int precision, int M) {
   return (M == 128 || M == 64) ? 128 : 0;
 }
 
+int tc_planes(int precision) { return precision == BT_PREC_BF16X3 ? 2 : 1; }
+
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
-  void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : &h->tc_fac_tf32;
+  void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : precision == BT_PREC_TF32 ? &h->tc_fac_tf32 : &h->tc_fac_bf16x3;
   if (*slot) return BT_OK;
   const size_t nb = (size_t)h->N * h->M * h->M;
-  const size_t eb = precision == BT_PREC_BF16 ? 2 : 4;
-  BT_TRY(h->arena.alloc(slot, 5 * nb * eb));
+  const int sp = tc_planes(precision);
+  const size_t eb = precision == BT_PREC_TF32 ? 4 : 2;
+  BT_TRY(h->arena.alloc(slot, (size_t)sp * 5 * nb * eb));
   if (precision == BT_PREC_BF16)
-    k_cast_factors<__nv_bfloat16><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
-                                                        reinterpret_cast<__nv_bfloat16*>(*slot), nb);
+    k_cast_factors<__nv_bfloat16, 1><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
+                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb);
+  else if (precision == BT_PREC_TF32)
+    k_cast_factors<float, 1><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V, reinterpret_cast<float*>(*slot),
+                                                   nb);
   else
-    k_cast_factors<float><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V, reinterpret_cast<float*>(*slot), nb);
+    k_cast_factors<__nv_bfloat16, 2><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
+                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb);
   BT_CUDA(cudaGetLastError());
   return BT_OK;
 }
@@ -915,9 +1020,12 @@ bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K
   if (precision == BT_PREC_BF16) {
     if (M == 128) return run_tc<__nv_bfloat16, SwB128, CoB128>(h, tb, K, X, accumulate, done, status, st);
     if (M == 64) return run_tc<__nv_bfloat16, SwB64, CoB64>(h, tb, K, X, accumulate, done, status, st);
-  } else {
+  } else if (precision == BT_PREC_TF32) {
     if (M == 128) return run_tc<float, SwT128, CoT128>(h, tb, K, X, accumulate, done, status, st);
     if (M == 64) return run_tc<float, SwT64, CoT64>(h, tb, K, X, accumulate, done, status, st);
+  } else if (precision == BT_PREC_BF16X3) {
+    if (M == 128) return run_tc<__nv_bfloat16, SwX128, CoX128>(h, tb, K, X, accumulate, done, status, st);
+    if (M == 64) return run_tc<__nv_bfloat16, SwX64, CoX64>(h, tb, K, X, accumulate, done, status, st);
   }
   set_error("the tensor-core solve supports block sizes M = 64 and M = 128");
   return BT_ERR_UNSUPPORTED;

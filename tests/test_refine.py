@@ -91,7 +91,7 @@ def test_refined_zero_rhs(bt):
 # ---------------------------------------------------------------------------
 # tensor-core inner solve (tcgen05, BF16 / TF32 operands, FP32 accumulation)
 # ---------------------------------------------------------------------------
-TC = ["bf16", "tf32"]
+TC = ["bf16", "tf32", "bf16x3"]
 
 
 @pytest.mark.parametrize("prec", TC)
@@ -146,3 +146,17 @@ def test_tc_unsupported_block_size(bt):
         with pytest.raises(bt.BtError) as ei:
             fac.solve(_t(F), precision="bf16")
         assert ei.value.name == "BT_ERR_UNSUPPORTED"
+
+
+def test_split_precision_needs_fewer_passes(bt):
+    # Two-term BF16 operands carry ~2^-17 relative precision: the first solve is
+    # far more accurate and refinement needs fewer passes than plain BF16.
+    N, M, K, S = 64, 128, 64, 8
+    A, B, C = gen.acoustic_system(N, M)
+    F = gen.acoustic_rhs(N, M, K, seed=9)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        _, i1 = fac.solve(_t(F), precision="bf16", tol=1e-12, return_info=True)
+        X3, i3 = fac.solve(_t(F), precision="bf16x3", tol=1e-12, return_info=True)
+    assert i3["rel_res0"] < 1e-2 * i1["rel_res0"], (i1, i3)
+    assert i3["iters"] < i1["iters"], (i1, i3)
+    assert oracle.rel_err(X3.cpu().numpy(), oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
