@@ -295,7 +295,13 @@ def main():
     ap.add_argument("--precision", choices=["f64", "f32", "tf32", "bf16", "bf16x3"], default="f64")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=N,
+                    help="block rows N (smaller values only for profiler captures; the bench workload is 4096)")
+    ap.add_argument("--segments", type=int, default=S, help="segments S (default 64)")
     args = ap.parse_args()
+    global WORKLOAD
+    globals()["N"], globals()["S"] = args.rows, args.segments
+    WORKLOAD = f"acoustic PML operator N={args.rows} M={M} K={K} S={args.segments} (tridiag C, A=B=I)"
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
