@@ -87,7 +87,7 @@ static void destroy_handle(bt_handle_s* h) {
   h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
-  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->ir_state, h->adj_lam})
+  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam})
     if (q) cudaFree(q);
   cudaSetDevice(prev);
   delete h;

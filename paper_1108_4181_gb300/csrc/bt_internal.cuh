@@ -142,7 +142,8 @@ struct bt_handle_s {
   void* lp_r = nullptr;
   void* lp_d = nullptr;
   void* lp_c = nullptr;
-  size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0;
+  void* lp_x = nullptr;  // FP32 correction panel of the tensor-core solve
+  size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0, lp_x_bytes = 0;
   void* ir_state = nullptr;
 
   bt::Profiler prof;
@@ -198,6 +199,7 @@ struct TcBuffers {
   void* r;
   void* w;
   float* c;
+  float* d;  // FP32 correction panel, block-transposed like w
   int64_t Kp;
 };
 

@@ -353,6 +353,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
   BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));
+  if (tcore) BT_TRY(grow(&h->lp_x, &h->lp_x_bytes, (size_t)h->N * M * Kp * sizeof(float), s));
   if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
   BT_TRY(make_f32_factors(h, s));
   if (tcore) BT_TRY(make_tc_factors(h, prec, s));
@@ -370,8 +371,8 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   auto inner = [&](int accumulate) -> bt_status {
     if (tcore) {
       TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : prec == BT_PREC_TF32 ? h->tc_fac_tf32 : h->tc_fac_bf16x3,
-                   h->lp_r, h->lp_d,
-                   reinterpret_cast<float*>(h->lp_c), Kp};
+                   h->lp_r, h->lp_d, reinterpret_cast<float*>(h->lp_c),
+                   reinterpret_cast<float*>(h->lp_x), Kp};
       return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, s);
     }
     return solve_simt_f32(h, reinterpret_cast<float*>(h->lp_r), K, reinterpret_cast<float*>(h->lp_d),

@@ -24,8 +24,9 @@
 //                 next row's MMA start while the previous one is drained.
 //   k_tc_iface / k_tc_dichotomy   step 2.2 on the CUDA cores in FP32 (a few
 //                 per cent of the flops: S (2 + depth) block products).
-//   k_tc_correct  eq. superposition, step 2.3: X_i (+)= W_i + U_i X~_s +
-//                 V_i X~_{s+1} with the FP64 solution updated in place.
+//   k_tc_correct  eq. superposition, step 2.3: d_i = W_i + U_i X~_s +
+//                 V_i X~_{s+1} into an FP32 correction panel (TMA stores);
+//   k_x_update    X (+)= d into the caller's FP64 solution.
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(192, 1)
         ok = __all_sync(0xffffffffu, ok);
         if (ok && has) {
           const uint8_t* tile = sP + ps * C::PT;
-#pragma unroll 8
+#pragma unroll
           for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
         }
         named_bar_sync(1, 128);
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(192, 1)
       named_bar_sync(1, 128);
       uint8_t* ybuf = sY + bsel * C::PT;
       if (ok && has) {
-#pragma unroll 8
+#pragma unroll
         for (int n = 0; n < C::NT; ++n) tile_put<E, C>(ybuf, n, row, v[n]);
       }
       fence_proxy_async_smem();
@@ -447,39 +448,28 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ======================================================================
-// Correction kernel: X_i (+)= W_i + U_i X~_s + V_i X~_{s+1}
-//
-// The FP64 solution tile of every row is moved by TMA (XT = true: X has an
-// even leading dimension and a 16-byte aligned base): the producer loads the
-// W_i tile and the X_i tile into one stage of the P ring, the epilogue adds
-// the accumulator and W_i into the X tile in shared memory and stores it back
-// with TMA, so the FP64 read-modify-write streams asynchronously.  With
-// XT = false the epilogue updates X with plain coalesced loads and stores.
-// Chunk 0 of every segment also updates the interface row: X_K (+)= X~_s.
+// Correction kernel, eq. superposition (step 2.3), interior rows:
+//   d_i = W_i + U_i X~_s + V_i X~_{s+1}
+// written as FP32 into the block-transposed correction panel D by TMA stores
+// (no FP64 work on this kernel's critical path); chunk 0 of every segment
+// also writes d_{k_s} = X~_s.  The FP64 solution is updated afterwards by
+// k_x_update (X (+)= d), a streaming kernel bound by the FP64 pipe.
 // ======================================================================
-template <class C>
-__device__ __forceinline__ uint32_t xt_off(int m, int n) {
-  // X tile: NT/16 boxes of [M rows][16 doubles], 128-byte swizzle
-  return (uint32_t)((n >> 4) * (C::M * 128) + m * 128 + ((((n & 15) >> 1) ^ (m & 7)) << 4) + (n & 1) * 8);
-}
-
-template <typename E, class C, bool XT>
+template <typename E, class C>
 __global__ void __launch_bounds__(192, 1)
     k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
-                 const __grid_constant__ CUtensorMap tm_x, int N, int L, int S, int Kp, int K, int rows_per_cta,
-                 double* __restrict__ X, int accumulate, const int* done, int* status) {
+                 const __grid_constant__ CUtensorMap tm_d, int N, int L, int S, int Kp, int rows_per_cta,
+                 const int* done, int* status) {
   if (flag_set(done)) return;
-  constexpr int XB = C::NT / 16;                 // X boxes per tile
-  constexpr int XBYTES = XT ? XB * C::M * 128 : 0;
-  constexpr int PST = C::PT + XBYTES;            // one P stage: W tile planes (+ X tile)
-  constexpr int SLD = C::NT + 1;
+  using CF = Cfg<float, C::M, C::NT, 1, 1>;      // layout of one FP32 d tile
+  constexpr int DT = CF::TILE;                    // bytes of one d tile
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLOT;
-  uint8_t* sB = sP + 2 * PST;  // X~_s, X~_{s+1} (all planes each)
-  float* stage = reinterpret_cast<float*>(sB + 2 * C::PT);
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(stage + (XT ? 0 : C::M * SLD) + 64);
+  uint8_t* sB = sP + 2 * C::PT;  // X~_s, X~_{s+1} (all planes each)
+  uint8_t* sD = sB + 2 * C::PT;  // two FP32 d tiles
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sD + 2 * DT);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
 
@@ -490,12 +480,9 @@ __global__ void __launch_bounds__(192, 1)
   const int r0 = s * L + 1 + blockIdx.z * rows_per_cta;
   const int r1 = min(r0 + rows_per_cta, s * L + L);
   const int T = max(0, r1 - r0);
-  const int pre = (XT && blockIdx.z == 0) ? 1 : 0;  // interface row through the P ring
   const bool do_iface = blockIdx.z == 0;
   const int fplane = 5 * N * C::M;
   const int pplane = N * Kp;
-  // X boxes that start inside the matrix (later ones are skipped, not clipped)
-  const int xboxes = XT ? max(0, min(XB, (K - n0 + 15) / 16)) : 0;
 
   if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
@@ -511,7 +498,7 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       prefetch_tmap(&tm_fac);
       prefetch_tmap(&tm_w);
-      if (XT) prefetch_tmap(&tm_x);
+      prefetch_tmap(&tm_d);
       bool ok = true;
       // X~_s and X~_{s+1}: the two B operands, loaded once
       mbar_arrive_expect_tx(&b.extra[0], (has_next ? 2 : 1) * C::PT);
@@ -521,26 +508,9 @@ __global__ void __launch_bounds__(192, 1)
             tma_load_2d(sB + q * C::PT + p * C::TILE + c * C::TCH, &tm_w, c * C::CE,
                         p * pplane + ((s + q) * L) * Kp + n0, &b.extra[0]);
       uint32_t ai = 0, pi = 0;
-      auto load_stage = [&](int irow, bool with_w) -> bool {
-        const uint32_t slot = pi % 2, use = pi / 2;
-        if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
-        const int xload = (XT && accumulate) ? xboxes : 0;
-        mbar_arrive_expect_tx(&b.fullP[slot], (with_w ? C::PT : 0) + xload * C::M * 128);
-        uint8_t* st = sP + slot * PST;
-        if (with_w)
-          for (int p = 0; p < C::SP; ++p)
-            for (int c = 0; c < C::NCH; ++c)
-              tma_load_2d(st + p * C::TILE + c * C::TCH, &tm_w, c * C::CE, p * pplane + irow * Kp + n0,
-                          &b.fullP[slot]);
-        for (int q = 0; q < xload; ++q)
-          tma_load_2d(st + C::PT + q * C::M * 128, &tm_x, n0 + 16 * q, irow * C::M, &b.fullP[slot]);
-        ++pi;
-        return true;
-      };
-      if (pre) ok = load_stage(s * L, false);
       for (int t = 0; t < T && ok; ++t) {
         const int i = r0 + t;
-        ok = load_stage(i, true);
+        ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
           ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane);
         if (has_next)
@@ -581,68 +551,35 @@ __global__ void __launch_bounds__(192, 1)
     int row;
     bool has;
     epi_row<C>(warp, lane, &row, &has);
-    const int et = threadIdx.x - 64;  // 0..127
-    const bool leader = et == 0;
+    const bool leader = (warp == 2 && lane == 0);
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const size_t MK = (size_t)C::M * K;
     bool ok = mbar_wait(&b.extra[0], 0);
     ok = __all_sync(0xffffffffu, ok);
-    uint32_t pe = 0;
-    // X tile of P stage `ps` (XT): this thread's row += v[] (or = v[]), then TMA store
-    auto xt_update = [&](uint32_t ps, const float (&v)[C::NT], int irow) {
-      uint8_t* xt = sP + ps * PST + C::PT;
+    int dsel = 0;  // d staging buffer of the next store
+    // FP32 tile v[] of this thread's row -> staging buffer -> TMA store into D row `irow`
+    auto emit = [&](const float (&v)[C::NT], int irow) {
+      if (leader) tma_store_wait_read<1>();
+      named_bar_sync(1, 128);
+      uint8_t* dt = sD + dsel * DT;
       if (ok && has) {
-#pragma unroll 4
-        for (int n = 0; n < C::NT; n += 2) {
-          double2* p = reinterpret_cast<double2*>(xt + xt_off<C>(row, n));
-          double2 x = accumulate ? *p : make_double2(0.0, 0.0);
-          x.x += (double)v[n];
-          x.y += (double)v[n + 1];
-          *p = x;
-        }
+#pragma unroll
+        for (int n = 0; n < C::NT; ++n) *reinterpret_cast<float*>(dt + kmaj_off<CF>(n, row)) = v[n];
       }
       fence_proxy_async_smem();
       named_bar_sync(1, 128);
       if (leader && ok) {
-        for (int q = 0; q < xboxes; ++q) tma_store_2d(&tm_x, n0 + 16 * q, irow * C::M, xt + q * C::M * 128);
+        for (int c = 0; c < CF::NCH; ++c) tma_store_2d(&tm_d, c * CF::CE, irow * Kp + n0, dt + c * CF::TCH);
         tma_store_commit();
-        // the previous stage's store has finished reading: hand its slot back
-        tma_store_wait_read<1>();
-        if (pe > 0) mbar_arrive(&b.emptyP[(pe - 1) % 2]);
       }
-    };
-    // SIMT path: cooperative, coalesced FP64 update of one tile from `stage`
-    auto flush = [&](int irow) {
-      double* xb = X + (size_t)irow * MK + n0;
-      for (int e = et; e < C::M * C::NT; e += 128) {
-        const int rr = e / C::NT, cc = e % C::NT;
-        if (n0 + cc < K) {
-          double* o = xb + (size_t)rr * K + cc;
-          const double v = (double)stage[rr * SLD + cc];
-          *o = accumulate ? *o + v : v;
-        }
-      }
+      dsel ^= 1;
     };
     if (do_iface) {
-      // interface row k_s: X_K (+)= X~_s
       float v[C::NT];
 #pragma unroll
       for (int n = 0; n < C::NT; ++n) v[n] = (ok && has) ? tile_get<E, C>(sB, n, row) : 0.f;
-      if constexpr (XT) {
-        const uint32_t ps = pe % 2;
-        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
-        ok = __all_sync(0xffffffffu, ok);
-        xt_update(ps, v, s * L);
-        ++pe;
-      } else {
-        if (has)
-#pragma unroll
-          for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = v[n];
-        named_bar_sync(1, 128);
-        if (ok) flush(s * L);
-        named_bar_sync(1, 128);
-      }
+      emit(v, s * L);
     }
+    uint32_t pe = 0;
     for (int t = 0; t < T; ++t) {
       const int i = r0 + t;
       const int bsel = t & 1;
@@ -663,30 +600,56 @@ __global__ void __launch_bounds__(192, 1)
       if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
       ok = __all_sync(0xffffffffu, ok);
       if (ok && has) {
-        const uint8_t* tile = sP + ps * PST;
-#pragma unroll 8
+        const uint8_t* tile = sP + ps * C::PT;
+#pragma unroll
         for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
       }
-      if constexpr (XT) {
-        xt_update(ps, v, i);
-      } else {
-        if (ok && has)
-#pragma unroll 8
-          for (int n = 0; n < C::NT; ++n) stage[row * SLD + n] = v[n];
-        named_bar_sync(1, 128);
-        if (ok && leader) mbar_arrive(&b.emptyP[ps]);
-        if (ok) flush(i);
-        named_bar_sync(1, 128);
-      }
+      named_bar_sync(1, 128);
+      if (ok && leader) mbar_arrive(&b.emptyP[ps]);
       ++pe;
+      emit(v, i);
     }
-    if (XT && leader) tma_store_wait<0>();
+    if (leader) tma_store_wait<0>();
     if (!ok && leader) atomicExch(status, 6);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// X (+)= d: block-transposed FP32 correction panel into the caller's row-major
+// FP64 solution, through a 32 x 32 shared-memory tile (coalesced on both
+// sides).  Two FP64-pipe instructions per entry (the widening and the add).
+__global__ void __launch_bounds__(256) k_x_update(const float* __restrict__ d, double* __restrict__ X, int N, int M,
+                                                  int K, int Kp, int accumulate, const int* done) {
+  if (flag_set(done)) return;
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const int64_t tn = (K + 31) / 32, tm = (M + 31) / 32;
+  const int64_t ntile = tn * tm * N;
+  const size_t MK = (size_t)M * K;
+  for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
+    const int n0 = (int)(q0 % tn) * 32;
+    const int m0 = (int)((q0 / tn) % tm) * 32;
+    const int64_t j = q0 / (tn * tm);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = n0 + ty + 8 * q, m = m0 + tx;
+      tile[ty + 8 * q][tx] = (m < M && n < K) ? d[((size_t)j * Kp + n) * M + m] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + ty + 8 * q, n = n0 + tx;
+      if (m < M && n < K) {
+        double* o = X + (size_t)j * MK + (size_t)m * K + n;
+        const double v = (double)tile[tx][ty + 8 * q];
+        *o = accumulate ? *o + v : v;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ======================================================================
@@ -852,11 +815,6 @@ bt_status make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int
   return BT_OK;
 }
 
-bt_status make_map_f64(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                       uint32_t box_outer) {
-  return make_map(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, inner, outer, box_inner, box_outer);
-}
-
 // [SP][5][N][M][M] rounded factor copies (Dinv, E, G, U, V); plane 1 holds the
 // rounding remainder of plane 0.
 template <typename E, int SP>
@@ -886,11 +844,9 @@ template <class C>
 size_t sweep_smem() {
   return 1024 + C::NA * C::SLOT + 4 * C::PT + kBars(C::NA) * 8 + 16;
 }
-template <class C, bool XT>
+template <class C>
 size_t correct_smem() {
-  const size_t xbytes = XT ? (size_t)(C::NT / 16) * C::M * 128 : 0;
-  return 1024 + C::NA * C::SLOT + 2 * (C::PT + xbytes) + 2 * C::PT + (XT ? 0 : (size_t)C::M * (C::NT + 1) * 4) +
-         256 + kBars(C::NA) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + 2 * C::PT + 2 * C::PT + 2 * (size_t)C::NT * C::M * 4 + kBars(C::NA) * 8 + 16;
 }
 
 // CS: configuration of the sweep kernel, CC: of the correction kernel.
@@ -900,18 +856,13 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   constexpr int SP = CS::SP;
   static_assert(CS::SP == CC::SP, "one plane count per precision");
   const int M = CS::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
-  CUtensorMap tm_fac, tm_r, tm_w, tm_wc, tm_x;
+  CUtensorMap tm_fac, tm_r, tm_w, tm_wc, tm_d;
   BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M));
   BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CC::CE, CC::NT));
-  // FP64 solution tiles by TMA need an even leading dimension and a 16-byte aligned base
-  const bool xt = (K % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
-  if (xt) {
-    BT_TRY(make_map_f64(&tm_x, X, (uint64_t)K, (uint64_t)N * M, 16, M));
-  } else {
-    std::memset(&tm_x, 0, sizeof(tm_x));
-  }
+  // FP32 correction panel d, block-transposed like the work panel
+  BT_TRY(make_map(&tm_d, tb.d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)N * Kp, 32, CC::NT));
   const E* r = reinterpret_cast<const E*>(tb.r);
   E* w = reinterpret_cast<E*>(tb.w);
   // step 2.1
@@ -953,17 +904,19 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     int chunks = std::max(1, std::min(rows, (2 * 152 + S * ntiles - 1) / (S * ntiles)));
     const int rpc = (rows + chunks - 1) / chunks;
     chunks = (rows + rpc - 1) / rpc;
-    ProfScope ps(h, st, "tc_correct");
-    if (xt) {
-      const size_t smem = correct_smem<CC, true>();
-      BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tc_correct<E, CC, true><<<dim3(ntiles, S, chunks), 192, smem, st>>>(
-          tm_fac, tm_wc, tm_x, N, L, S, Kp, (int)K, L > 1 ? rpc : 0, X, accumulate, done, status);
-    } else {
-      const size_t smem = correct_smem<CC, false>();
-      BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tc_correct<E, CC, false><<<dim3(ntiles, S, chunks), 192, smem, st>>>(
-          tm_fac, tm_wc, tm_x, N, L, S, Kp, (int)K, L > 1 ? rpc : 0, X, accumulate, done, status);
+    {
+      const size_t smem = correct_smem<CC>();
+      BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ProfScope ps(h, st, "tc_correct");
+      k_tc_correct<E, CC><<<dim3(ntiles, S, chunks), 192, smem, st>>>(tm_fac, tm_wc, tm_d, N, L, S, Kp,
+                                                                       L > 1 ? rpc : 0, done, status);
+    }
+    BT_CUDA(cudaGetLastError());
+    {
+      const int64_t ntile = (int64_t)((K + 31) / 32) * ((M + 31) / 32) * N;
+      const int blocks = (int)std::min<int64_t>(ntile, 152 * 8);
+      ProfScope ps(h, st, "x_update");
+      k_x_update<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
     }
   }
   BT_CUDA(cudaGetLastError());
