@@ -75,6 +75,13 @@ struct LowFactors {
   bool ready = false;
 };
 
+// FP32 transposed copies (element (m, k) at k*M + m) of the interface blocks
+// used by the tensor-core path's interface and dichotomy kernels.
+struct TransposedF32 {
+  float *AK = nullptr, *BK = nullptr, *R = nullptr, *HL = nullptr, *HR = nullptr;
+  bool ready = false;
+};
+
 // Everything a handle owns.  Block arrays are FP64, row-major M x M blocks.
 struct bt_handle_s {
   int device = 0;
@@ -132,6 +139,7 @@ struct bt_handle_s {
   size_t adj_lam_bytes = 0;
 
   LowFactors f32;
+  TransposedF32 f32t;
   // Tensor-core factor copies [5][N][M][M] (Dinv, E, G, U, V) in BF16 / FP32.
   void* tc_fac_bf16 = nullptr;
   void* tc_fac_tf32 = nullptr;

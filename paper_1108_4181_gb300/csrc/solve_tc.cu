@@ -77,9 +77,9 @@ __host__ __device__ constexpr int pow2ceil(int v) {
   return p;
 }
 
-template <typename E, int M_, int NT_, int NA_, int SP_>
+template <typename E, int M_, int NT_, int NA_, int SP_, int NP_ = 2>
 struct Cfg {
-  static constexpr int M = M_, NT = NT_, NA = NA_, SP = SP_;
+  static constexpr int M = M_, NT = NT_, NA = NA_, SP = SP_, NP = NP_;  // NP: panel-ring stages
   static constexpr int eb = (int)sizeof(E);
   static constexpr int CE = 128 / eb;      // elements in one 128-byte swizzle row
   static constexpr int KS = 32 / eb;       // K of one MMA instruction
@@ -91,6 +91,10 @@ struct Cfg {
   static constexpr int PT = SP * TILE;     // a panel tile with all its planes
   static constexpr int TMEM_COLS = pow2ceil(2 * NT);
   static constexpr uint32_t IDESC = instr_desc(ET<E>::fmt, 0, M, NT);
+  static constexpr int EG = 2;                  // epilogue warp groups, each drains NT/EG columns
+  static constexpr int NH = NT / EG;
+  static constexpr int THREADS = 64 + 128 * EG;
+  static_assert(NH % 16 == 0, "epilogue column share");
   static_assert(M == 64 || M == 128, "tensor-core path supports M = 64 and M = 128");
   static_assert(NT % 32 == 0 && NT <= 256, "column tile");
   static_assert(TCH % 1024 == 0, "swizzle atoms");
@@ -161,43 +165,63 @@ __device__ __forceinline__ Bars carve(uint64_t* b) {
   r.fullA = b;
   r.emptyA = b + C::NA;
   r.fullP = b + 2 * C::NA;
-  r.emptyP = r.fullP + 2;
-  r.mdone = r.emptyP + 2;
+  r.emptyP = r.fullP + C::NP;
+  r.mdone = r.emptyP + C::NP;
   r.afree = r.mdone + 2;
   r.yrdy = r.afree + 2;
   r.extra = r.yrdy + 2;
   return r;
 }
 
-__host__ __device__ constexpr int kBars(int na) { return 2 * na + 12; }
+__host__ __device__ constexpr int kBars(int na, int np) { return 2 * na + 2 * np + 8; }
 
+// csize: CTAs of the cluster that consume every A slice (each releases it).
 template <class C>
-__device__ __forceinline__ void init_bars(const Bars& b) {
+__device__ __forceinline__ void init_bars(const Bars& b, int csize) {
   for (int i = 0; i < C::NA; ++i) {
     mbar_init(&b.fullA[i], 1);
-    mbar_init(&b.emptyA[i], 1);
+    mbar_init(&b.emptyA[i], csize);
   }
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < C::NP; ++i) {
     mbar_init(&b.fullP[i], 1);
     mbar_init(&b.emptyP[i], 1);
+  }
+  for (int i = 0; i < 2; ++i) {
     mbar_init(&b.mdone[i], 1);
-    mbar_init(&b.afree[i], 4);
+    mbar_init(&b.afree[i], 4 * C::EG);
     mbar_init(&b.yrdy[i], 1);
     mbar_init(&b.extra[i], 1);
   }
   fence_mbar_init();
 }
 
+// Cluster sharing of the A slices: the `csize` CTAs of a cluster work on the
+// same segment (different column tiles) and need the same factor slices.  Each
+// loads rows [rank*M/csize, (rank+1)*M/csize) of every slice and multicasts
+// them to all; every CTA's MMA releases a slot in all of them, so a slot is
+// refilled only when the whole cluster has consumed it.
+struct Share {
+  int csize, crank;
+  uint16_t mask;
+};
+
 // Producer helper: one A slice (every plane) into the ring; waits for the slot.
 // fplane: tensor-map rows between factor planes.
 template <class C>
 __device__ __forceinline__ bool load_slice(uint8_t* sA, const Bars& b, uint32_t& ai, const CUtensorMap* tm, int x,
-                                           int y, int fplane) {
+                                           int y, int fplane, const Share& sh) {
   const uint32_t slot = ai % C::NA, use = ai / C::NA;
   if (use > 0 && !mbar_wait(&b.emptyA[slot], (use - 1) & 1)) return false;
-  mbar_arrive_expect_tx(&b.fullA[slot], C::SLOT);
+  mbar_arrive_expect_tx(&b.fullA[slot], C::SLOT);  // the whole slot, from every CTA of the cluster
+  const int rs = C::M / sh.csize;
 #pragma unroll
-  for (int p = 0; p < C::SP; ++p) tma_load_2d(sA + slot * C::SLOT + p * C::SLICE, tm, x, y + p * fplane, &b.fullA[slot]);
+  for (int p = 0; p < C::SP; ++p) {
+    uint8_t* dst = sA + slot * C::SLOT + p * C::SLICE + sh.crank * rs * 128;
+    if (sh.csize == 1)
+      tma_load_2d(dst, tm, x, y + p * fplane, &b.fullA[slot]);
+    else
+      tma_load_2d_mc(dst, tm, x, y + p * fplane + sh.crank * rs, &b.fullA[slot], sh.mask);
+  }
   ++ai;
   return true;
 }
@@ -207,7 +231,7 @@ __device__ __forceinline__ bool load_slice(uint8_t* sA, const Bars& b, uint32_t&
 template <class C>
 __device__ __forceinline__ bool load_tile(uint8_t* sP, const Bars& b, uint32_t& pi, const CUtensorMap* tm, int y,
                                           int pplane) {
-  const uint32_t slot = pi % 2, use = pi / 2;
+  const uint32_t slot = pi % C::NP, use = pi / C::NP;
   if (use > 0 && !mbar_wait(&b.emptyP[slot], (use - 1) & 1)) return false;
   mbar_arrive_expect_tx(&b.fullP[slot], C::PT);
 #pragma unroll
@@ -231,7 +255,7 @@ __device__ __forceinline__ void mma1(uint32_t d, uint64_t a, uint64_t bdesc, uin
 // two planes: D += Ahi Bhi + Ahi Blo + Alo Bhi.
 template <typename E, class C>
 __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& ai, uint32_t dtmem, uint32_t btile,
-                                          bool& first) {
+                                          bool& first, const Share& sh) {
   for (int c = 0; c < C::NCH; ++c) {
     const uint32_t slot = ai % C::NA, use = ai / C::NA;
     if (!mbar_wait(&b.fullA[slot], use & 1)) return false;
@@ -247,22 +271,34 @@ __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& 
         mma1<E>(dtmem, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), smem_desc(boff, 16, 1024), C::IDESC, true);
       }
     }
-    mma_commit(&b.emptyA[slot]);
+    if (sh.csize == 1)
+      mma_commit(&b.emptyA[slot]);
+    else
+      mma_commit_mc(&b.emptyA[slot], sh.mask);
     ++ai;
   }
   return true;
 }
 
-// Drains NT accumulator columns of this thread's TMEM lane into v[].
-template <class C>
-__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[C::NT]) {
+// Drains NH accumulator columns of this thread's TMEM lane into v[].
+template <int NH>
+__device__ __forceinline__ void tmem_cols(uint32_t taddr, float (&v)[NH]) {
+  if constexpr (NH % 32 == 0) {
 #pragma unroll
-  for (int c0 = 0; c0 < C::NT; c0 += 32) {
-    float t[32];
-    tmem_ld32(taddr + c0, t);
-    tmem_wait_ld();
+    for (int c0 = 0; c0 < NH; c0 += 32) {
+      float t[32];
+      tmem_ld32(taddr + c0, t);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[c0 + i] = t[i];
+      for (int i = 0; i < 32; ++i) v[c0 + i] = t[i];
+    }
+  } else {
+#pragma unroll
+    for (int c0 = 0; c0 < NH; c0 += 16) {
+      float t[16];
+      tmem_ld16(taddr + c0, t);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[c0 + i] = t[i];
+    }
   }
 }
 
@@ -273,18 +309,19 @@ enum { FT_DINV = 0, FT_E = 1, FT_G = 2, FT_U = 3, FT_V = 4 };
 // Sweep kernel
 // ======================================================================
 template <typename E, class C>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_sweep(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_r,
-               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, const int* done, int* status) {
+               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, int csize, const int* done,
+               int* status) {
   if (flag_set(done)) return;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLOT;
-  uint8_t* sY = sP + 2 * C::PT;
+  uint8_t* sY = sP + C::NP * C::PT;
   uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + 2 * C::PT);
   const Bars b = carve<C>(barmem);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * C::NT;
@@ -295,13 +332,20 @@ __global__ void __launch_bounds__(192, 1)
   const int fplane = 5 * N * C::M;  // tensor-map rows per factor plane
   const int pplane = N * Kp;        // tensor-map rows per panel plane
 
-  if (threadIdx.x == 0) init_bars<C>(b);
+  Share sh;
+  sh.csize = csize;
+  sh.crank = csize > 1 ? (int)cluster_rank() : 0;
+  sh.mask = (uint16_t)((1u << csize) - 1u);
+  if (threadIdx.x == 0) init_bars<C>(b, csize);
   if (warp == 1) {
     tmem_alloc(tslot, C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if (csize > 1)
+    cluster_sync();  // every CTA's barriers exist before any multicast reaches them
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -320,10 +364,10 @@ __global__ void __launch_bounds__(192, 1)
         if (ok) ok = load_tile<C>(sP, b, pi, fwd ? &tm_r : &tm_w, i * Kp + n0, pplane);
         const int first_type = fwd ? FT_DINV : FT_G;
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane, sh);
         if (fwd && t > 0)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane, sh);
       }
       if (!ok) atomicExch(status, 1);
       // no copy may still be landing when the CTA exits
@@ -331,9 +375,9 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t last = (ai - 1 - q);
         mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
       }
-      for (uint32_t q = 0; q < 2 && q < pi; ++q) {
+      for (uint32_t q = 0; q < C::NP && q < pi; ++q) {
         const uint32_t last = pi - 1 - q;
-        mbar_wait(&b.fullP[last % 2], (last / 2) & 1);
+        mbar_wait(&b.fullP[last % C::NP], (last / C::NP) & 1);
       }
     }
   } else if (warp == 1) {
@@ -349,19 +393,19 @@ __global__ void __launch_bounds__(192, 1)
         bool first = true;
         uint32_t pslot = 0;
         if (ok && fwd) {
-          pslot = pi % 2;
-          ok = mbar_wait(&b.fullP[pslot], (pi / 2) & 1);
+          pslot = pi % C::NP;
+          ok = mbar_wait(&b.fullP[pslot], (pi / C::NP) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::PT), first);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::PT), first, sh);
           if (ok && t > 0) {
             ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
             tc_fence_after();
-            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first);
+            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first, sh);
           }
         } else if (ok) {
           ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first, sh);
         }
         if (ok) {
           mma_commit(&b.mdone[bsel]);
@@ -377,10 +421,13 @@ __global__ void __launch_bounds__(192, 1)
       mbar_wait(&b.extra[1], 0);
     }
   } else {
-    // epilogue: 128 threads, thread <-> accumulator row
+    // epilogue: EG groups of 4 warps; thread <-> accumulator row, group g
+    // drains columns [g*NH, (g+1)*NH)
+    constexpr int ET_THREADS = 128 * C::EG;
     int row;
     bool has;
     epi_row<C>(warp, lane, &row, &has);
+    const int cb = ((warp - 2) / 4) * C::NH;
     const bool leader = (warp == 2 && lane == 0);
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     uint32_t pe = (uint32_t)nrow;  // P tiles consumed here start after the forward ones
@@ -393,38 +440,38 @@ __global__ void __launch_bounds__(192, 1)
       if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       tc_fence_after();
-      float v[C::NT];
+      float v[C::NH];
       if (ok) {
-        tmem_row<C>(tmem + lane_base + bsel * C::NT, v);
+        tmem_cols<C::NH>(tmem + lane_base + bsel * C::NT + cb, v);
       } else {
 #pragma unroll
-        for (int n = 0; n < C::NT; ++n) v[n] = 0.f;
+        for (int n = 0; n < C::NH; ++n) v[n] = 0.f;
       }
       tc_fence_before();
       __syncwarp();
       if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
       if (!fwd) {
-        const uint32_t ps = pe % 2;
-        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+        const uint32_t ps = pe % C::NP;
+        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / C::NP) & 1);
         ok = __all_sync(0xffffffffu, ok);
         if (ok && has) {
           const uint8_t* tile = sP + ps * C::PT;
 #pragma unroll
-          for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
+          for (int n = 0; n < C::NH; ++n) v[n] += tile_get<E, C>(tile, cb + n, row);
         }
-        named_bar_sync(1, 128);
+        named_bar_sync(1, ET_THREADS);
         if (ok && leader) mbar_arrive(&b.emptyP[ps]);
         ++pe;
       }
       if (leader) tma_store_wait_read<1>();
-      named_bar_sync(1, 128);
+      named_bar_sync(1, ET_THREADS);
       uint8_t* ybuf = sY + bsel * C::PT;
       if (ok && has) {
 #pragma unroll
-        for (int n = 0; n < C::NT; ++n) tile_put<E, C>(ybuf, n, row, v[n]);
+        for (int n = 0; n < C::NH; ++n) tile_put<E, C>(ybuf, cb + n, row, v[n]);
       }
       fence_proxy_async_smem();
-      named_bar_sync(1, 128);
+      named_bar_sync(1, ET_THREADS);
       if (leader && ok) {
         mbar_arrive(&b.yrdy[bsel]);
         for (int p = 0; p < C::SP; ++p)
@@ -442,7 +489,10 @@ __global__ void __launch_bounds__(192, 1)
     if (!ok && leader) atomicExch(status, 3);
   }
   tc_fence_before();
-  __syncthreads();
+  if (csize > 1)
+    cluster_sync();  // no CTA leaves while another may still signal it
+  else
+    __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -456,9 +506,9 @@ __global__ void __launch_bounds__(192, 1)
 // k_x_update (X (+)= d), a streaming kernel bound by the FP64 pipe.
 // ======================================================================
 template <typename E, class C>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
-                 const __grid_constant__ CUtensorMap tm_d, int N, int L, int S, int Kp, int rows_per_cta,
+                 const __grid_constant__ CUtensorMap tm_d, int N, int L, int S, int Kp, int rows_per_cta, int csize,
                  const int* done, int* status) {
   if (flag_set(done)) return;
   using CF = Cfg<float, C::M, C::NT, 1, 1>;      // layout of one FP32 d tile
@@ -467,11 +517,11 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLOT;
-  uint8_t* sB = sP + 2 * C::PT;  // X~_s, X~_{s+1} (all planes each)
+  uint8_t* sB = sP + C::NP * C::PT;  // X~_s, X~_{s+1} (all planes each)
   uint8_t* sD = sB + 2 * C::PT;  // two FP32 d tiles
   uint64_t* barmem = reinterpret_cast<uint64_t*>(sD + 2 * DT);
   const Bars b = carve<C>(barmem);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * C::NT;
@@ -484,13 +534,20 @@ __global__ void __launch_bounds__(192, 1)
   const int fplane = 5 * N * C::M;
   const int pplane = N * Kp;
 
-  if (threadIdx.x == 0) init_bars<C>(b);
+  Share sh;
+  sh.csize = csize;
+  sh.crank = csize > 1 ? (int)cluster_rank() : 0;
+  sh.mask = (uint16_t)((1u << csize) - 1u);
+  if (threadIdx.x == 0) init_bars<C>(b, csize);
   if (warp == 1) {
     tmem_alloc(tslot, C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if (csize > 1)
+    cluster_sync();  // every CTA's barriers exist before any multicast reaches them
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -512,10 +569,10 @@ __global__ void __launch_bounds__(192, 1)
         const int i = r0 + t;
         ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
         if (has_next)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane, sh);
       }
       if (!ok) atomicExch(status, 4);
       mbar_wait(&b.extra[0], 0);
@@ -523,9 +580,9 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t last = (ai - 1 - q);
         mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
       }
-      for (uint32_t q = 0; q < 2 && q < pi; ++q) {
+      for (uint32_t q = 0; q < C::NP && q < pi; ++q) {
         const uint32_t last = pi - 1 - q;
-        mbar_wait(&b.fullP[last % 2], (last / 2) & 1);
+        mbar_wait(&b.fullP[last % C::NP], (last / C::NP) & 1);
       }
     }
   } else if (warp == 1) {
@@ -539,8 +596,8 @@ __global__ void __launch_bounds__(192, 1)
         if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
         tc_fence_after();
         bool first = true;
-        if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first);
-        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::PT), first);
+        if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first, sh);
+        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::PT), first, sh);
         if (ok) mma_commit(&b.mdone[bsel]);
       }
       if (!ok) atomicExch(status, 5);
@@ -548,25 +605,27 @@ __global__ void __launch_bounds__(192, 1)
       mbar_wait(&b.extra[1], 0);
     }
   } else {
+    constexpr int ET_THREADS = 128 * C::EG;
     int row;
     bool has;
     epi_row<C>(warp, lane, &row, &has);
+    const int cb = ((warp - 2) / 4) * C::NH;
     const bool leader = (warp == 2 && lane == 0);
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = mbar_wait(&b.extra[0], 0);
     ok = __all_sync(0xffffffffu, ok);
     int dsel = 0;  // d staging buffer of the next store
-    // FP32 tile v[] of this thread's row -> staging buffer -> TMA store into D row `irow`
-    auto emit = [&](const float (&v)[C::NT], int irow) {
+    // FP32 values v[] of this thread's row and column share -> staging buffer -> TMA store into D row `irow`
+    auto emit = [&](const float (&v)[C::NH], int irow) {
       if (leader) tma_store_wait_read<1>();
-      named_bar_sync(1, 128);
+      named_bar_sync(1, ET_THREADS);
       uint8_t* dt = sD + dsel * DT;
       if (ok && has) {
 #pragma unroll
-        for (int n = 0; n < C::NT; ++n) *reinterpret_cast<float*>(dt + kmaj_off<CF>(n, row)) = v[n];
+        for (int n = 0; n < C::NH; ++n) *reinterpret_cast<float*>(dt + kmaj_off<CF>(cb + n, row)) = v[n];
       }
       fence_proxy_async_smem();
-      named_bar_sync(1, 128);
+      named_bar_sync(1, ET_THREADS);
       if (leader && ok) {
         for (int c = 0; c < CF::NCH; ++c) tma_store_2d(&tm_d, c * CF::CE, irow * Kp + n0, dt + c * CF::TCH);
         tma_store_commit();
@@ -574,9 +633,9 @@ __global__ void __launch_bounds__(192, 1)
       dsel ^= 1;
     };
     if (do_iface) {
-      float v[C::NT];
+      float v[C::NH];
 #pragma unroll
-      for (int n = 0; n < C::NT; ++n) v[n] = (ok && has) ? tile_get<E, C>(sB, n, row) : 0.f;
+      for (int n = 0; n < C::NH; ++n) v[n] = (ok && has) ? tile_get<E, C>(sB, cb + n, row) : 0.f;
       emit(v, s * L);
     }
     uint32_t pe = 0;
@@ -586,25 +645,25 @@ __global__ void __launch_bounds__(192, 1)
       if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       tc_fence_after();
-      float v[C::NT];
+      float v[C::NH];
       if (ok) {
-        tmem_row<C>(tmem + lane_base + bsel * C::NT, v);
+        tmem_cols<C::NH>(tmem + lane_base + bsel * C::NT + cb, v);
       } else {
 #pragma unroll
-        for (int n = 0; n < C::NT; ++n) v[n] = 0.f;
+        for (int n = 0; n < C::NH; ++n) v[n] = 0.f;
       }
       tc_fence_before();
       __syncwarp();
       if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
-      const uint32_t ps = pe % 2;
-      if (ok) ok = mbar_wait(&b.fullP[ps], (pe / 2) & 1);
+      const uint32_t ps = pe % C::NP;
+      if (ok) ok = mbar_wait(&b.fullP[ps], (pe / C::NP) & 1);
       ok = __all_sync(0xffffffffu, ok);
       if (ok && has) {
         const uint8_t* tile = sP + ps * C::PT;
 #pragma unroll
-        for (int n = 0; n < C::NT; ++n) v[n] += tile_get<E, C>(tile, n, row);
+        for (int n = 0; n < C::NH; ++n) v[n] += tile_get<E, C>(tile, cb + n, row);
       }
-      named_bar_sync(1, 128);
+      named_bar_sync(1, ET_THREADS);
       if (ok && leader) mbar_arrive(&b.emptyP[ps]);
       ++pe;
       emit(v, i);
@@ -613,7 +672,10 @@ __global__ void __launch_bounds__(192, 1)
     if (!ok && leader) atomicExch(status, 6);
   }
   tc_fence_before();
-  __syncthreads();
+  if (csize > 1)
+    cluster_sync();  // no CTA leaves while another may still signal it
+  else
+    __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -654,7 +716,11 @@ __global__ void __launch_bounds__(256) k_x_update(const float* __restrict__ d, d
 
 // ======================================================================
 // Step 2.2 on the CUDA cores (FP32), block-transposed panels of type E with
-// SP planes (plane stride `ps` elements)
+// SP planes (plane stride `ps` elements).  Each thread owns a 4 x 8 register
+// tile (4 block rows x 8 columns); the FP32 interface blocks are stored
+// transposed (element (m, k) at k*M + m) so the four rows of one k are one
+// 16-byte load, and the panel tile is read from shared memory as two
+// broadcast 16-byte loads per k.
 // ======================================================================
 template <typename E, int SP>
 __device__ __forceinline__ float pget(const E* base, size_t idx, size_t ps) {
@@ -663,120 +729,149 @@ __device__ __forceinline__ float pget(const E* base, size_t idx, size_t ps) {
   return v;
 }
 
+// acc[i][j] += sum_k At[k][r0+i] * pan[k][c0+j]
+template <int KT>
+__device__ __forceinline__ void mt_gemm(float (&acc)[4][8], const float* __restrict__ At, int M, int r0,
+                                        const float* pan, int c0) {
+#pragma unroll 4
+  for (int k = 0; k < M; ++k) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(At + (size_t)k * M + r0));
+    const float4 p0 = *reinterpret_cast<const float4*>(pan + k * KT + c0);
+    const float4 p1 = *reinterpret_cast<const float4*>(pan + k * KT + c0 + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], pv[j], acc[i][j]);
+  }
+}
+
 // F~_s = r_K + A_K W_{K-1} + B_K W_{K+1};  c[l][s] = R[l][s] F~_s  (FP32, c row-major [M][Kp])
-template <typename E, int SP, int CW>
-__global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, const float* __restrict__ AK,
-                           const float* __restrict__ BK, const float* __restrict__ R, const int* __restrict__ mid_level,
-                           float* __restrict__ cbuf, int N, int M, int S, int L, int Kp, const int* done) {
+template <typename E, int SP, int KT>
+__global__ void k_tc_iface(const E* __restrict__ r, const E* __restrict__ w, const float* __restrict__ tAK,
+                           const float* __restrict__ tBK, const float* __restrict__ tR,
+                           const int* __restrict__ mid_level, float* __restrict__ cbuf, int N, int M, int S, int L,
+                           int Kp, const int* done) {
   if (flag_set(done)) return;
-  extern __shared__ float fsm[];
-  const int CG = blockDim.x / M, kt = CW * CG;
-  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
-  const int s = blockIdx.x, col0 = blockIdx.y * kt;
+  extern __shared__ __align__(16) float fsm[];
+  constexpr int CGS = KT / 8;
+  const int t = threadIdx.x, r0 = (t / CGS) * 4, c0 = (t % CGS) * 8;
+  const int s = blockIdx.x, col0 = blockIdx.y * KT;
   const int Kr = s * L;
   const size_t ps = (size_t)N * Kp * M;
   float* pa = fsm;
-  float* pb = fsm + M * kt;
-  float* pt = fsm + 2 * M * kt;
+  float* pb = fsm + M * KT;
+  float* pt = fsm + 2 * M * KT;
   const bool hasL = s > 0 && L > 1, hasR = Kr + 1 < N && L > 1;
-  for (int e = t; e < M * kt; e += blockDim.x) {
+  for (int e = t; e < M * KT; e += blockDim.x) {
     const int mm = e % M, n = e / M;  // coalesced along m
     const size_t off = (size_t)(col0 + n) * M + mm;
-    pa[mm * kt + n] = hasL ? pget<E, SP>(w, (size_t)(Kr - 1) * Kp * M + off, ps) : 0.f;
-    pb[mm * kt + n] = hasR ? pget<E, SP>(w, (size_t)(Kr + 1) * Kp * M + off, ps) : 0.f;
-    pt[mm * kt + n] = pget<E, SP>(r, (size_t)Kr * Kp * M + off, ps);
+    pa[mm * KT + n] = hasL ? pget<E, SP>(w, (size_t)(Kr - 1) * Kp * M + off, ps) : 0.f;
+    pb[mm * KT + n] = hasR ? pget<E, SP>(w, (size_t)(Kr + 1) * Kp * M + off, ps) : 0.f;
+    pt[mm * KT + n] = pget<E, SP>(r, (size_t)Kr * Kp * M + off, ps);
   }
   __syncthreads();
   const size_t MM = (size_t)M * M;
-  float acc[CW];
+  float acc[4][8];
 #pragma unroll
-  for (int c = 0; c < CW; ++c) acc[c] = pt[m * kt + c0 + c];
-  const float* arow = AK + s * MM + (size_t)m * M;
-  const float* brow = BK + s * MM + (size_t)m * M;
-  for (int k = 0; k < M; ++k) {
-    const float av = hasL ? __ldg(arow + k) : 0.f, bv = hasR ? __ldg(brow + k) : 0.f;
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] = fmaf(av, pa[k * kt + c0 + c], fmaf(bv, pb[k * kt + c0 + c], acc[c]));
-  }
+    for (int j = 0; j < 8; ++j) acc[i][j] = pt[(r0 + i) * KT + c0 + j];
+  if (hasL) mt_gemm<KT>(acc, tAK + s * MM, M, r0, pa, c0);
+  if (hasR) mt_gemm<KT>(acc, tBK + s * MM, M, r0, pb, c0);
   __syncthreads();
 #pragma unroll
-  for (int c = 0; c < CW; ++c) pt[m * kt + c0 + c] = acc[c];
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pt[(r0 + i) * KT + c0 + j] = acc[i][j];
   __syncthreads();
   const int top = mid_level[s];
   for (int lev = 0; lev <= top; ++lev) {
-    float cc[CW];
+    float cc[4][8];
 #pragma unroll
-    for (int c = 0; c < CW; ++c) cc[c] = 0.f;
-    const float* rr = R + ((size_t)lev * S + s) * MM + (size_t)m * M;
-    for (int k = 0; k < M; ++k) {
-      const float rv = __ldg(rr + k);
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int c = 0; c < CW; ++c) cc[c] = fmaf(rv, pt[k * kt + c0 + c], cc[c]);
+      for (int j = 0; j < 8; ++j) cc[i][j] = 0.f;
+    mt_gemm<KT>(cc, tR + ((size_t)lev * S + s) * MM, M, r0, pt, c0);
+    float* out = cbuf + ((size_t)lev * S + s) * M * Kp + (size_t)r0 * Kp + col0 + c0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float4* o = reinterpret_cast<float4*>(out + (size_t)i * Kp);
+      o[0] = make_float4(cc[i][0], cc[i][1], cc[i][2], cc[i][3]);
+      o[1] = make_float4(cc[i][4], cc[i][5], cc[i][6], cc[i][7]);
     }
-    float* out = cbuf + ((size_t)lev * S + s) * M * Kp + (size_t)m * Kp + col0 + c0;
-#pragma unroll
-    for (int c = 0; c < CW; ++c) out[c] = cc[c];
   }
 }
 
 // X~_m = sum_{j in [l, r]} c[level][j] + HL_m X~_{l-1} + HR_m X~_{r+1}, written
 // into the work panel's interface row k_m (all planes).
-template <typename E, int SP, int CW>
-__global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf, const float* __restrict__ HL,
-                               const float* __restrict__ HR, const int* __restrict__ nodes, int lev, int node_off,
+template <typename E, int SP, int KT>
+__global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf, const float* __restrict__ tHL,
+                               const float* __restrict__ tHR, const int* __restrict__ nodes, int lev, int node_off,
                                int N, int M, int S, int L, int Kp, const int* done) {
   if (flag_set(done)) return;
-  extern __shared__ float fsm[];
-  const int CG = blockDim.x / M, kt = CW * CG;
-  const int t = threadIdx.x, m = t / CG, c0 = (t % CG) * CW;
+  extern __shared__ __align__(16) float fsm[];
+  constexpr int CGS = KT / 8;
+  const int t = threadIdx.x, r0 = (t / CGS) * 4, c0 = (t % CGS) * 8;
   const int q = node_off + blockIdx.x;
   const int l = nodes[3 * q], r = nodes[3 * q + 1], mid = nodes[3 * q + 2];
-  const int col0 = blockIdx.y * kt;
+  const int col0 = blockIdx.y * KT;
   const size_t ps = (size_t)N * Kp * M;
   float* pl = fsm;
-  float* pr = fsm + M * kt;
+  float* pr = fsm + M * KT;
   const bool hl = l > 0, hr = r < S - 1;
-  for (int e = t; e < M * kt; e += blockDim.x) {
+  for (int e = t; e < M * KT; e += blockDim.x) {
     const int mm = e % M, n = e / M;
     const size_t off = (size_t)(col0 + n) * M + mm;
-    pl[mm * kt + n] = hl ? pget<E, SP>(w, (size_t)(l - 1) * L * Kp * M + off, ps) : 0.f;
-    pr[mm * kt + n] = hr ? pget<E, SP>(w, (size_t)(r + 1) * L * Kp * M + off, ps) : 0.f;
+    pl[mm * KT + n] = hl ? pget<E, SP>(w, (size_t)(l - 1) * L * Kp * M + off, ps) : 0.f;
+    pr[mm * KT + n] = hr ? pget<E, SP>(w, (size_t)(r + 1) * L * Kp * M + off, ps) : 0.f;
   }
   __syncthreads();
   const size_t MM = (size_t)M * M;
-  float acc[CW];
+  float acc[4][8];
 #pragma unroll
-  for (int c = 0; c < CW; ++c) acc[c] = 0.f;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
   for (int j = l; j <= r; ++j) {
-    const float* cj = cbuf + ((size_t)lev * S + j) * M * Kp + (size_t)m * Kp + col0 + c0;
+    const float* cj = cbuf + ((size_t)lev * S + j) * M * Kp + (size_t)r0 * Kp + col0 + c0;
 #pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] += cj[c];
-  }
-  const float* hlr = HL + (size_t)mid * MM + (size_t)m * M;
-  const float* hrr = HR + (size_t)mid * MM + (size_t)m * M;
-  for (int k = 0; k < M; ++k) {
-    const float a1 = hl ? __ldg(hlr + k) : 0.f, a2 = hr ? __ldg(hrr + k) : 0.f;
-#pragma unroll
-    for (int c = 0; c < CW; ++c) acc[c] = fmaf(a1, pl[k * kt + c0 + c], fmaf(a2, pr[k * kt + c0 + c], acc[c]));
-  }
-  __syncthreads();
-  // transpose through shared memory for a coalesced store along m
-#pragma unroll
-  for (int c = 0; c < CW; ++c) pl[m * kt + c0 + c] = acc[c];
-  __syncthreads();
-  E* out = w + (size_t)mid * L * Kp * M;
-  for (int e = t; e < M * kt; e += blockDim.x) {
-    const int mm = e % M, n = e / M;
-    const size_t off = (size_t)(col0 + n) * M + mm;
-    const float v = pl[mm * kt + n];
-    if (SP == 2) {
-      E hi, lo;
-      ET<E>::split(v, hi, lo);
-      out[off] = hi;
-      out[off + ps] = lo;
-    } else {
-      out[off] = ET<E>::from(v);
+    for (int i = 0; i < 4; ++i) {
+      const float4 u0 = *reinterpret_cast<const float4*>(cj + (size_t)i * Kp);
+      const float4 u1 = *reinterpret_cast<const float4*>(cj + (size_t)i * Kp + 4);
+      acc[i][0] += u0.x; acc[i][1] += u0.y; acc[i][2] += u0.z; acc[i][3] += u0.w;
+      acc[i][4] += u1.x; acc[i][5] += u1.y; acc[i][6] += u1.z; acc[i][7] += u1.w;
     }
+  }
+  if (hl) mt_gemm<KT>(acc, tHL + (size_t)mid * MM, M, r0, pl, c0);
+  if (hr) mt_gemm<KT>(acc, tHR + (size_t)mid * MM, M, r0, pr, c0);
+  // rows r0..r0+3 are contiguous in the block-transposed panel: write them per column
+  E* out = w + (size_t)mid * L * Kp * M;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const size_t off = (size_t)(col0 + c0 + j) * M + r0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (SP == 2) {
+        E hi, lo;
+        ET<E>::split(acc[i][j], hi, lo);
+        out[off + i] = hi;
+        out[off + i + ps] = lo;
+      } else {
+        out[off + i] = ET<E>::from(acc[i][j]);
+      }
+    }
+  }
+}
+
+// FP32 transposed copies of the interface blocks (element (m, k) at k*M + m).
+__global__ void k_cast_transpose(const double* __restrict__ src, float* __restrict__ dst, size_t nblk, int M) {
+  const size_t MM = (size_t)M * M, n = nblk * MM;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t bI = e / MM, o = e % MM;
+    const int k = (int)(o / M), m = (int)(o % M);
+    dst[e] = (float)src[bI * MM + (size_t)m * M + k];
   }
 }
 
@@ -842,11 +937,12 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
 
 template <class C>
 size_t sweep_smem() {
-  return 1024 + C::NA * C::SLOT + 4 * C::PT + kBars(C::NA) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + (C::NP + 2) * C::PT + kBars(C::NA, C::NP) * 8 + 16;
 }
 template <class C>
 size_t correct_smem() {
-  return 1024 + C::NA * C::SLOT + 2 * C::PT + 2 * C::PT + 2 * (size_t)C::NT * C::M * 4 + kBars(C::NA) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + C::NP * C::PT + 2 * C::PT + 2 * (size_t)C::NT * C::M * 4 + kBars(C::NA, C::NP) * 8 +
+         16;
 }
 
 // CS: configuration of the sweep kernel, CC: of the correction kernel.
@@ -856,8 +952,15 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   constexpr int SP = CS::SP;
   static_assert(CS::SP == CC::SP, "one plane count per precision");
   const int M = CS::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
-  CUtensorMap tm_fac, tm_r, tm_w, tm_wc, tm_d;
-  BT_TRY(make_map(&tm_fac, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M));
+  CUtensorMap tm_fac_s, tm_fac_c, tm_r, tm_w, tm_wc, tm_d;
+  // cluster size along the column tiles: every A slice is loaded once per cluster
+  // (measured on the acoustic workload: sharing through clusters of 2-4 made the
+  // sweep slower -- the kernels are latency-bound, not L2-bound -- so every
+  // CTA loads its own slices; the multicast path stays for other shapes)
+  auto pick_cluster = [](int ntiles) { (void)ntiles; return 1; };
+  const int cs_sweep = pick_cluster(Kp / CS::NT), cs_corr = pick_cluster(Kp / CC::NT);
+  BT_TRY(make_map(&tm_fac_s, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M / cs_sweep));
+  BT_TRY(make_map(&tm_fac_c, tb.fac, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CC::CE, M / cs_corr));
   BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CC::CE, CC::NT));
@@ -870,29 +973,38 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     const size_t smem = sweep_smem<CS>();
     BT_CUDA(cudaFuncSetAttribute(k_tc_sweep<E, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(h, st, "tc_sweep");
-    k_tc_sweep<E, CS><<<dim3(Kp / CS::NT, S), 192, smem, st>>>(tm_fac, tm_r, tm_w, N, L, Kp, done, status);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs_sweep;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(Kp / CS::NT, S);
+    cfg.blockDim = dim3(CS::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_sweep<E, CS>, tm_fac_s, tm_r, tm_w, N, L, Kp, cs_sweep, done, status));
   }
   BT_CUDA(cudaGetLastError());
   // step 2.2 (FP32 on the CUDA cores)
   {
-    constexpr int CW = 8;
-    const int CG = 4;
-    const int kt = CW * CG;
-    const int nt2 = Kp / kt;
-    const LowFactors& f = h->f32;
-    const size_t sm3 = 3 * (size_t)M * kt * sizeof(float);
-    BT_CUDA(cudaFuncSetAttribute(k_tc_iface<E, SP, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    BT_CUDA(cudaFuncSetAttribute(k_tc_dichotomy<E, SP, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    constexpr int KT = 32;   // columns per interface CTA
+    constexpr int KD = 16;   // columns per dichotomy CTA (more CTAs on the narrow top levels)
+    const TransposedF32& f = h->f32t;
+    const size_t sm3 = 3 * (size_t)M * KT * sizeof(float);
+    BT_CUDA(cudaFuncSetAttribute(k_tc_iface<E, SP, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
     {
       ProfScope ps(h, st, "tc_iface");
-      k_tc_iface<E, SP, CW><<<dim3(S, nt2), M * CG, sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level, tb.c, N, M, S,
-                                                               L, Kp, done);
+      k_tc_iface<E, SP, KT><<<dim3(S, Kp / KT), (M / 4) * (KT / 8), sm3, st>>>(r, w, f.AK, f.BK, f.R, h->d_mid_level,
+                                                                            tb.c, N, M, S, L, Kp, done);
     }
     BT_CUDA(cudaGetLastError());
     for (int lev = 0; lev < h->depth; ++lev) {
       const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
       ProfScope ps(h, st, "tc_dichotomy");
-      k_tc_dichotomy<E, SP, CW><<<dim3(nn, nt2), M * CG, 2 * (size_t)M * kt * sizeof(float), st>>>(
+      k_tc_dichotomy<E, SP, KD><<<dim3(nn, Kp / KD), (M / 4) * (KD / 8), 2 * (size_t)M * KD * sizeof(float), st>>>(
           w, tb.c, f.HL, f.HR, h->d_nodes, lev, n0, N, M, S, L, Kp, done);
     }
     BT_CUDA(cudaGetLastError());
@@ -908,8 +1020,20 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       const size_t smem = correct_smem<CC>();
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       ProfScope ps(h, st, "tc_correct");
-      k_tc_correct<E, CC><<<dim3(ntiles, S, chunks), 192, smem, st>>>(tm_fac, tm_wc, tm_d, N, L, S, Kp,
-                                                                       L > 1 ? rpc : 0, done, status);
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cs_corr;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(ntiles, S, chunks);
+      cfg.blockDim = dim3(CC::THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_correct<E, CC>, tm_fac_c, tm_wc, tm_d, N, L, S, Kp, L > 1 ? rpc : 0,
+                                 cs_corr, done, status));
     }
     BT_CUDA(cudaGetLastError());
     {
@@ -924,18 +1048,21 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
 }
 
 // sweep / correction configurations per (operand type, block size, planes)
-using SwB128 = Cfg<__nv_bfloat16, 128, 64, 6, 1>;
-using CoB128 = Cfg<__nv_bfloat16, 128, 32, 4, 1>;
-using SwT128 = Cfg<float, 128, 32, 6, 1>;
-using CoT128 = Cfg<float, 128, 32, 4, 1>;
-using SwB64 = Cfg<__nv_bfloat16, 64, 128, 8, 1>;
-using CoB64 = Cfg<__nv_bfloat16, 64, 64, 4, 1>;
-using SwT64 = Cfg<float, 64, 64, 8, 1>;
-using CoT64 = Cfg<float, 64, 64, 4, 1>;
-using SwX128 = Cfg<__nv_bfloat16, 128, 32, 4, 2>;
-using CoX128 = Cfg<__nv_bfloat16, 128, 32, 3, 2>;
-using SwX64 = Cfg<__nv_bfloat16, 64, 64, 8, 2>;
-using CoX64 = Cfg<__nv_bfloat16, 64, 64, 4, 2>;
+// (sweep rings as deep as shared memory allows: a forward step consumes two
+// blocks, so a ring of more than two blocks lets the next step's slices land
+// while the current step waits for its recurrence operand)
+using SwB128 = Cfg<__nv_bfloat16, 128, 64, 8, 1, 4>;
+using CoB128 = Cfg<__nv_bfloat16, 128, 32, 6, 1, 4>;
+using SwT128 = Cfg<float, 128, 32, 8, 1, 4>;
+using CoT128 = Cfg<float, 128, 32, 6, 1, 4>;
+using SwB64 = Cfg<__nv_bfloat16, 64, 128, 16, 1, 4>;
+using CoB64 = Cfg<__nv_bfloat16, 64, 64, 8, 1, 4>;
+using SwT64 = Cfg<float, 64, 64, 16, 1, 4>;
+using CoT64 = Cfg<float, 64, 64, 8, 1, 4>;
+using SwX128 = Cfg<__nv_bfloat16, 128, 64, 3, 2, 2>;
+using CoX128 = Cfg<__nv_bfloat16, 128, 32, 3, 2, 4>;
+using SwX64 = Cfg<__nv_bfloat16, 64, 64, 8, 2, 4>;
+using CoX64 = Cfg<__nv_bfloat16, 64, 64, 6, 2, 4>;
 
 }  // namespace
 
@@ -947,7 +1074,27 @@ int tc_col_tile(int precision, int M) {
 
 int tc_planes(int precision) { return precision == BT_PREC_BF16X3 ? 2 : 1; }
 
+bt_status make_f32t_factors(bt_handle_s* h, cudaStream_t st) {
+  TransposedF32& f = h->f32t;
+  if (f.ready) return BT_OK;
+  const size_t MM = (size_t)h->M * h->M;
+  struct Item {
+    float** dst;
+    const double* src;
+    size_t nblk;
+  } items[] = {{&f.AK, h->AK, (size_t)h->S}, {&f.BK, h->BK, (size_t)h->S}, {&f.R, h->R, (size_t)h->depth * h->S},
+               {&f.HL, h->HL, (size_t)h->S}, {&f.HR, h->HR, (size_t)h->S}};
+  for (auto& it : items) {
+    BT_TRY(h->arena.alloc((void**)it.dst, it.nblk * MM * sizeof(float)));
+    k_cast_transpose<<<512, 256, 0, st>>>(it.src, *it.dst, it.nblk, (int)h->M);
+  }
+  BT_CUDA(cudaGetLastError());
+  f.ready = true;
+  return BT_OK;
+}
+
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
+  BT_TRY(make_f32t_factors(h, st));
   void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : precision == BT_PREC_TF32 ? &h->tc_fac_tf32 : &h->tc_fac_bf16x3;
   if (*slot) return BT_OK;
   const size_t nb = (size_t)h->N * h->M * h->M;
