@@ -136,6 +136,42 @@ bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_
                            double* dA, double* dB, double* dC, void* stream);
 
 /*
+ * Batched solves (not in the paper): many right-hand-side sets, each against
+ * its own factored matrix, solved in FP64 by ONE persistent cooperative
+ * launch that runs stage 2 of Algorithm 2 for all of them -- sweeps,
+ * interface terms, one stage per dichotomy level, corrections, separated by
+ * grid-wide barriers -- and that is replayed from a CUDA graph.
+ *
+ * bt_batch_create -- plans a batch of n >= 1 sets; set i solves
+ *   P_{h[i]} X_i = F_i, F[i] and X[i] being device [N_i][M][K[i]] FP64 panels
+ *   as for bt_solve.  h, F, K, X are HOST arrays of n entries; the panels are
+ *   device memory owned by the caller that must keep their addresses while
+ *   the plan is used (the plan records the pointers).  All handles live on the
+ *   current device and share one block size M (N and S may differ).  No X[i]
+ *   may overlap an F[j] or another X[j].  opts (may be NULL): precision must
+ *   be BT_PREC_F64 (otherwise BT_ERR_UNSUPPORTED); k_tile = right-hand-side
+ *   columns per work item (0 = automatic); stream is not used.  The plan owns
+ *   its scratch (the sum over sets of depth*S*M*K[i] doubles) and its graph;
+ *   the handles must outlive it.  Synchronous; BT_ERR_ARG on invalid input.
+ * bt_batch_run -- enqueues one batched solve on `stream` (one graph launch).
+ * bt_batch_status -- waits for the plan's work and returns BT_OK, or
+ *   BT_ERR_TIMEOUT if a grid-barrier wait of the last run gave up (20 s).
+ * bt_batch_query -- out[0] work items, out[1] stages, out[2] CTAs of the
+ *   persistent launch, out[3] threads per CTA, out[4] columns per item,
+ *   out[5] 1 when runs replay a CUDA graph.
+ * bt_solve_batched -- create, run on opts->stream, wait, destroy.
+ */
+typedef struct bt_batch_s* bt_batch;
+bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,
+                          double* const* X, const bt_opts* opts, bt_batch* out);
+bt_status bt_batch_run(bt_batch b, void* stream);
+bt_status bt_batch_status(bt_batch b);
+bt_status bt_batch_query(bt_batch b, int64_t out[6]);
+void bt_batch_destroy(bt_batch b);
+bt_status bt_solve_batched(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,
+                           double* const* X, const bt_opts* opts);
+
+/*
  * bt_solve_noalloc -- the FP64 solve of bt_solve, for callers that cannot
  * allocate device memory at solve time.  The paper has no counterpart: it is a
  * service of this library.  Some callers cannot call cudaMalloc once they are

@@ -54,6 +54,14 @@ SIGNATURES = {
     "bt_solve_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "bt_profile_enable": (ctypes.c_int, [_vp, _i32]),
     "bt_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(BtKernelStat), _i32, ctypes.POINTER(_i32)]),
+    "bt_batch_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                                       ctypes.POINTER(_vp), ctypes.POINTER(BtOpts), ctypes.POINTER(_vp)]),
+    "bt_batch_run": (ctypes.c_int, [_vp, _vp]),
+    "bt_batch_status": (ctypes.c_int, [_vp]),
+    "bt_batch_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "bt_batch_destroy": (None, [_vp]),
+    "bt_solve_batched": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                                        ctypes.POINTER(_vp), ctypes.POINTER(BtOpts)]),
 }
 
 _LIB = None

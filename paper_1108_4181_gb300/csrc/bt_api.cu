@@ -16,6 +16,17 @@ bt_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? BT_ERR_OOM : BT_ERR_CUDA;
 }
 
+int resident_grid(const void* fn, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms * per_sm;
+}
+
 bt_status DevArena::alloc(void** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 16;
@@ -261,6 +272,169 @@ bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_
 }
 
 void bt_destroy(bt_handle h) { destroy_handle(h); }
+
+// ---------------------------------------------------------------- batches
+static void destroy_batch(bt_batch_s* b) {
+  if (!b) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->arena.release();
+  cudaSetDevice(prev);
+  delete b;
+}
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
+bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,
+                          double* const* X, const bt_opts* opts, bt_batch* out) {
+  if (!out) {
+    set_error("bt_batch_create: out is NULL");
+    return BT_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n < 1 || !h || !F || !K || !X) {
+    set_error("bt_batch_create: need n >= 1 and host arrays h, F, K, X");
+    return BT_ERR_ARG;
+  }
+  bt_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.precision != BT_PREC_F64) {
+    set_error("bt_batch_create: batched solves run in FP64 only (precision BT_PREC_F64)");
+    return BT_ERR_UNSUPPORTED;
+  }
+  if (o.k_tile < 0) {
+    set_error("bt_batch_create: k_tile must be >= 0");
+    return BT_ERR_ARG;
+  }
+  int dev = 0;
+  BT_CUDA(cudaGetDevice(&dev));
+  for (int32_t i = 0; i < n; ++i) {
+    if (!h[i] || !F[i] || !X[i] || K[i] < 1) {
+      set_error("bt_batch_create: set " + std::to_string(i) + " needs a handle, device F and X, K >= 1");
+      return BT_ERR_ARG;
+    }
+    if (h[i]->device != dev || h[i]->M != h[0]->M) {
+      set_error("bt_batch_create: every handle must be on the current device and share one block size M");
+      return BT_ERR_ARG;
+    }
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    const size_t bi = (size_t)h[i]->N * h[i]->M * K[i] * sizeof(double);
+    for (int32_t j = 0; j < n; ++j) {
+      const size_t bj = (size_t)h[j]->N * h[j]->M * K[j] * sizeof(double);
+      if (overlaps(X[i], bi, F[j], bj) || (j != i && overlaps(X[i], bi, X[j], bj))) {
+        set_error("bt_batch_create: X of set " + std::to_string(i) + " overlaps the panels of set " +
+                  std::to_string(j));
+        return BT_ERR_ARG;
+      }
+    }
+  }
+  bt_batch_s* b = new (std::nothrow) bt_batch_s();
+  if (!b) {
+    set_error("bt_batch_create: host allocation failed");
+    return BT_ERR_OOM;
+  }
+  b->device = dev;
+  b->n = n;
+  b->precision = o.precision;
+  bt_status st = batch_build(b, n, h, F, K, X, o);
+  if (st == BT_OK) {
+    // capture one run into a CUDA graph on a private stream
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const bt_status q = batch_enqueue(b, cs);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (q == BT_OK && e == cudaSuccess && g) {
+          if (cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess)
+            b->graph = g;
+          else
+            cudaGraphDestroy(g);
+        } else if (g) {
+          cudaGraphDestroy(g);
+        }
+      }
+      cudaStreamDestroy(cs);
+    }
+    cudaGetLastError();  // a failed capture leaves plain launches in use
+  }
+  if (st != BT_OK) {
+    destroy_batch(b);
+    return st;
+  }
+  *out = b;
+  return BT_OK;
+}
+
+bt_status bt_batch_run(bt_batch b, void* stream) {
+  if (!b) {
+    set_error("bt_batch_run: NULL plan");
+    return BT_ERR_ARG;
+  }
+  if (b->exec) {
+    BT_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return BT_OK;
+  }
+  return batch_enqueue(b, (cudaStream_t)stream);
+}
+
+bt_status bt_batch_status(bt_batch b) {
+  if (!b) {
+    set_error("bt_batch_status: NULL plan");
+    return BT_ERR_ARG;
+  }
+  BT_CUDA(cudaDeviceSynchronize());
+  int code = 0;
+  BT_CUDA(cudaMemcpy(&code, reinterpret_cast<int*>(b->d_ctl) + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code != 0) {
+    set_error("bt_batch: a grid-barrier wait of the persistent launch gave up");
+    return BT_ERR_TIMEOUT;
+  }
+  return BT_OK;
+}
+
+bt_status bt_batch_query(bt_batch b, int64_t out[6]) {
+  if (!b || !out) {
+    set_error("bt_batch_query: NULL argument");
+    return BT_ERR_ARG;
+  }
+  out[0] = b->n_items;
+  out[1] = b->n_stages;
+  out[2] = b->grid;
+  out[3] = b->threads;
+  out[4] = b->k_tile;
+  out[5] = b->exec ? 1 : 0;
+  return BT_OK;
+}
+
+void bt_batch_destroy(bt_batch b) { destroy_batch(b); }
+
+bt_status bt_solve_batched(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,
+                           double* const* X, const bt_opts* opts) {
+  bt_batch b = nullptr;
+  BT_TRY(bt_batch_create(n, h, F, K, X, opts, &b));
+  bt_status st = bt_batch_run(b, opts ? opts->stream : nullptr);
+  if (st == BT_OK) {
+    cudaError_t e = cudaStreamSynchronize(opts ? (cudaStream_t)opts->stream : nullptr);
+    if (e != cudaSuccess) st = cuda_fail(e, "bt_solve_batched");
+  }
+  if (st == BT_OK) st = bt_batch_status(b);
+  destroy_batch(b);
+  return st;
+}
+
 
 bt_status bt_handle_query(bt_handle h, int64_t out[6]) {
   if (!h || !out) {

@@ -157,6 +157,29 @@ struct bt_handle_s {
   bt::Profiler prof;
 };
 
+// A batched-solve plan (bt_batch_create): the work-item table of one
+// persistent launch over many right-hand-side sets, its scratch, and the CUDA
+// graph that replays it.
+struct bt_batch_s {
+  int device = 0;
+  int32_t n = 0;
+  int32_t precision = 0;
+  bt::DevArena arena;
+  void* scratch = nullptr;        // series terms of every set
+  void* d_sets = nullptr;         // per-set arguments
+  void* d_items = nullptr;        // work items, grouped by stage
+  int* d_stage_off = nullptr;     // items of stage t: [off[t], off[t+1])
+  int* d_stage_kind = nullptr;
+  void* d_ctl = nullptr;          // grid-barrier counters and the status word
+  int n_stages = 0;
+  int64_t n_items = 0;
+  int CW = 4, threads = 0, grid = 0, k_tile = 0;
+  size_t smem = 0;
+  const void* kernel = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 namespace bt {
 // Records an event pair around one kernel launch when profiling is on.
 struct ProfScope {
@@ -227,6 +250,17 @@ bt_status solve_adjoint(bt_handle_s* h, const double* X, const double* G, int64_
 
 // Builds h->f32 from the FP64 factors (once per handle).
 bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st);
+
+// CTAs of `fn` (threads per CTA, dynamic shared memory) that are resident on
+// the whole current device at once: the grid of a grid-stride kernel, so that
+// it runs in exactly one wave.
+int resident_grid(const void* fn, int threads, size_t smem);
+
+// Batched FP64 solve: builds the item table and launch shape of a plan, and
+// enqueues its persistent launch (used directly and under graph capture).
+bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const double* const* F, const int64_t* K,
+                      double* const* X, const bt_opts& o);
+bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
 
 // Mixed-precision solve with iterative refinement (bt_solve_ex).
 bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info);

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "bt_internal.cuh"
+#include "fpconv.cuh"
 
 namespace bt {
 
@@ -35,7 +36,7 @@ struct IrState {
 template <typename T>
 __device__ __forceinline__ T to_lp(double v);
 template <>
-__device__ __forceinline__ float to_lp<float>(double v) { return (float)v; }
+__device__ __forceinline__ float to_lp<float>(double v) { return f64_to_f32_rz(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
@@ -131,26 +132,25 @@ __global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restric
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   const int64_t tn = (Kp + 31) / 32, tm = (M + 31) / 32;
   const int64_t ntile = tn * tm * N;
-  double acc = 0.0;
-  // grid-stride over 32 x 32 tiles; one partial sum per CTA.  The entry is
-  // rounded to FP32 once (the only FP64 conversion); the stored value and the
-  // squared norm are formed from the FP32 copy on the FP32 pipe.
+  // Five FP64 operations per entry (none with X = 0); the rounding to FP32
+  // and the squared norm (accumulated per thread in FP32, a stopping test
+  // needs a few digits) stay off the FP64 pipe.  Grid-stride over 32 x 32
+  // tiles; one partial sum per CTA.
+  float acc = 0.f;
   __shared__ float ftile[32][33];
   for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
     const int64_t n0 = (q0 % tn) * 32;
     const int m0 = (int)((q0 / tn) % tm) * 32;
     const int64_t j = q0 / (tn * tm);
-    float part = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int m = m0 + ty + 8 * q;
       const int64_t n = n0 + tx;
       float v = 0.f;
-      if (m < M && n < K) v = __double2float_rn(stencil_res(F, X, Cd, N, M, K, j, m, n, first));
-      part = fmaf(v, v, part);
+      if (m < M && n < K) v = f64_to_f32_rz(stencil_res(F, X, Cd, N, M, K, j, m, n, first));
+      acc = fmaf(v, v, acc);
       ftile[ty + 8 * q][tx] = v;
     }
-    acc += (double)part;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restric
     }
     __syncthreads();
   }
-  block_add(acc, first ? &st->fn2 : &st->rn2[pass]);
-  if (first) block_add(acc, &st->rn2[0]);
+  block_add((double)acc, first ? &st->fn2 : &st->rn2[pass]);
+  if (first) block_add((double)acc, &st->rn2[0]);
 }
 
 // r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
@@ -215,7 +215,7 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
       if (TRANS) {
         if (col + c < ldr)
           put_planes(r, ((size_t)j * ldr + col + c) * M + m, (size_t)N * ldr * M, sp,
-                     in ? __double2float_rn(acc[c]) : 0.f);
+                     in ? f64_to_f32_rz(acc[c]) : 0.f);
       } else if (in) {
         r[j * (size_t)M * ldr + (size_t)m * ldr + col + c] = to_lp<TR>(acc[c]);
       }
@@ -276,11 +276,13 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   if (first || h->stencil) {
     if (trans) {
       const int64_t ntile = ((Kp + 31) / 32) * ((M + 31) / 32) * h->N;
-      const int blocks = (int)std::min<int64_t>(ntile, 152 * 8);
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil_t<TR>), 256, 0);
+      const int blocks = (int)std::min<int64_t>(ntile, grid);
       k_resid_stencil_t<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
     } else {
       const size_t n = (size_t)h->N * M * K;
-      const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
+      const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)grid);
       k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st);
     }
   } else {
@@ -379,14 +381,21 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
                           reinterpret_cast<float*>(h->lp_c), X, accumulate, done, s);
   };
 
+  auto check = [&](int pass) {
+    ProfScope ps(h, s, "ir_check");
+    k_ir_check<<<1, 1, 0, s>>>(st, pass, tol2);
+  };
   BT_TRY(residual(1, 0));
-  k_ir_check<<<1, 1, 0, s>>>(st, 0, tol2);
+  check(0);
   BT_TRY(inner(0));
   for (int pass = 1; pass <= max_it + 1; ++pass) {
     BT_TRY(residual(0, pass));
-    k_ir_check<<<1, 1, 0, s>>>(st, pass, tol2);
+    check(pass);
     if (pass <= max_it) {
-      k_count_solve<<<1, 1, 0, s>>>(st);
+      {
+        ProfScope ps(h, s, "ir_check");
+        k_count_solve<<<1, 1, 0, s>>>(st);
+      }
       BT_TRY(inner(1));
     }
   }

@@ -36,6 +36,7 @@
 #include <cstring>
 
 #include "bt_internal.cuh"
+#include "fpconv.cuh"
 #include "tc_ptx.cuh"
 
 namespace bt {
@@ -77,9 +78,17 @@ __host__ __device__ constexpr int pow2ceil(int v) {
   return p;
 }
 
-template <typename E, int M_, int NT_, int NA_, int SP_, int NP_ = 2>
+// SW_ (swapped operand roles): the panel tile is the MMA's A operand (NT = 128
+// rows: the tile's columns n) and the factor block the B operand (N = M: its
+// rows); the accumulator then holds the transposed product -- TMEM lane n,
+// column m' -- and one epilogue thread owns a whole column of the result, so
+// it reads and writes the K-major panel tiles in 16-byte vectors.  Both
+// operands keep the K-major 128-byte-swizzled smem layout of the default
+// roles (factor slice: rows x 128 B; panel tile: NT rows x 128 B per chunk).
+template <typename E, int M_, int NT_, int NA_, int SP_, int NP_ = 2, bool SW_ = false>
 struct Cfg {
   static constexpr int M = M_, NT = NT_, NA = NA_, SP = SP_, NP = NP_;  // NP: panel-ring stages
+  static constexpr bool SW = SW_;
   static constexpr int eb = (int)sizeof(E);
   static constexpr int CE = 128 / eb;      // elements in one 128-byte swizzle row
   static constexpr int KS = 32 / eb;       // K of one MMA instruction
@@ -89,12 +98,16 @@ struct Cfg {
   static constexpr int TCH = NT * 128;     // one tile chunk: NT rows x 128 bytes
   static constexpr int TILE = NCH * TCH;   // one NT x M panel tile of one plane
   static constexpr int PT = SP * TILE;     // a panel tile with all its planes
-  static constexpr int TMEM_COLS = pow2ceil(2 * NT);
-  static constexpr uint32_t IDESC = instr_desc(ET<E>::fmt, 0, M, NT);
-  static constexpr int EG = 2;                  // epilogue warp groups, each drains NT/EG columns
-  static constexpr int NH = NT / EG;
+  static constexpr int ACC = SW ? M : NT;         // TMEM columns of one accumulator buffer
+  static constexpr int TMEM_COLS = pow2ceil(2 * ACC);
+  static constexpr uint32_t IDESC = SW ? instr_desc(ET<E>::fmt, 0, NT, M) : instr_desc(ET<E>::fmt, 0, M, NT);
+  static constexpr int EG = 2;                  // epilogue warp groups, each drains ACC/EG columns
+  static constexpr int NH = NT / EG;            // default roles: tile columns per epilogue thread
+  static constexpr int MH = M / EG;             // swapped roles: block rows per epilogue thread
+  static constexpr int YB = SW ? 1 : 2;         // recurrence-operand buffers of the sweep
   static constexpr int THREADS = 64 + 128 * EG;
   static_assert(NH % 16 == 0, "epilogue column share");
+  static_assert(!SW || (NT == 128 && MH % 32 == 0), "swapped roles: 128-column tiles");
   static_assert(M == 64 || M == 128, "tensor-core path supports M = 64 and M = 128");
   static_assert(NT % 32 == 0 && NT <= 256, "column tile");
   static_assert(TCH % 1024 == 0, "swizzle atoms");
@@ -129,6 +142,92 @@ __device__ __forceinline__ void tile_put(uint8_t* tile, int n, int m, float v) {
     *reinterpret_cast<E*>(tile + C::TILE + o) = lo;
   } else {
     *reinterpret_cast<E*>(tile + o) = ET<E>::from(v);
+  }
+}
+
+// ---- swapped roles: whole rows (one tile column n, block rows m0..m0+MH) of a
+// K-major swizzled tile, 16 bytes at a time.
+template <class C>
+__device__ __forceinline__ uint32_t unit_off(int n, int m) {
+  constexpr int per16 = 16 / C::eb;
+  return (uint32_t)((m / C::CE) * C::TCH + n * 128 + ((((m % C::CE) / per16) ^ (n & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+// 16 bytes of planes 0 (rounded) and 1 (remainder) from per16 FP32 values.
+template <typename E, int SP>
+__device__ __forceinline__ void pack16(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4] = {0u, 0u, 0u, 0u};
+  if constexpr (sizeof(E) == 2) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+      h[q] = bf2_bits(b);
+      if (SP == 2) {
+        const float2 f = __bfloat1622float2(b);
+        l[q] = bf2_bits(__floats2bfloat162_rn(v[2 * q] - f.x, v[2 * q + 1] - f.y));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (SP == 2) {
+        h[q] = __float_as_uint(v[q]) & 0xFFFFE000u;  // exactly a TF32 value
+        l[q] = __float_as_uint(v[q] - __uint_as_float(h[q]));
+      } else {
+        h[q] = __float_as_uint(v[q]);
+      }
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// v[j] += value (n, m0 + j) summed over the planes, from 16-byte units.
+template <typename E, int SP>
+__device__ __forceinline__ void unpack16_add(const uint4& hi, const uint4& lo, float* v) {
+  const uint32_t h[4] = {hi.x, hi.y, hi.z, hi.w}, l[4] = {lo.x, lo.y, lo.z, lo.w};
+  if constexpr (sizeof(E) == 2) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h[q]));
+      if (SP == 2) {
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&l[q]));
+        a.x += b.x;
+        a.y += b.y;
+      }
+      v[2 * q] += a.x;
+      v[2 * q + 1] += a.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += __uint_as_float(h[q]) + (SP == 2 ? __uint_as_float(l[q]) : 0.f);
+  }
+}
+
+template <typename E, class C>
+__device__ __forceinline__ void row_put(uint8_t* tile, int n, int m0, const float (&v)[C::MH]) {
+  constexpr int per16 = 16 / C::eb;
+#pragma unroll
+  for (int u = 0; u < C::MH / per16; ++u) {
+    uint4 hi, lo;
+    pack16<E, C::SP>(&v[u * per16], hi, lo);
+    const uint32_t o = unit_off<C>(n, m0 + u * per16);
+    *reinterpret_cast<uint4*>(tile + o) = hi;
+    if (C::SP == 2) *reinterpret_cast<uint4*>(tile + C::TILE + o) = lo;
+  }
+}
+
+template <typename E, class C>
+__device__ __forceinline__ void row_add(const uint8_t* tile, int n, int m0, float (&v)[C::MH]) {
+  constexpr int per16 = 16 / C::eb;
+#pragma unroll
+  for (int u = 0; u < C::MH / per16; ++u) {
+    const uint32_t o = unit_off<C>(n, m0 + u * per16);
+    const uint4 hi = *reinterpret_cast<const uint4*>(tile + o);
+    const uint4 lo = C::SP == 2 ? *reinterpret_cast<const uint4*>(tile + C::TILE + o) : make_uint4(0, 0, 0, 0);
+    unpack16_add<E, C::SP>(hi, lo, &v[u * per16]);
   }
 }
 
@@ -264,11 +363,21 @@ __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& 
 #pragma unroll
     for (int kq = 0; kq < C::CE / C::KS; ++kq) {
       const uint32_t boff = btile + c * C::TCH + kq * 32;
-      mma1<E>(dtmem, smem_desc(ahi + kq * 32, 16, 1024), smem_desc(boff, 16, 1024), C::IDESC, !first);
-      first = false;
-      if (C::SP == 2) {
-        mma1<E>(dtmem, smem_desc(ahi + kq * 32, 16, 1024), smem_desc(boff + C::TILE, 16, 1024), C::IDESC, true);
-        mma1<E>(dtmem, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), smem_desc(boff, 16, 1024), C::IDESC, true);
+      const uint64_t fhi = smem_desc(ahi + kq * 32, 16, 1024), phi = smem_desc(boff, 16, 1024);
+      if constexpr (C::SW) {
+        mma1<E>(dtmem, phi, fhi, C::IDESC, !first);
+        first = false;
+        if (C::SP == 2) {
+          mma1<E>(dtmem, smem_desc(boff + C::TILE, 16, 1024), fhi, C::IDESC, true);
+          mma1<E>(dtmem, phi, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), C::IDESC, true);
+        }
+      } else {
+        mma1<E>(dtmem, fhi, phi, C::IDESC, !first);
+        first = false;
+        if (C::SP == 2) {
+          mma1<E>(dtmem, fhi, smem_desc(boff + C::TILE, 16, 1024), C::IDESC, true);
+          mma1<E>(dtmem, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), phi, C::IDESC, true);
+        }
       }
     }
     if (sh.csize == 1)
@@ -319,7 +428,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLOT;
   uint8_t* sY = sP + C::NP * C::PT;
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + 2 * C::PT);
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + C::YB * C::PT);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
 
@@ -387,7 +496,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       for (int t = 0; t < T && ok; ++t) {
         const bool fwd = t < nrow;
         const int bsel = t & 1;
-        const uint32_t dt = tmem + bsel * C::NT;
+        const uint32_t dt = tmem + bsel * C::ACC;
+        const uint32_t yop = smem_u32(sY + (C::YB == 2 ? ((t - 1) & 1) : 0) * C::PT);  // y_{t-1} / W_{i+1}
         if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
         tc_fence_after();
         bool first = true;
@@ -400,12 +510,12 @@ __global__ void __launch_bounds__(C::THREADS, 1)
           if (ok && t > 0) {
             ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
             tc_fence_after();
-            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first, sh);
+            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first, sh);
           }
         } else if (ok) {
           ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY + ((t - 1) & 1) * C::PT), first, sh);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first, sh);
         }
         if (ok) {
           mma_commit(&b.mdone[bsel]);
@@ -420,6 +530,65 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       mma_commit(&b.extra[1]);
       mbar_wait(&b.extra[1], 0);
     }
+  } else if constexpr (C::SW) {
+    // epilogue, swapped roles: thread <-> tile column n (TMEM lane), group g
+    // drains block rows [g*MH, (g+1)*MH) of it
+    constexpr int ET_THREADS = 128 * C::EG;
+    const int n = 32 * (warp & 3) + lane;
+    const int m0 = ((warp - 2) / 4) * C::MH;
+    const bool leader = (warp == 2 && lane == 0);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    uint32_t pe = (uint32_t)nrow;
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const bool fwd = t < nrow;
+      const int o = fwd ? t : nrow - 2 - (t - nrow);
+      const int i = a + o;
+      const int bsel = t & 1;
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      float v[C::MH];
+      if (ok) {
+        tmem_cols<C::MH>(tmem + lane_base + bsel * C::ACC + m0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      if (!fwd) {
+        const uint32_t ps = pe % C::NP;
+        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / C::NP) & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) row_add<E, C>(sP + ps * C::PT, n, m0, v);  // + y_i
+        named_bar_sync(1, ET_THREADS);
+        if (ok && leader) mbar_arrive(&b.emptyP[ps]);
+        ++pe;
+      }
+      // one y buffer: the previous row's store must have read it (its MMA
+      // finished before mdone of this row)
+      if (leader) tma_store_wait_read<0>();
+      named_bar_sync(1, ET_THREADS);
+      if (ok) row_put<E, C>(sY, n, m0, v);
+      fence_proxy_async_smem();
+      named_bar_sync(1, ET_THREADS);
+      if (leader && ok) {
+        mbar_arrive(&b.yrdy[bsel]);
+        for (int p = 0; p < C::SP; ++p)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_store_2d(&tm_w, c * C::CE, p * pplane + i * Kp + n0, sY + p * C::TILE + c * C::TCH);
+        tma_store_commit();
+        if (t == nrow - 1) {
+          tma_store_wait<0>();
+          fence_proxy_async_all();
+          mbar_arrive(&b.extra[0]);
+        }
+      }
+    }
+    if (leader) tma_store_wait<0>();
+    if (!ok && leader) atomicExch(status, 3);
   } else {
     // epilogue: EG groups of 4 warps; thread <-> accumulator row, group g
     // drains columns [g*NH, (g+1)*NH)
@@ -508,18 +677,22 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
-                 const __grid_constant__ CUtensorMap tm_d, int N, int L, int S, int Kp, int rows_per_cta, int csize,
-                 const int* done, int* status) {
+                 const __grid_constant__ CUtensorMap tm_d, const E* __restrict__ wp, float* __restrict__ dp, int N,
+                 int L, int S, int Kp, int rows_per_cta, int csize, const int* done, int* status) {
   if (flag_set(done)) return;
   using CF = Cfg<float, C::M, C::NT, 1, 1>;      // layout of one FP32 d tile
   constexpr int DT = CF::TILE;                    // bytes of one d tile
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  // swapped roles: no staging of W or d in shared memory (the epilogue reads
+  // and writes whole rows of them in 16-byte vectors)
+  constexpr int NPS = C::SW ? 0 : C::NP;
+  constexpr int NDS = C::SW ? 0 : 2;
   uint8_t* sA = sm;
   uint8_t* sP = sA + C::NA * C::SLOT;
-  uint8_t* sB = sP + C::NP * C::PT;  // X~_s, X~_{s+1} (all planes each)
-  uint8_t* sD = sB + 2 * C::PT;  // two FP32 d tiles
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(sD + 2 * DT);
+  uint8_t* sB = sP + NPS * C::PT;  // X~_s, X~_{s+1} (all planes each)
+  uint8_t* sD = sB + 2 * C::PT;    // two FP32 d tiles
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sD + NDS * DT);
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
 
@@ -567,7 +740,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       uint32_t ai = 0, pi = 0;
       for (int t = 0; t < T && ok; ++t) {
         const int i = r0 + t;
-        ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
+        if constexpr (!C::SW) ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
           ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
         if (has_next)
@@ -592,7 +765,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       uint32_t ai = 0;
       for (int t = 0; t < T && ok; ++t) {
         const int bsel = t & 1;
-        const uint32_t dt = tmem + bsel * C::NT;
+        const uint32_t dt = tmem + bsel * C::ACC;
         if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
         tc_fence_after();
         bool first = true;
@@ -604,6 +777,59 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       mma_commit(&b.extra[1]);
       mbar_wait(&b.extra[1], 0);
     }
+  } else if constexpr (C::SW) {
+    // swapped roles: thread <-> tile column n; W_i read and d_i written as
+    // whole rows straight from / to global memory
+    constexpr int per16 = 16 / C::eb;
+    constexpr int NU = C::MH / per16;  // 16-byte units of one plane of a row share
+    const int nl = 32 * (warp & 3) + lane;
+    const int m0 = ((warp - 2) / 4) * C::MH;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const size_t wplane = (size_t)N * Kp * C::M;
+    bool ok = mbar_wait(&b.extra[0], 0);
+    ok = __all_sync(0xffffffffu, ok);
+    auto put_d = [&](const float (&v)[C::MH], int irow) {
+      float4* o = reinterpret_cast<float4*>(dp + ((size_t)irow * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int q = 0; q < C::MH / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    };
+    if (do_iface && ok) {
+      float v[C::MH];
+#pragma unroll
+      for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      row_add<E, C>(sB, nl, m0, v);  // d_{k_s} = X~_s
+      put_d(v, s * L);
+    }
+    for (int t = 0; t < T; ++t) {
+      const int i = r0 + t;
+      const int bsel = t & 1;
+      // W_i row share, fetched before the wait so its latency overlaps the MMAs
+      uint4 whi[NU], wlo[NU];
+      const uint4* wsrc = reinterpret_cast<const uint4*>(wp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        whi[u] = __ldg(wsrc + u);
+        wlo[u] = C::SP == 2 ? __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(wsrc) + wplane) + u)
+                            : make_uint4(0, 0, 0, 0);
+      }
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      float v[C::MH];
+      if (ok) {
+        tmem_cols<C::MH>(tmem + lane_base + bsel * C::ACC + m0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) unpack16_add<E, C::SP>(whi[u], wlo[u], &v[u * per16]);
+      if (ok) put_d(v, i);
+    }
+    if (!ok && threadIdx.x == 64) atomicExch(status, 6);
   } else {
     constexpr int ET_THREADS = 128 * C::EG;
     int row;
@@ -706,7 +932,7 @@ __global__ void __launch_bounds__(256) k_x_update(const float* __restrict__ d, d
       const int m = m0 + ty + 8 * q, n = n0 + tx;
       if (m < M && n < K) {
         double* o = X + (size_t)j * MK + (size_t)m * K + n;
-        const double v = (double)tile[tx][ty + 8 * q];
+        const double v = f32_to_f64(tile[tx][ty + 8 * q]);  // exact, on the integer pipe
         *o = accumulate ? *o + v : v;
       }
     }
@@ -937,12 +1163,12 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
 
 template <class C>
 size_t sweep_smem() {
-  return 1024 + C::NA * C::SLOT + (C::NP + 2) * C::PT + kBars(C::NA, C::NP) * 8 + 16;
+  return 1024 + C::NA * C::SLOT + (C::NP + C::YB) * C::PT + kBars(C::NA, C::NP) * 8 + 16;
 }
 template <class C>
 size_t correct_smem() {
-  return 1024 + C::NA * C::SLOT + C::NP * C::PT + 2 * C::PT + 2 * (size_t)C::NT * C::M * 4 + kBars(C::NA, C::NP) * 8 +
-         16;
+  const size_t staging = C::SW ? 0 : C::NP * C::PT + 2 * (size_t)C::NT * C::M * 4;
+  return 1024 + C::NA * C::SLOT + 2 * C::PT + staging + kBars(C::NA, C::NP) * 8 + 16;
 }
 
 // CS: configuration of the sweep kernel, CC: of the correction kernel.
@@ -1032,13 +1258,14 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       cfg.stream = st;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_correct<E, CC>, tm_fac_c, tm_wc, tm_d, N, L, S, Kp, L > 1 ? rpc : 0,
-                                 cs_corr, done, status));
+      BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_correct<E, CC>, tm_fac_c, tm_wc, tm_d, (const E*)w, tb.d, N, L, S, Kp,
+                                 L > 1 ? rpc : 0, cs_corr, done, status));
     }
     BT_CUDA(cudaGetLastError());
     {
       const int64_t ntile = (int64_t)((K + 31) / 32) * ((M + 31) / 32) * N;
-      const int blocks = (int)std::min<int64_t>(ntile, 152 * 8);
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update), 256, 0);
+      const int blocks = (int)std::min<int64_t>(ntile, grid);
       ProfScope ps(h, st, "x_update");
       k_x_update<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
     }

@@ -165,3 +165,72 @@ def factor(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, S: int,
                                    ctypes.byref(h))
     _lib.check(st, "bt_factor")
     return Factorization(h, dev)
+
+
+def _batch_arrays(facs, Fs, Xs):
+    n = len(facs)
+    if not (len(Fs) == len(Xs) == n) or n < 1:
+        raise ValueError("need one F and one X per factorization, n >= 1")
+    H = (ctypes.c_void_p * n)(*[f._h.value for f in facs])
+    Fp = (ctypes.c_void_p * n)()
+    Xp = (ctypes.c_void_p * n)()
+    K = (ctypes.c_int64 * n)()
+    for i, (f, F, X) in enumerate(zip(facs, Fs, Xs)):
+        F = _as_device_f64(f._panel(F, "F"), f.device, "F")
+        X = f._panel(X, "X")
+        if X.dtype != torch.float64 or X.device != f.device or not X.is_contiguous() or X.shape != F.shape:
+            raise ValueError("X must be a contiguous float64 CUDA tensor shaped like F")
+        Fp[i], Xp[i], K[i] = F.data_ptr(), X.data_ptr(), F.shape[2]
+    return H, Fp, K, Xp
+
+
+class BatchPlan:
+    """A planned batch of solves (bt_batch_*): set i solves facs[i] X_i = F_i.
+
+    The plan records the tensors' device addresses: keep F and X alive and in
+    place while it is used.  run() enqueues one persistent launch (a CUDA
+    graph replay) on the current stream."""
+
+    def __init__(self, facs, Fs, Xs, k_tile: int = 0):
+        self.facs, self.Fs, self.Xs = list(facs), list(Fs), list(Xs)  # keep alive
+        self.device = self.facs[0].device
+        H, Fp, K, Xp = _batch_arrays(self.facs, self.Fs, self.Xs)
+        opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=None, k_tile=int(k_tile), reserved=0)
+        self._b = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().bt_batch_create(len(self.facs), H, Fp, K, Xp, ctypes.byref(opts),
+                                                   ctypes.byref(self._b)), "bt_batch_create")
+        q = (ctypes.c_int64 * 6)()
+        _lib.check(_lib.load().bt_batch_query(self._b, q), "bt_batch_query")
+        self.items, self.stages, self.ctas, self.threads, self.k_tile, self.graph = (int(v) for v in q)
+
+    def run(self, stream: Optional[torch.cuda.Stream] = None):
+        _lib.check(_lib.load().bt_batch_run(self._b, _stream_ptr(stream, self.device)), "bt_batch_run")
+
+    def status(self):
+        """Waits for the plan's work; raises if a bounded grid-barrier wait gave up."""
+        _lib.check(_lib.load().bt_batch_status(self._b), "bt_batch_status")
+
+    def close(self):
+        if self._b is not None and self._b.value:
+            _lib.load().bt_batch_destroy(self._b)
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(facs, Fs, Xs=None, k_tile: int = 0, stream: Optional[torch.cuda.Stream] = None):
+    """X_i = P_i^{-1} F_i for every set i in one persistent launch (FP64, bt_solve_batched)."""
+    if Xs is None:
+        Xs = [torch.empty_like(F) for F in Fs]
+    H, Fp, K, Xp = _batch_arrays(facs, Fs, Xs)
+    dev = facs[0].device
+    opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=_stream_ptr(stream, dev), k_tile=int(k_tile),
+                       reserved=0)
+    with torch.cuda.device(dev):
+        _lib.check(_lib.load().bt_solve_batched(len(facs), H, Fp, K, Xp, ctypes.byref(opts)), "bt_solve_batched")
+    return Xs

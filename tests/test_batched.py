@@ -1,0 +1,133 @@
+"""Batched FP64 solves (bt_batch_*, bt_solve_batched) vs the CPU oracle (GPU only).
+
+Many right-hand-side sets of uneven K against several factored matrices run
+as one persistent launch replayed from a CUDA graph.  Every set must match the
+FP64 oracle to 1e-12 relative error, the bar of the plain FP64 method.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1108_4181_gb300 as bt
+
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    return bt
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _factors(bt, mats, Ss):
+    return [bt.factor(_t(A), _t(B), _t(C), S) for (A, B, C), S in zip(mats, Ss)]
+
+
+def _check(mats, sets, Xs):
+    for st, X in zip(sets, Xs):
+        A, B, C = mats[st.matrix]
+        Xr = oracle.solve_block_thomas(A, B, C, st.F)
+        err = oracle.rel_err(X.cpu().numpy(), Xr)
+        assert err <= TOL, (st.K, err)
+
+
+@pytest.mark.parametrize("S_list", [(8, 16, 4), (1, 64, 2)])
+def test_batched_uneven_sets_match_oracle(bt, S_list):
+    # three matrices with different segment counts (S = 1 and S = N included),
+    # eleven sets with K from 1 to 70 (several column tiles, ragged tails)
+    N, M = 64, 8
+    mats = [gen.dominant_blocks(N, M, seed) for seed in (1, 2, 3)]
+    Ks = [1, 2, 3, 5, 8, 9, 17, 33, 64, 70, 4]
+    sets = [gen.RhsSet(matrix=i % 3, K=k, F=gen.uniform_rhs(N, M, k, seed=50 + i)) for i, k in enumerate(Ks)]
+    facs = _factors(bt, mats, S_list)
+    Fs = [_t(s.F) for s in sets]
+    Xs = bt.solve_batched([facs[s.matrix] for s in sets], Fs)
+    torch.cuda.synchronize()
+    _check(mats, sets, Xs)
+
+
+def test_batched_plan_replays_graph(bt):
+    # a plan is built once and replayed; new values in the same F buffers give
+    # new solutions, and the launch is a single persistent cooperative kernel
+    N, M = 128, 16
+    mats = [gen.dominant_blocks(N, M, seed) for seed in (4, 5)]
+    Ks = [7, 40, 1, 129]
+    sets = [gen.RhsSet(matrix=i % 2, K=k, F=gen.uniform_rhs(N, M, k, seed=70 + i)) for i, k in enumerate(Ks)]
+    facs = _factors(bt, mats, (16, 32))
+    Fs = [_t(s.F) for s in sets]
+    Xs = [torch.empty_like(F) for F in Fs]
+    plan = bt.BatchPlan([facs[s.matrix] for s in sets], Fs, Xs)
+    assert plan.graph == 1
+    assert plan.items > 0 and plan.stages >= 3 and plan.ctas >= 1
+    plan.run()
+    plan.status()
+    _check(mats, sets, Xs)
+    sets2 = [gen.RhsSet(matrix=s.matrix, K=s.K, F=gen.uniform_rhs(N, M, s.K, seed=90 + i)) for i, s in enumerate(sets)]
+    for F, s in zip(Fs, sets2):
+        F.copy_(_t(s.F))
+    for _ in range(3):
+        plan.run()
+    plan.status()
+    _check(mats, sets2, Xs)
+    plan.close()
+
+
+@pytest.mark.parametrize("k_tile", [4, 16, 32])
+def test_batched_tile_choices(bt, k_tile):
+    N, M = 64, 16
+    mats = [gen.dominant_blocks(N, M, 9)]
+    sets = [gen.RhsSet(matrix=0, K=k, F=gen.uniform_rhs(N, M, k, seed=k)) for k in (3, 31, 45)]
+    facs = _factors(bt, mats, (8,))
+    Xs = bt.solve_batched([facs[0]] * 3, [_t(s.F) for s in sets], k_tile=k_tile)
+    torch.cuda.synchronize()
+    _check(mats, sets, Xs)
+
+
+def test_batched_config3_shape_sampled(bt):
+    # the uneven-set workload at full matrix size (N = 2048, M = 64, four
+    # matrices); 16 of its 64 sets, checked on sampled columns
+    mats, sets = gen.config3(n_sets=16)
+    facs = _factors(bt, mats, (64, 64, 64, 64))
+    Fs = [_t(s.F) for s in sets]
+    Xs = bt.solve_batched([facs[s.matrix] for s in sets], Fs)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for st, X in zip(sets, Xs):
+        cols = sorted(set(rng.integers(0, st.K, size=min(3, st.K)).tolist()))
+        A, B, C = mats[st.matrix]
+        Xr = oracle.solve_block_thomas(A, B, C, st.F[:, :, cols])
+        err = oracle.rel_err(X[:, :, cols].cpu().numpy(), Xr)
+        assert err <= TOL, (st.K, err)
+
+
+def test_batched_rejects_bad_input(bt):
+    N = 32
+    f8 = bt.factor(*(_t(a) for a in gen.dominant_blocks(N, 8, 1)), 4)
+    f4 = bt.factor(*(_t(a) for a in gen.dominant_blocks(N, 4, 1)), 4)
+    F8 = _t(gen.uniform_rhs(N, 8, 3, seed=1))
+    F4 = _t(gen.uniform_rhs(N, 4, 3, seed=1))
+    with pytest.raises(bt.BtError) as e:
+        bt.solve_batched([f8, f4], [F8, F4])  # block sizes differ
+    assert e.value.name == "BT_ERR_ARG"
+    with pytest.raises(bt.BtError) as e:
+        bt.solve_batched([f8, f8], [F8, F8], [F8, torch.empty_like(F8)])  # X overlaps F
+    assert e.value.name == "BT_ERR_ARG"
+    X = torch.empty_like(F8)
+    with pytest.raises(bt.BtError) as e:
+        bt.solve_batched([f8, f8], [F8, torch.empty_like(F8)], [X, X])  # two outputs share memory
+    assert e.value.name == "BT_ERR_ARG"

@@ -97,7 +97,8 @@ TC = ["bf16", "tf32", "bf16x3"]
 @pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("N,M,K,S", [
     (64, 64, 20, 8),     # one column tile, ragged
-    (48, 128, 70, 6),    # M = 128, two column tiles with a ragged tail
+    (48, 128, 70, 6),    # M = 128, one ragged column tile
+    (24, 128, 300, 3),   # M = 128, three 128-column tiles, the last ragged
     (40, 64, 130, 20),   # L = 2: one interior row per segment
     (32, 128, 33, 32),   # S = N: every row an interface (no sweep)
     (96, 64, 1, 1),      # S = 1, single right-hand side
