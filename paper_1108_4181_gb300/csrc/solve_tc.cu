@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "bt_internal.cuh"
@@ -1183,7 +1184,16 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   // (measured on the acoustic workload: sharing through clusters of 2-4 made the
   // sweep slower -- the kernels are latency-bound, not L2-bound -- so every
   // CTA loads its own slices; the multicast path stays for other shapes)
-  auto pick_cluster = [](int ntiles) { (void)ntiles; return 1; };
+  // BT_TC_CLUSTER (1, 2 or 4; default 1) overrides the cluster size when it
+  // divides the number of column tiles.
+  auto pick_cluster = [](int ntiles) {
+    static const int want = [] {
+      const char* e = std::getenv("BT_TC_CLUSTER");
+      const int v = e ? std::atoi(e) : 1;
+      return (v == 2 || v == 4) ? v : 1;
+    }();
+    return (ntiles % want == 0) ? want : 1;
+  };
   const int cs_sweep = pick_cluster(Kp / CS::NT), cs_corr = pick_cluster(Kp / CC::NT);
   BT_TRY(make_map(&tm_fac_s, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M / cs_sweep));
   BT_TRY(make_map(&tm_fac_c, tb.fac, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CC::CE, M / cs_corr));
@@ -1286,8 +1296,8 @@ using SwB64 = Cfg<__nv_bfloat16, 64, 128, 16, 1, 4>;
 using CoB64 = Cfg<__nv_bfloat16, 64, 64, 8, 1, 4>;
 using SwT64 = Cfg<float, 64, 64, 16, 1, 4>;
 using CoT64 = Cfg<float, 64, 64, 8, 1, 4>;
-using SwX128 = Cfg<__nv_bfloat16, 128, 64, 3, 2, 2>;
-using CoX128 = Cfg<__nv_bfloat16, 128, 32, 3, 2, 4>;
+using SwX128 = Cfg<__nv_bfloat16, 128, 128, 3, 2, 1, true>;
+using CoX128 = Cfg<__nv_bfloat16, 128, 128, 3, 2, 1, true>;
 using SwX64 = Cfg<__nv_bfloat16, 64, 64, 8, 2, 4>;
 using CoX64 = Cfg<__nv_bfloat16, 64, 64, 6, 2, 4>;
 
