@@ -198,8 +198,10 @@ def _kernel_work(name, prof, steps, info, precision):
     pb = planes * eb  # bytes of one panel entry
     fb = planes * eb * M * M  # bytes of one factor block
     if name == "tc_sweep":
-        # r in, W out (panels), Dinv, E, G per interior row
-        return "hbm", full * (2.0 * pb * NMK + 3.0 * fb * (N - S)), "B"
+        # forward: r in, y out; backward: y in, W out (the y panel of a
+        # segment exceeds on-chip memory, so it makes one round trip); Dinv,
+        # E, G per interior row
+        return "hbm", full * (4.0 * pb * NMK + 3.0 * fb * (N - S)), "B"
     if name == "tc_correct":
         # W in, d (FP32) out, U, V per interior row
         return "hbm", full * ((pb + 4.0) * NMK + 2.0 * fb * (N - S)), "B"

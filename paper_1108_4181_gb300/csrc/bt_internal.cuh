@@ -144,6 +144,12 @@ struct bt_handle_s {
   void* tc_fac_bf16 = nullptr;
   void* tc_fac_tf32 = nullptr;
   void* tc_fac_bf16x3 = nullptr;  // [2][5][N][M][M]: rounded values and their remainders
+  // Split-BF16 copies of the interface blocks for the tensor-core step 2.2,
+  // [2][AK (S), BK (S), R (depth*S), HL (S), HR (S)][M][M], and the job table of
+  // that step (device; host offsets: F~ jobs, series-term jobs, one group per level).
+  void* tc_if_bf16x3 = nullptr;
+  void* if_jobs = nullptr;
+  std::vector<int> if_off;
 
   // Refinement buffers (grown on demand): residual panel, work panel,
   // series terms and the device-side refinement state.

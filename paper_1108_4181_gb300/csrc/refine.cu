@@ -351,7 +351,8 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     eb = prec == BT_PREC_TF32 ? 4 : 2;
   }
   const size_t panel = (size_t)sp * h->N * M * Kp * eb;
-  const size_t cbytes = (size_t)h->depth * h->S * M * Kp * sizeof(float);
+  // series terms [depth][S] and, for the tensor-core step 2.2, one node sum per tree node
+  const size_t cbytes = ((size_t)h->depth * h->S + h->nodes.size()) * M * Kp * sizeof(float);
   BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
   BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));

@@ -780,7 +780,9 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     }
   } else if constexpr (C::SW) {
     // swapped roles: thread <-> tile column n; W_i read and d_i written as
-    // whole rows straight from / to global memory
+    // whole row shares straight from / to global memory (an FP64 update of X
+    // here, with the 8 epilogue warps of a CTA, measured 2.7x slower than the
+    // separate streaming update)
     constexpr int per16 = 16 / C::eb;
     constexpr int NU = C::MH / per16;  // 16-byte units of one plane of a row share
     const int nl = 32 * (warp & 3) + lane;
@@ -903,6 +905,165 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     cluster_sync();  // no CTA leaves while another may still signal it
   else
     __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ======================================================================
+// Step 2.2 on the tensor cores (swapped roles): one job per CTA row of the
+// grid, one 128-column tile per CTA column.  A job computes
+//   v = sum_p  T_p B_p  (+ r panel row)  (+ sum of series terms)
+// with up to two products of a work-panel tile T_p (A operand) and an
+// interface block B_p (B operand), and writes v to a work-panel row and/or
+// an FP32 series-term row.  The three uses, in launch order:
+//   F~_s = r_{k_s} + A_{k_s} W_{k_s - 1} + B_{k_s} W_{k_s + 1}  -> panel row k_s (eq. red1)
+//   c[l][s] = R[l][s] F~_s                                      -> series terms
+//   X~_m = sum_{j in node} c[l][j] + HL_m X~_{l-1} + HR_m X~_{r+1} -> panel row k_m
+// (one launch per tree level, Algorithm 1; the node sums of the series terms
+// come from k_node_sums, one tile per node).  Series terms are FP32, laid out
+// [depth * S][Kp][M] so one thread reads and writes a contiguous row share.
+// ======================================================================
+struct IfJob {
+  int32_t a[2];      // work-panel block rows of the A operands (-1: absent)
+  int32_t b[2];      // interface block index paired with a[p]
+  int32_t add_r;     // r-panel block row added to the result (-1: none)
+  int32_t sum_lev;   // series terms c[sum_lev][sum_lo..sum_hi] added (sum_lo > sum_hi: none)
+  int32_t sum_lo, sum_hi;
+  int32_t out_w;     // work-panel block row receiving the result (-1: none)
+  int32_t out_c;     // series-term slot (level * S + s) receiving the result (-1: none)
+};
+
+template <typename E, class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+    k_tc_ifgemm(const __grid_constant__ CUtensorMap tm_if, const __grid_constant__ CUtensorMap tm_w,
+                const IfJob* __restrict__ jobs, int job0, const E* __restrict__ rp, E* __restrict__ wp,
+                float* __restrict__ cp, const float* __restrict__ sumbase, int N, int S, int nblk, int Kp,
+                const int* done, int* status) {
+  static_assert(C::SW, "swapped roles only");
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;                    // interface-block slices (B operands)
+  uint8_t* sT = sA + C::NA * C::SLOT;  // up to two panel tiles (A operands)
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sT + 2 * C::PT);
+  const Bars b = carve<C>(barmem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const IfJob jb = jobs[job0 + blockIdx.y];
+  const int np = (jb.a[0] >= 0 ? 1 : 0) + (jb.a[1] >= 0 ? 1 : 0);
+  const int pplane = N * Kp;
+  const Share sh{1, 0, 1};
+  if (threadIdx.x == 0) init_bars<C>(b, 1);
+  if (warp == 1) {
+    tmem_alloc(tslot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0 && np > 0) {
+      prefetch_tmap(&tm_if);
+      prefetch_tmap(&tm_w);
+      mbar_arrive_expect_tx(&b.extra[0], np * C::PT);
+      int k = 0;
+      for (int p = 0; p < 2; ++p) {
+        if (jb.a[p] < 0) continue;
+        for (int pl = 0; pl < C::SP; ++pl)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_load_2d(sT + k * C::PT + pl * C::TILE + c * C::TCH, &tm_w, c * C::CE,
+                        pl * pplane + jb.a[p] * Kp + n0, &b.extra[0]);
+        ++k;
+      }
+      uint32_t ai = 0;
+      bool ok = true;
+      for (int p = 0; p < 2 && ok; ++p) {
+        if (jb.a[p] < 0) continue;
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_if, c * C::CE, jb.b[p] * C::M, nblk * C::M, sh);
+      }
+      if (!ok) atomicExch(status, 7);
+      mbar_wait(&b.extra[0], 0);
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = ai - 1 - q;
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && np > 0) {
+      bool ok = mbar_wait(&b.extra[0], 0);
+      tc_fence_after();
+      uint32_t ai = 0;
+      bool first = true;
+      for (int k = 0; k < np && ok; ++k) ok = mma_block<E, C>(sA, b, ai, tmem, smem_u32(sT + k * C::PT), first, sh);
+      if (ok) mma_commit(&b.mdone[0]);
+      if (!ok) atomicExch(status, 8);
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    constexpr int per16 = 16 / C::eb;
+    constexpr int NU = C::MH / per16;
+    const int nl = 32 * (warp & 3) + lane;
+    const int m0 = ((warp - 2) / 4) * C::MH;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const size_t wplane = (size_t)N * Kp * C::M;
+    float v[C::MH];
+#pragma unroll
+    for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+    bool ok = true;
+    if (np > 0) {
+      ok = mbar_wait(&b.mdone[0], 0);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      if (ok) tmem_cols<C::MH>(tmem + lane_base + m0, v);
+      tc_fence_before();
+    }
+    if (jb.add_r >= 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(rp + ((size_t)jb.add_r * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const uint4 hi = __ldg(src + u);
+        const uint4 lo = C::SP == 2 ? __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(src) + wplane) + u)
+                                    : make_uint4(0, 0, 0, 0);
+        unpack16_add<E, C::SP>(hi, lo, &v[u * per16]);
+      }
+    }
+    for (int j = jb.sum_lo; j <= jb.sum_hi; ++j) {
+      const float4* src =
+          reinterpret_cast<const float4*>(sumbase + (((size_t)jb.sum_lev * S + j) * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int q = 0; q < C::MH / 4; ++q) {
+        const float4 t = __ldg(src + q);
+        v[4 * q] += t.x;
+        v[4 * q + 1] += t.y;
+        v[4 * q + 2] += t.z;
+        v[4 * q + 3] += t.w;
+      }
+    }
+    if (ok && jb.out_w >= 0) {
+      uint4* dst = reinterpret_cast<uint4*>(wp + ((size_t)jb.out_w * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        uint4 hi, lo;
+        pack16<E, C::SP>(&v[u * per16], hi, lo);
+        dst[u] = hi;
+        if (C::SP == 2) reinterpret_cast<uint4*>(reinterpret_cast<E*>(dst) + wplane)[u] = lo;
+      }
+    }
+    if (ok && jb.out_c >= 0) {
+      float4* dst = reinterpret_cast<float4*>(cp + ((size_t)jb.out_c * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int q = 0; q < C::MH / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    if (!ok && threadIdx.x == 64) atomicExch(status, 9);
+  }
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -1162,6 +1323,172 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
   }
 }
 
+// Split-BF16 copy of n FP64 values: plane 0 at dst, plane 1 (remainder) at dst + plane.
+__global__ void k_cast_split(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n, size_t plane) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[e];
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    dst[e] = hi;
+    dst[e + plane] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+  }
+}
+
+// Sum of the series terms of every tree node, sum_{j = l..r} c[level][j], into
+// csum[q] ([Kp][M] FP32 per node q): one CTA per (1024-entry chunk, node).
+__global__ void __launch_bounds__(256) k_node_sums(const float* __restrict__ c, float* __restrict__ csum,
+                                                   const int* __restrict__ nodes, const int* __restrict__ mid_level,
+                                                   int S, size_t tile, const int* done) {
+  if (flag_set(done)) return;
+  const int q = blockIdx.y;
+  const int l = nodes[3 * q], r = nodes[3 * q + 1], lev = mid_level[nodes[3 * q + 2]];
+  const size_t e = (size_t)blockIdx.x * 1024 + 4 * threadIdx.x;
+  if (e >= tile) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* src = c + ((size_t)lev * S + l) * tile + e;
+#pragma unroll 8
+  for (int j = l; j <= r; ++j, src += tile) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(src));
+    acc.x += t.x;
+    acc.y += t.y;
+    acc.z += t.z;
+    acc.w += t.w;
+  }
+  *reinterpret_cast<float4*>(csum + (size_t)q * tile + e) = acc;
+}
+
+// Interface blocks for the tensor-core step 2.2 and its job table (once per handle).
+bt_status make_tc_interface(bt_handle_s* h, cudaStream_t st) {
+  if (h->tc_if_bf16x3) return BT_OK;
+  const int S = (int)h->S, L = (int)h->L, N = (int)h->N, depth = h->depth;
+  const size_t MM = (size_t)h->M * h->M;
+  const size_t nblk = (size_t)(4 + depth) * S;
+  void* buf = nullptr;
+  BT_TRY(h->arena.alloc(&buf, 2 * nblk * MM * sizeof(__nv_bfloat16)));
+  __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(buf);
+  const size_t plane = nblk * MM;
+  struct Src {
+    const double* p;
+    size_t nb;
+  } srcs[] = {{h->AK, (size_t)S}, {h->BK, (size_t)S}, {h->R, (size_t)depth * S}, {h->HL, (size_t)S}, {h->HR, (size_t)S}};
+  size_t at = 0;
+  for (const Src& q : srcs) {
+    k_cast_split<<<512, 256, 0, st>>>(q.p, d + at * MM, q.nb * MM, plane);
+    at += q.nb;
+  }
+  BT_CUDA(cudaGetLastError());
+  // jobs: F~ per interface, series terms per (interface, level), nodes per level
+  std::vector<int> top(S, 0);
+  for (const TreeNode& nd : h->nodes) top[nd.m] = nd.level;
+  std::vector<IfJob> jobs;
+  auto blank = [] {
+    IfJob j;
+    j.a[0] = j.a[1] = -1;
+    j.b[0] = j.b[1] = 0;
+    j.add_r = -1;
+    j.sum_lev = 0;
+    j.sum_lo = 0;
+    j.sum_hi = -1;
+    j.out_w = -1;
+    j.out_c = -1;
+    return j;
+  };
+  h->if_off.assign(1, 0);
+  for (int s = 0; s < S; ++s) {
+    IfJob j = blank();
+    if (s > 0 && L > 1) {
+      j.a[0] = s * L - 1;  // W_{k_s - 1}: last interior row of segment s-1
+      j.b[0] = s;          // A_{k_s}
+    }
+    if (s * L + 1 < N && L > 1) {
+      j.a[1] = s * L + 1;  // W_{k_s + 1}: first interior row of segment s
+      j.b[1] = S + s;      // B_{k_s}
+    }
+    j.add_r = s * L;
+    j.out_w = s * L;
+    jobs.push_back(j);
+  }
+  h->if_off.push_back((int)jobs.size());
+  for (int s = 0; s < S; ++s)
+    for (int lev = 0; lev <= top[s]; ++lev) {
+      IfJob j = blank();
+      j.a[0] = s * L;                 // F~_s
+      j.b[0] = 2 * S + lev * S + s;   // R[lev][s]
+      j.out_c = lev * S + s;
+      jobs.push_back(j);
+    }
+  h->if_off.push_back((int)jobs.size());
+  for (int lev = 0; lev < depth; ++lev) {
+    for (int q = h->level_off[lev]; q < h->level_off[lev + 1]; ++q) {
+      const TreeNode& nd = h->nodes[q];
+      IfJob j = blank();
+      if (nd.l > 0) {
+        j.a[0] = (nd.l - 1) * L;                 // X~_{l-1}
+        j.b[0] = 2 * S + depth * S + nd.m;       // HL_m
+      }
+      if (nd.r < S - 1) {
+        j.a[1] = (nd.r + 1) * L;                 // X~_{r+1}
+        j.b[1] = 3 * S + depth * S + nd.m;       // HR_m
+      }
+      j.sum_lev = 0;  // the node's own slot of the node-sum buffer
+      j.sum_lo = q;
+      j.sum_hi = q;
+      j.out_w = nd.m * L;
+      jobs.push_back(j);
+    }
+    h->if_off.push_back((int)jobs.size());
+  }
+  BT_TRY(h->arena.alloc(&h->if_jobs, jobs.size() * sizeof(IfJob)));
+  BT_CUDA(cudaMemcpyAsync(h->if_jobs, jobs.data(), jobs.size() * sizeof(IfJob), cudaMemcpyHostToDevice, st));
+  BT_CUDA(cudaStreamSynchronize(st));  // the host vector goes out of scope
+  h->tc_if_bf16x3 = buf;
+  return BT_OK;
+}
+
+template <class C>
+size_t ifgemm_smem() {
+  return 1024 + C::NA * C::SLOT + 2 * C::PT + kBars(C::NA, C::NP) * 8 + 16;
+}
+
+// Step 2.2 on the tensor cores (split BF16): F~, series terms, then one launch per level.
+template <class CI>
+bt_status run_interface_tc(bt_handle_s* h, const TcBuffers& tb, const int* done, int* status, cudaStream_t st) {
+  using E = __nv_bfloat16;
+  const int M = CI::M, N = (int)h->N, S = (int)h->S, Kp = (int)tb.Kp;
+  BT_TRY(make_tc_interface(h, st));
+  const int nblk = (4 + h->depth) * S;
+  CUtensorMap tm_if, tm_w;
+  BT_TRY(make_map(&tm_if, h->tc_if_bf16x3, ET<E>::dt, CI::eb, (uint64_t)M, (uint64_t)CI::SP * nblk * M, CI::CE, M));
+  BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CI::eb, (uint64_t)M, (uint64_t)CI::SP * N * Kp, CI::CE, CI::NT));
+  const size_t smem = ifgemm_smem<CI>();
+  BT_CUDA(cudaFuncSetAttribute(k_tc_ifgemm<E, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const IfJob* jobs = reinterpret_cast<const IfJob*>(h->if_jobs);
+  const E* r = reinterpret_cast<const E*>(tb.r);
+  E* w = reinterpret_cast<E*>(tb.w);
+  // node sums of the series terms: [nodes][Kp][M] FP32 after the series terms
+  const size_t tile = (size_t)Kp * M;
+  const int nnodes = (int)h->nodes.size();
+  float* csum = tb.c + (size_t)h->depth * S * tile;
+  auto launch = [&](int g, const char* name, const float* sums) -> bt_status {
+    const int j0 = h->if_off[g], nj = h->if_off[g + 1] - j0;
+    if (nj <= 0) return BT_OK;
+    ProfScope ps(h, st, name);
+    k_tc_ifgemm<E, CI><<<dim3(Kp / CI::NT, nj), CI::THREADS, smem, st>>>(tm_if, tm_w, jobs, j0, r, w, tb.c, sums,
+                                                                        N, S, nblk, Kp, done, status);
+    BT_CUDA(cudaGetLastError());
+    return BT_OK;
+  };
+  BT_TRY(launch(0, "tc_iface", tb.c));
+  BT_TRY(launch(1, "tc_iface", tb.c));
+  {
+    ProfScope ps(h, st, "tc_dichotomy");
+    k_node_sums<<<dim3((unsigned)((tile + 1023) / 1024), nnodes), 256, 0, st>>>(tb.c, csum, h->d_nodes,
+                                                                               h->d_mid_level, S, tile, done);
+    BT_CUDA(cudaGetLastError());
+  }
+  for (int lev = 0; lev < h->depth; ++lev) BT_TRY(launch(2 + lev, "tc_dichotomy", csum));
+  return BT_OK;
+}
+
 template <class C>
 size_t sweep_smem() {
   return 1024 + C::NA * C::SLOT + (C::NP + C::YB) * C::PT + kBars(C::NA, C::NP) * 8 + 16;
@@ -1224,8 +1551,11 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_sweep<E, CS>, tm_fac_s, tm_r, tm_w, N, L, Kp, cs_sweep, done, status));
   }
   BT_CUDA(cudaGetLastError());
-  // step 2.2 (FP32 on the CUDA cores)
-  {
+  // step 2.2: tensor cores for the split-BF16 precision, FP32 CUDA cores otherwise
+  if constexpr (SP == 2) {
+    using CI = Cfg<E, CS::M, 128, 3, 2, 1, true>;
+    BT_TRY(run_interface_tc<CI>(h, tb, done, status, st));
+  } else {
     constexpr int KT = 32;   // columns per interface CTA
     constexpr int KD = 16;   // columns per dichotomy CTA (more CTAs on the narrow top levels)
     const TransposedF32& f = h->f32t;
