@@ -100,6 +100,9 @@ static void destroy_handle(bt_handle_s* h) {
   if (h->scratch) cudaFree(h->scratch);
   for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam})
     if (q) cudaFree(q);
+  if (h->rgraph.exec) cudaGraphExecDestroy(h->rgraph.exec);
+  if (h->rgraph.graph) cudaGraphDestroy(h->rgraph.graph);
+  if (h->rgraph.cap) cudaStreamDestroy(h->rgraph.cap);
   cudaSetDevice(prev);
   delete h;
 }

@@ -159,6 +159,22 @@ struct bt_handle_s {
   void* lp_x = nullptr;  // FP32 correction panel of the tensor-core solve
   size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0, lp_x_bytes = 0;
   void* ir_state = nullptr;
+  int lp_gen = 0;  // bumped whenever a refinement buffer is reallocated
+
+  // The refined solve captured as a CUDA graph: replayed when a call repeats
+  // the previous call's arguments (and no buffer moved since the capture).
+  struct RefineGraph {
+    const double* F = nullptr;
+    double* X = nullptr;
+    int64_t K = 0;
+    int precision = -1, max_it = 0, gen = -1;
+    double tol = 0.0;
+    bool seen = false;  // the previous call had this key (capture on the next)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;  // private capture stream
+    bool broken = false;         // capture failed once: enqueue directly from then on
+  } rgraph;
 
   bt::Profiler prof;
 };

@@ -161,3 +161,24 @@ def test_split_precision_needs_fewer_passes(bt):
     assert i3["rel_res0"] < 1e-2 * i1["rel_res0"], (i1, i3)
     assert i3["iters"] < i1["iters"], (i1, i3)
     assert oracle.rel_err(X3.cpu().numpy(), oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+
+
+def test_repeated_solves_replay_a_graph(bt):
+    # the second call with the same arguments captures the refinement into a
+    # CUDA graph, later calls replay it: identical results, and new values in
+    # the same F buffer are solved
+    N, M, K, S = 64, 128, 96, 8
+    A, B, C = gen.acoustic_system(N, M)
+    F1 = gen.acoustic_rhs(N, M, K, seed=21)
+    F2 = gen.acoustic_rhs(N, M, K, seed=22)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        Fd = _t(F1)
+        X = torch.empty_like(Fd)
+        X1 = fac.solve(Fd, precision="bf16x3", tol=1e-10, out=X).clone()
+        fac.solve(Fd, precision="bf16x3", tol=1e-10, out=X)
+        X3 = fac.solve(Fd, precision="bf16x3", tol=1e-10, out=X).clone()
+        assert torch.equal(X1, X3)
+        Fd.copy_(_t(F2))
+        X4, info = fac.solve(Fd, precision="bf16x3", tol=1e-10, out=X, return_info=True)
+        assert info["converged"]
+        assert oracle.rel_res(A, B, C, X4.cpu().numpy(), F2) <= 1e-10
