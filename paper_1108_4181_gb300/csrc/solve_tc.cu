@@ -1068,6 +1068,192 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
+// ======================================================================
+// Correction with the interface tiles in tensor memory (split BF16, swapped
+// roles, M = 128): X~_s and X~_{s+1} are the A operands of every row's MMAs,
+// so the epilogue warps load them once from the work panel and store them
+// into TMEM (lane n = tile column n, two block rows per 32-bit column, one
+// region per plane); shared memory then holds only the factor-slice ring,
+// seven slots deep.  TMEM: two accumulators [0, 2M) and four A regions of
+// M/2 columns each [2M, 4M).
+// ======================================================================
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+    k_tc_correct_ta(const __grid_constant__ CUtensorMap tm_fac, const __nv_bfloat16* __restrict__ wp,
+                    float* __restrict__ dp, int N, int L, int S, int Kp, int rows_per_cta, const int* done,
+                    int* status) {
+  using E = __nv_bfloat16;
+  static_assert(C::SW && C::SP == 2 && C::M == 128 && C::MH == 64, "split BF16, M = 128, swapped roles");
+  constexpr int TCOLS = 4 * C::M;
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sA + C::NA * C::SLOT);
+  const Bars b = carve<C>(barmem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const int s = blockIdx.y;
+  const bool has_next = s + 1 < S;
+  const int r0 = s * L + 1 + blockIdx.z * rows_per_cta;
+  const int r1 = min(r0 + rows_per_cta, s * L + L);
+  const int T = max(0, r1 - r0);
+  const bool do_iface = blockIdx.z == 0;
+  const int fplane = 5 * N * C::M;
+  const Share sh{1, 0, 1};
+  auto acol = [](int q, int pl) { return (uint32_t)(2 * C::M + (2 * q + pl) * (C::M / 2)); };
+  if (threadIdx.x == 0) {
+    init_bars<C>(b, 1);
+    mbar_init(&b.yrdy[0], 4 * C::EG);  // A operands stored by every epilogue warp
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tm_fac);
+      uint32_t ai = 0;
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const int i = r0 + t;
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
+        if (has_next)
+          for (int c = 0; c < C::NCH && ok; ++c)
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane, sh);
+      }
+      if (!ok) atomicExch(status, 4);
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = ai - 1 - q;
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(&b.yrdy[0], 0);
+      tc_fence_after();
+      uint32_t ai = 0;
+      for (int t = 0; t < T && ok; ++t) {
+        const int bsel = t & 1;
+        const uint32_t dt = tmem + bsel * C::ACC;
+        if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
+        tc_fence_after();
+        bool first = true;
+        for (int q = 0; q < (has_next ? 2 : 1) && ok; ++q) {
+          for (int c = 0; c < C::NCH && ok; ++c) {
+            const uint32_t slot = ai % C::NA, use = ai / C::NA;
+            ok = mbar_wait(&b.fullA[slot], use & 1);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t fb = smem_u32(sA + slot * C::SLOT);
+#pragma unroll
+            for (int kq = 0; kq < C::CE / C::KS; ++kq) {
+              const uint32_t kc = (uint32_t)(c * (C::CE / C::KS) + kq) * (C::KS / 2);  // 2 elements per column
+              const uint32_t ahi = tmem + acol(q, 0) + kc, alo = tmem + acol(q, 1) + kc;
+              const uint64_t bhi = smem_desc(fb + kq * 32, 16, 1024);
+              const uint64_t blo = smem_desc(fb + C::SLICE + kq * 32, 16, 1024);
+              mma_f16_ta(dt, ahi, bhi, C::IDESC, first ? 0u : 1u);
+              first = false;
+              mma_f16_ta(dt, alo, bhi, C::IDESC, 1u);
+              mma_f16_ta(dt, ahi, blo, C::IDESC, 1u);
+            }
+            mma_commit(&b.emptyA[slot]);
+            ++ai;
+          }
+        }
+        if (ok) mma_commit(&b.mdone[bsel]);
+      }
+      if (!ok) atomicExch(status, 5);
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    constexpr int per16 = 8;           // bf16 per 16 bytes
+    constexpr int NU = C::MH / per16;  // 16-byte units of one plane of a row share
+    const int nl = 32 * (warp & 3) + lane;
+    const int g = (warp - 2) / 4;
+    const int m0 = g * C::MH;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const size_t wplane = (size_t)N * Kp * C::M;
+    // the A operands: rows s*L and (s+1)*L of the work panel into TMEM
+    for (int q = 0; q < 2; ++q) {
+      if (q == 1 && !has_next) break;
+      const uint4* src = reinterpret_cast<const uint4*>(wp + ((size_t)(s + q) * L * Kp + n0 + nl) * C::M + m0);
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const uint4 h4 = __ldg(src + u);
+        const uint4 l4 = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(src) + wplane) + u);
+        hi[4 * u] = h4.x; hi[4 * u + 1] = h4.y; hi[4 * u + 2] = h4.z; hi[4 * u + 3] = h4.w;
+        lo[4 * u] = l4.x; lo[4 * u + 1] = l4.y; lo[4 * u + 2] = l4.z; lo[4 * u + 3] = l4.w;
+      }
+      tmem_st32(tmem + lane_base + acol(q, 0) + g * (C::MH / 2), hi);
+      tmem_st32(tmem + lane_base + acol(q, 1) + g * (C::MH / 2), lo);
+      if (q == 0 && do_iface) {  // d_{k_s} = X~_s
+        float v[C::MH];
+#pragma unroll
+        for (int e = 0; e < C::MH; ++e) v[e] = 0.f;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+          unpack16_add<E, 2>(make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]),
+                             make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]), &v[u * per16]);
+        float4* o = reinterpret_cast<float4*>(dp + ((size_t)s * L * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+        for (int e = 0; e < C::MH / 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&b.yrdy[0]);
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const int i = r0 + t;
+      const int bsel = t & 1;
+      uint4 whi[NU], wlo[NU];
+      const uint4* wsrc = reinterpret_cast<const uint4*>(wp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        whi[u] = __ldg(wsrc + u);
+        wlo[u] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(wsrc) + wplane) + u);
+      }
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      float v[C::MH];
+      if (ok) {
+        tmem_cols<C::MH>(tmem + lane_base + bsel * C::ACC + m0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) unpack16_add<E, 2>(whi[u], wlo[u], &v[u * per16]);
+      if (ok) {
+        float4* o = reinterpret_cast<float4*>(dp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+        for (int q = 0; q < C::MH / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+    if (!ok && threadIdx.x == 64) atomicExch(status, 6);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
 // X (+)= d: block-transposed FP32 correction panel into the caller's row-major
 // FP64 solution, through a 32 x 32 shared-memory tile (coalesced on both
 // sides).  Two FP64-pipe instructions per entry (the widening and the add).
@@ -1582,7 +1768,14 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     int chunks = std::max(1, std::min(rows, (2 * 152 + S * ntiles - 1) / (S * ntiles)));
     const int rpc = (rows + chunks - 1) / chunks;
     chunks = (rows + rpc - 1) / rpc;
-    {
+    if constexpr (CC::SW && CC::SP == 2 && CC::M == 128) {
+      using CT = Cfg<E, 128, 128, 7, 2, 1, true>;  // seven-slot factor ring, interface tiles in TMEM
+      const size_t smem = 1024 + CT::NA * CT::SLOT + kBars(CT::NA, CT::NP) * 8 + 16;
+      BT_CUDA(cudaFuncSetAttribute(k_tc_correct_ta<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ProfScope ps(h, st, "tc_correct");
+      k_tc_correct_ta<CT><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(tm_fac_c, (const E*)w, tb.d, N, L, S, Kp,
+                                                                             L > 1 ? rpc : 0, done, status);
+    } else {
       const size_t smem = correct_smem<CC>();
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       ProfScope ps(h, st, "tc_correct");
