@@ -101,12 +101,34 @@ def _dist():
     return ws, rank, local
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's right-hand sides: every rank solves its own K columns
+    against the same matrix (weak scaling over K replicas, no exchange)."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(v: float, ws: int, device) -> float:
+    """The slowest rank's time (all ranks call this; ws == 1 is a no-op)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        v = float(t.item())
+    return v
+
+
+def job_rate(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * ws / seconds
+
+
 def _workload(rank: int):
     from workloads import gen
 
-    # every rank solves its own 512 columns against the same matrix (weak scaling)
     A, B, C = gen.acoustic_system(N, M)
-    F = gen.acoustic_rhs(N, M, K, seed=2 + 1000 * rank)
+    F = gen.acoustic_rhs(N, M, K, seed=rank_seed(rank))
     return A, B, C, F
 
 
@@ -271,12 +293,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(v):
-        if ws > 1:
-            t = torch.tensor([v], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            v = float(t.item())
-        return v
+    def ranks_max(v):
+        return max_over_ranks(v, ws, dev)
 
     A, B, C, F = _workload(rank)
     At, Bt, Ct = (torch.from_numpy(a).to(dev) for a in (A, B, C))
@@ -300,8 +318,8 @@ def run_ours(args):
     # repeated call replays the library's CUDA graph of the whole refinement.
     with ClockSampler(local) as clk:
         ms, _ = _time_solves(fac, Fd, X, precision, tol, args.steps, args.warmup, barrier, stream, profile=False)
-    ms_step = max_over_ranks(ms / args.steps)
-    value = unknowns * ws / (ms_step * 1e-3)
+    ms_step = ranks_max(ms / args.steps)
+    value = job_rate(unknowns, ws, ms_step * 1e-3)
     # ---- the same K steps with a CUDA-event pair around every launch (direct
     # launches: events cannot be read per kernel inside a graph replay)
     ms_prof, prof = _time_solves(fac, Fd, X, precision, tol, args.steps, 1, barrier, stream, profile=True)
@@ -321,8 +339,8 @@ def run_ours(args):
         X64 = torch.empty_like(Fd)
         k64 = max(1, min(args.steps, 3))
         ms64, prof64 = _time_solves(fac, Fd, X64, "f64", 0.0, k64, 3, barrier, stream)
-        ms64 = max_over_ranks(ms64 / k64)
-        fp64 = {"value": unknowns * ws / (ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
+        ms64 = ranks_max(ms64 / k64)
+        fp64 = {"value": job_rate(unknowns, ws, ms64 * 1e-3), "ms_per_step": ms64, "steps": k64,
                 "kernels_ms_per_step": {k: v[1] / k64 for k, v in prof64.items()}}
         fp64["roofline"] = _rooflines(prof64, k64, None, "f64", hbm_peak, peak_kind)
         X64s = X64[:, :, :ORACLE_COLS].cpu().numpy() if rank == 0 else None
@@ -337,8 +355,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         fac.solve(F_host, precision=precision, tol=tol, out=Xh)
     barrier()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
-    e2e_value = unknowns * ws / e2e_s
+    e2e_s = ranks_max((time.perf_counter() - t0) / e2e_steps)
+    e2e_value = job_rate(unknowns, ws, e2e_s)
 
     # ---- roofline of the dominant kernel (and of every kernel with a model)
     roofs = _rooflines(prof, args.steps, info, precision, hbm_peak, peak_kind)

@@ -164,6 +164,97 @@ __global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restric
   if (first) block_add((double)acc, &st->rn2[0]);
 }
 
+// Block-transposed residual panel, one warp per (block row j, 8 rows m,
+// 32 columns n) item: lane n loads rows m0-1 .. m0+8 of its column (every load
+// a coalesced 256-byte row), so the m-neighbours of its 8 entries are in its
+// own registers and its 8 results are contiguous in the block-transposed
+// panel -- one 16-byte store per plane, no shared memory, no CTA barrier.
+// Five FP64 operations per entry (none with X = 0); FP32 rounding and the
+// squared norm off the FP64 pipe.  Requires M % 8 == 0.
+template <typename TR>
+__global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict__ F, const double* __restrict__ X,
+                                                      const double* __restrict__ Cd, TR* __restrict__ r, int64_t N,
+                                                      int M, int64_t K, int64_t Kp, int first, int pass, int sp,
+                                                      IrState* st) {
+  if (st->done) return;
+  const size_t plane = (size_t)N * Kp * M;
+  const size_t MK = (size_t)M * K;
+  const int lane = threadIdx.x % 32;
+  const int tn = (int)((Kp + 31) / 32), tm = M / 8;
+  const int64_t nitem = N * tm * tn;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  float acc = 0.f;
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
+    const int n = (int)(it % tn) * 32 + lane;
+    const int m0 = (int)((it / tn) % tm) * 8;
+    const int64_t j = it / ((int64_t)tn * tm);
+    const bool ncol = n < K;
+    const double* xj = X + (size_t)j * MK + n;
+    const double* fj = F + (size_t)j * MK + n;
+    double f[8], xs[10], xu[8], xd[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) f[q] = ncol ? fj[(size_t)(m0 + q) * K] : 0.0;
+    if (!first) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) {
+        const int m = m0 - 1 + q;
+        xs[q] = (ncol && m >= 0 && m < M) ? xj[(size_t)m * K] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        xu[q] = (ncol && j > 0) ? xj[(size_t)(m0 + q) * K - MK] : 0.0;
+        xd[q] = (ncol && j + 1 < N) ? xj[(size_t)(m0 + q) * K + MK] : 0.0;
+      }
+    }
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int m = m0 + q;
+      double w = f[q];
+      if (!first) {
+        const double* cd = Cd + 3 * ((size_t)j * M + m);
+        w = (w + xu[q]) + xd[q];
+        w = fma(-cd[1], xs[q + 1], w);
+        if (m > 0) w = fma(-cd[0], xs[q], w);
+        if (m + 1 < M) w = fma(-cd[2], xs[q + 2], w);
+      }
+      v[q] = ncol ? f64_to_f32_rz(w) : 0.f;
+      acc = fmaf(v[q], v[q], acc);
+    }
+    if (n < Kp) {
+      TR* o = r + ((size_t)j * Kp + n) * M + m0;
+      if constexpr (sizeof(TR) == 2) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+          const float2 bf = __bfloat1622float2(b);
+          const __nv_bfloat162 c = __floats2bfloat162_rn(v[2 * q] - bf.x, v[2 * q + 1] - bf.y);
+          h[q] = *reinterpret_cast<const uint32_t*>(&b);
+          l[q] = *reinterpret_cast<const uint32_t*>(&c);
+        }
+        *reinterpret_cast<uint4*>(o) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (sp == 2) *reinterpret_cast<uint4*>(o + plane) = make_uint4(l[0], l[1], l[2], l[3]);
+      } else {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          hi[q] = sp == 2 ? __uint_as_float(__float_as_uint(v[q]) & 0xFFFFE000u) : v[q];
+          lo[q] = v[q] - hi[q];
+        }
+        reinterpret_cast<float4*>(o)[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        reinterpret_cast<float4*>(o)[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
+        if (sp == 2) {
+          reinterpret_cast<float4*>(o + plane)[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          reinterpret_cast<float4*>(o + plane)[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+        }
+      }
+    }
+  }
+  block_add((double)acc, first ? &st->fn2 : &st->rn2[pass]);
+  if (first) block_add((double)acc, &st->rn2[0]);
+}
+
 // r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
 // One CTA per (block row, column tile); a thread owns row m and CW columns.
 // Output row-major (TRANS = false, leading dimension ldr) or block-transposed
@@ -274,7 +365,12 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   const int M = (int)h->M;
   ProfScope ps(h, s, "residual");
   if (first || h->stencil) {
-    if (trans) {
+    if (trans && M % 8 == 0) {
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
+      const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
+      const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
+      k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
+    } else if (trans) {
       const int64_t ntile = ((Kp + 31) / 32) * ((M + 31) / 32) * h->N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil_t<TR>), 256, 0);
       const int blocks = (int)std::min<int64_t>(ntile, grid);

@@ -353,6 +353,35 @@ __device__ __forceinline__ void mma1(uint32_t d, uint64_t a, uint64_t bdesc, uin
 // MMA helper: D (+)= A_block * B_tile over the M-long contraction, streaming
 // the block's NCH slices from the ring; frees each slot when consumed.  With
 // two planes: D += Ahi Bhi + Ahi Blo + Alo Bhi.
+// The MMAs of one contraction chunk (CE values) of one factor slice (at smem
+// address fslot, all planes) against chunk c of a panel tile: D (+)= slice x
+// tile (roles per C::SW); with two planes hi*hi + hi*lo + lo*hi.
+template <typename E, class C>
+__device__ __forceinline__ void mma_chunk(uint32_t dtmem, uint32_t fslot, uint32_t btile, int c, bool& first) {
+#pragma unroll
+  for (int kq = 0; kq < C::CE / C::KS; ++kq) {
+    const uint32_t boff = btile + c * C::TCH + kq * 32;
+    const uint64_t fhi = smem_desc(fslot + kq * 32, 16, 1024), phi = smem_desc(boff, 16, 1024);
+    if constexpr (C::SW) {
+      mma1<E>(dtmem, phi, fhi, C::IDESC, !first);
+      first = false;
+      if (C::SP == 2) {
+        mma1<E>(dtmem, smem_desc(boff + C::TILE, 16, 1024), fhi, C::IDESC, true);
+        mma1<E>(dtmem, phi, smem_desc(fslot + C::SLICE + kq * 32, 16, 1024), C::IDESC, true);
+      }
+    } else {
+      mma1<E>(dtmem, fhi, phi, C::IDESC, !first);
+      first = false;
+      if (C::SP == 2) {
+        mma1<E>(dtmem, fhi, smem_desc(boff + C::TILE, 16, 1024), C::IDESC, true);
+        mma1<E>(dtmem, smem_desc(fslot + C::SLICE + kq * 32, 16, 1024), phi, C::IDESC, true);
+      }
+    }
+  }
+}
+
+// MMA helper: D (+)= A_block * B_tile over the M-long contraction, streaming
+// the block's NCH slices from the ring; frees each slot when consumed.
 template <typename E, class C>
 __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& ai, uint32_t dtmem, uint32_t btile,
                                           bool& first, const Share& sh) {
@@ -360,27 +389,7 @@ __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& 
     const uint32_t slot = ai % C::NA, use = ai / C::NA;
     if (!mbar_wait(&b.fullA[slot], use & 1)) return false;
     tc_fence_after();
-    const uint32_t ahi = smem_u32(sA + slot * C::SLOT);
-#pragma unroll
-    for (int kq = 0; kq < C::CE / C::KS; ++kq) {
-      const uint32_t boff = btile + c * C::TCH + kq * 32;
-      const uint64_t fhi = smem_desc(ahi + kq * 32, 16, 1024), phi = smem_desc(boff, 16, 1024);
-      if constexpr (C::SW) {
-        mma1<E>(dtmem, phi, fhi, C::IDESC, !first);
-        first = false;
-        if (C::SP == 2) {
-          mma1<E>(dtmem, smem_desc(boff + C::TILE, 16, 1024), fhi, C::IDESC, true);
-          mma1<E>(dtmem, phi, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), C::IDESC, true);
-        }
-      } else {
-        mma1<E>(dtmem, fhi, phi, C::IDESC, !first);
-        first = false;
-        if (C::SP == 2) {
-          mma1<E>(dtmem, fhi, smem_desc(boff + C::TILE, 16, 1024), C::IDESC, true);
-          mma1<E>(dtmem, smem_desc(ahi + C::SLICE + kq * 32, 16, 1024), phi, C::IDESC, true);
-        }
-      }
-    }
+    mma_chunk<E, C>(dtmem, smem_u32(sA + slot * C::SLOT), btile, c, first);
     if (sh.csize == 1)
       mma_commit(&b.emptyA[slot]);
     else
@@ -421,8 +430,8 @@ enum { FT_DINV = 0, FT_E = 1, FT_G = 2, FT_U = 3, FT_V = 4 };
 template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_sweep(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_r,
-               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, int csize, const int* done,
-               int* status) {
+               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, int csize, int shareD,
+               const int* done, int* status) {
   if (flag_set(done)) return;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -475,7 +484,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         const int first_type = fwd ? FT_DINV : FT_G;
         for (int c = 0; c < C::NCH && ok; ++c)
           ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane, sh);
-        if (fwd && t > 0)
+        if (fwd && t > 0 && !shareD)
           for (int c = 0; c < C::NCH && ok; ++c)
             ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane, sh);
       }
@@ -503,7 +512,28 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         tc_fence_after();
         bool first = true;
         uint32_t pslot = 0;
-        if (ok && fwd) {
+        if (ok && fwd && shareD && t > 0) {
+          // A_i = I: E_i = Dinv_i, so y_i = Dinv_i (r_i + y_{i-1}); each Dinv
+          // slice serves both products and is released after the second
+          pslot = pi % C::NP;
+          ok = mbar_wait(&b.fullP[pslot], (pi / C::NP) & 1);
+          tc_fence_after();
+          const uint32_t ai0 = ai;
+          for (int c = 0; c < C::NCH && ok; ++c) {
+            const uint32_t q = ai0 + c, slot = q % C::NA;
+            ok = mbar_wait(&b.fullA[slot], (q / C::NA) & 1);
+            tc_fence_after();
+            if (ok) mma_chunk<E, C>(dt, smem_u32(sA + slot * C::SLOT), smem_u32(sP + pslot * C::PT), c, first);
+          }
+          if (ok) ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
+          tc_fence_after();
+          for (int c = 0; c < C::NCH && ok; ++c) {
+            const uint32_t slot = (ai0 + c) % C::NA;
+            mma_chunk<E, C>(dt, smem_u32(sA + slot * C::SLOT), yop, c, first);
+            mma_commit(&b.emptyA[slot]);
+          }
+          ai = ai0 + C::NCH;
+        } else if (ok && fwd) {
           pslot = pi % C::NP;
           ok = mbar_wait(&b.fullP[pslot], (pi / C::NP) & 1);
           tc_fence_after();
@@ -1734,7 +1764,11 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_sweep<E, CS>, tm_fac_s, tm_r, tm_w, N, L, Kp, cs_sweep, done, status));
+    // A_i = I lets the forward sweep reuse Dinv_i for the recurrence term (needs a
+    // ring that holds all of a block's slices plus one; no multicast sharing)
+    const int shareD = (h->stencil && cs_sweep == 1 && CS::NA > CS::NCH) ? 1 : 0;
+    BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_sweep<E, CS>, tm_fac_s, tm_r, tm_w, N, L, Kp, cs_sweep, shareD, done,
+                               status));
   }
   BT_CUDA(cudaGetLastError());
   // step 2.2: tensor cores for the split-BF16 precision, FP32 CUDA cores otherwise
