@@ -1318,6 +1318,36 @@ __global__ void __launch_bounds__(256) k_x_update(const float* __restrict__ d, d
   }
 }
 
+// The same update, one warp per (block row j, 8 rows m, 32 columns n): lane n
+// reads its 8 FP32 corrections (32 contiguous bytes of the block-transposed
+// panel) and updates rows m0..m0+7 of column n of the row-major solution
+// (each a coalesced 256-byte row); no shared memory, no barrier.  M % 8 == 0.
+__global__ void __launch_bounds__(256) k_x_update_warp(const float* __restrict__ d, double* __restrict__ X, int N,
+                                                       int M, int K, int Kp, int accumulate, const int* done) {
+  if (flag_set(done)) return;
+  const int lane = threadIdx.x % 32;
+  const int tn = (K + 31) / 32, tm = M / 8;
+  const int64_t nitem = (int64_t)N * tm * tn;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
+    const int n = (int)(it % tn) * 32 + lane;
+    const int m0 = (int)((it / tn) % tm) * 8;
+    const int64_t j = it / ((int64_t)tn * tm);
+    if (n >= K) continue;
+    const float4* src = reinterpret_cast<const float4*>(d + ((size_t)j * Kp + n) * M + m0);
+    const float4 a = __ldg(src), b = __ldg(src + 1);
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    double* x = X + ((size_t)j * M + m0) * K + n;
+    if (accumulate) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[(size_t)q * K] += f32_to_f64(v[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[(size_t)q * K] = f32_to_f64(v[q]);
+    }
+  }
+}
+
 // ======================================================================
 // Step 2.2 on the CUDA cores (FP32), block-transposed panels of type E with
 // SP planes (plane stride `ps` elements).  Each thread owns a 4 x 8 register
@@ -1829,7 +1859,13 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
                                  L > 1 ? rpc : 0, cs_corr, done, status));
     }
     BT_CUDA(cudaGetLastError());
-    {
+    if (M % 8 == 0) {
+      const int64_t nitem = (int64_t)((K + 31) / 32) * (M / 8) * N;
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update_warp), 256, 0);
+      const int blocks = (int)std::min<int64_t>((nitem + 7) / 8, grid);
+      ProfScope ps(h, st, "x_update");
+      k_x_update_warp<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
+    } else {
       const int64_t ntile = (int64_t)((K + 31) / 32) * ((M + 31) / 32) * N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update), 256, 0);
       const int blocks = (int)std::min<int64_t>(ntile, grid);
