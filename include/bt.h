@@ -58,7 +58,8 @@ typedef enum {
 /* Options of bt_solve_ex.  Zero-initialised options mean: FP64, defaults. */
 typedef struct {
   int32_t precision;  /* bt_precision */
-  int32_t max_it;     /* refinement passes after the first solve (0 = default 12) */
+  int32_t max_it;     /* refinement passes after the first solve (0 = default: 6 for
+                         BT_PREC_BF16X3, 12 otherwise) */
   double tol;         /* target ||F - P X||_F / ||F||_F (0 = default 1e-10) */
   void* stream;       /* cudaStream_t */
   int32_t k_tile;     /* right-hand-side columns per CTA (0 = automatic) */

@@ -119,51 +119,6 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
   if (first) block_add(acc, &st->rn2[0]);
 }
 
-// Block-transposed residual panel (element (m, n) of block j at (j*Kp + n)*M + m),
-// through a 32 x 32 shared-memory tile so that both the FP64 reads (along n)
-// and the stores (along m) are coalesced.  Columns K..Kp-1 are written as zero.
-template <typename TR>
-__global__ void __launch_bounds__(256) k_resid_stencil_t(const double* __restrict__ F, const double* __restrict__ X,
-                                                        const double* __restrict__ Cd, TR* __restrict__ r,
-                                                        int64_t N, int M, int64_t K, int64_t Kp, int first,
-                                                        int pass, int sp, IrState* st) {
-  const size_t plane = (size_t)N * Kp * M;
-  if (st->done) return;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int64_t tn = (Kp + 31) / 32, tm = (M + 31) / 32;
-  const int64_t ntile = tn * tm * N;
-  // Five FP64 operations per entry (none with X = 0); the rounding to FP32
-  // and the squared norm (accumulated per thread in FP32, a stopping test
-  // needs a few digits) stay off the FP64 pipe.  Grid-stride over 32 x 32
-  // tiles; one partial sum per CTA.
-  float acc = 0.f;
-  __shared__ float ftile[32][33];
-  for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
-    const int64_t n0 = (q0 % tn) * 32;
-    const int m0 = (int)((q0 / tn) % tm) * 32;
-    const int64_t j = q0 / (tn * tm);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int m = m0 + ty + 8 * q;
-      const int64_t n = n0 + tx;
-      float v = 0.f;
-      if (m < M && n < K) v = f64_to_f32_rz(stencil_res(F, X, Cd, N, M, K, j, m, n, first));
-      acc = fmaf(v, v, acc);
-      ftile[ty + 8 * q][tx] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t n = n0 + ty + 8 * q;
-      const int m = m0 + tx;
-      if (m < M && n < Kp) put_planes(r, ((size_t)j * Kp + n) * M + m, plane, sp, ftile[tx][ty + 8 * q]);
-    }
-    __syncthreads();
-  }
-  block_add((double)acc, first ? &st->fn2 : &st->rn2[pass]);
-  if (first) block_add((double)acc, &st->rn2[0]);
-}
-
 // Block-transposed residual panel, one warp per (block row j, 8 rows m,
 // 32 columns n) item: lane n loads rows m0-1 .. m0+8 of its column (every load
 // a coalesced 256-byte row), so the m-neighbours of its 8 entries are in its
@@ -365,16 +320,11 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   const int M = (int)h->M;
   ProfScope ps(h, s, "residual");
   if (first || h->stencil) {
-    if (trans && M % 8 == 0) {
+    if (trans) {  // the tensor-core panels: M is 64 or 128
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
       const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
       const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
       k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
-    } else if (trans) {
-      const int64_t ntile = ((Kp + 31) / 32) * ((M + 31) / 32) * h->N;
-      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil_t<TR>), 256, 0);
-      const int blocks = (int)std::min<int64_t>(ntile, grid);
-      k_resid_stencil_t<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
     } else {
       const size_t n = (size_t)h->N * M * K;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
@@ -429,7 +379,9 @@ bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st) {
 
 bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info) {
   cudaStream_t s = (cudaStream_t)o.stream;
-  const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : 12;
+  // default passes: the split-BF16 solve gains about five digits per pass, the
+  // single-plane precisions about two to three
+  const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : (o.precision == BT_PREC_BF16X3 ? 6 : 12);
   const double tol = o.tol > 0 ? o.tol : 1e-10;
   const int prec = o.precision;
   const bool tcore = prec == BT_PREC_BF16 || prec == BT_PREC_TF32 || prec == BT_PREC_BF16X3;

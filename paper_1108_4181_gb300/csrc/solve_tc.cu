@@ -26,7 +26,7 @@
 //                 per cent of the flops: S (2 + depth) block products).
 //   k_tc_correct  eq. superposition, step 2.3: d_i = W_i + U_i X~_s +
 //                 V_i X~_{s+1} into an FP32 correction panel (TMA stores);
-//   k_x_update    X (+)= d into the caller's FP64 solution.
+//   k_x_update_warp  X (+)= d into the caller's FP64 solution.
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 // written as FP32 into the block-transposed correction panel D by TMA stores
 // (no FP64 work on this kernel's critical path); chunk 0 of every segment
 // also writes d_{k_s} = X~_s.  The FP64 solution is updated afterwards by
-// k_x_update (X (+)= d), a streaming kernel bound by the FP64 pipe.
+// k_x_update_warp (X (+)= d), a streaming kernel bound by HBM.
 // ======================================================================
 template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
@@ -1284,41 +1284,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   if (warp == 1) tmem_dealloc(tmem, TCOLS);
 }
 
-// X (+)= d: block-transposed FP32 correction panel into the caller's row-major
-// FP64 solution, through a 32 x 32 shared-memory tile (coalesced on both
-// sides).  Two FP64-pipe instructions per entry (the widening and the add).
-__global__ void __launch_bounds__(256) k_x_update(const float* __restrict__ d, double* __restrict__ X, int N, int M,
-                                                  int K, int Kp, int accumulate, const int* done) {
-  if (flag_set(done)) return;
-  __shared__ float tile[32][33];
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const int64_t tn = (K + 31) / 32, tm = (M + 31) / 32;
-  const int64_t ntile = tn * tm * N;
-  const size_t MK = (size_t)M * K;
-  for (int64_t q0 = blockIdx.x; q0 < ntile; q0 += gridDim.x) {
-    const int n0 = (int)(q0 % tn) * 32;
-    const int m0 = (int)((q0 / tn) % tm) * 32;
-    const int64_t j = q0 / (tn * tm);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int n = n0 + ty + 8 * q, m = m0 + tx;
-      tile[ty + 8 * q][tx] = (m < M && n < K) ? d[((size_t)j * Kp + n) * M + m] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int m = m0 + ty + 8 * q, n = n0 + tx;
-      if (m < M && n < K) {
-        double* o = X + (size_t)j * MK + (size_t)m * K + n;
-        const double v = f32_to_f64(tile[tx][ty + 8 * q]);  // exact, on the integer pipe
-        *o = accumulate ? *o + v : v;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// The same update, one warp per (block row j, 8 rows m, 32 columns n): lane n
+// X (+)= d: the block-transposed FP32 correction panel into the caller's
+// row-major FP64 solution, one warp per (block row j, 8 rows m, 32 columns n): lane n
 // reads its 8 FP32 corrections (32 contiguous bytes of the block-transposed
 // panel) and updates rows m0..m0+7 of column n of the row-major solution
 // (each a coalesced 256-byte row); no shared memory, no barrier.  M % 8 == 0.
@@ -1859,18 +1826,12 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
                                  L > 1 ? rpc : 0, cs_corr, done, status));
     }
     BT_CUDA(cudaGetLastError());
-    if (M % 8 == 0) {
+    {  // M is 64 or 128
       const int64_t nitem = (int64_t)((K + 31) / 32) * (M / 8) * N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update_warp), 256, 0);
       const int blocks = (int)std::min<int64_t>((nitem + 7) / 8, grid);
       ProfScope ps(h, st, "x_update");
       k_x_update_warp<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
-    } else {
-      const int64_t ntile = (int64_t)((K + 31) / 32) * ((M + 31) / 32) * N;
-      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update), 256, 0);
-      const int blocks = (int)std::min<int64_t>(ntile, grid);
-      ProfScope ps(h, st, "x_update");
-      k_x_update<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
     }
   }
   BT_CUDA(cudaGetLastError());

@@ -131,3 +131,16 @@ def test_batched_rejects_bad_input(bt):
     with pytest.raises(bt.BtError) as e:
         bt.solve_batched([f8, f8], [F8, torch.empty_like(F8)], [X, X])  # two outputs share memory
     assert e.value.name == "BT_ERR_ARG"
+
+
+def test_batched_matrices_of_different_sizes(bt):
+    # one launch over sets whose matrices differ in N and S (same block size)
+    M = 8
+    mats = [gen.dominant_blocks(48, M, 11), gen.dominant_blocks(96, M, 12)]
+    facs = _factors(bt, mats, (6, 32))
+    sets = [gen.RhsSet(matrix=0, K=5, F=gen.uniform_rhs(48, M, 5, seed=1)),
+            gen.RhsSet(matrix=1, K=19, F=gen.uniform_rhs(96, M, 19, seed=2)),
+            gen.RhsSet(matrix=0, K=1, F=gen.uniform_rhs(48, M, 1, seed=3))]
+    Xs = bt.solve_batched([facs[s.matrix] for s in sets], [_t(s.F) for s in sets])
+    torch.cuda.synchronize()
+    _check(mats, sets, Xs)
