@@ -1103,15 +1103,17 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 // roles, M = 128): X~_s and X~_{s+1} are the A operands of every row's MMAs,
 // so the epilogue warps load them once from the work panel and store them
 // into TMEM (lane n = tile column n, two block rows per 32-bit column, one
-// region per plane); shared memory then holds only the factor-slice ring,
-// seven slots deep.  TMEM: two accumulators [0, 2M) and four A regions of
+// region per plane); shared memory holds the factor-slice ring and, with WR,
+// a ring of W tiles.  TMEM: two accumulators [0, 2M) and four A regions of
 // M/2 columns each [2M, 4M).
 // ======================================================================
-template <class C>
+// WR: W_i rows come through a C::NP-stage TMA tile ring (else each epilogue
+// thread loads its row share from global memory).
+template <class C, bool WR>
 __global__ void __launch_bounds__(C::THREADS, 1)
-    k_tc_correct_ta(const __grid_constant__ CUtensorMap tm_fac, const __nv_bfloat16* __restrict__ wp,
-                    float* __restrict__ dp, int N, int L, int S, int Kp, int rows_per_cta, const int* done,
-                    int* status) {
+    k_tc_correct_ta(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
+                    const __nv_bfloat16* __restrict__ wp, float* __restrict__ dp, int N, int L, int S, int Kp,
+                    int rows_per_cta, const int* done, int* status) {
   using E = __nv_bfloat16;
   static_assert(C::SW && C::SP == 2 && C::M == 128 && C::MH == 64, "split BF16, M = 128, swapped roles");
   constexpr int TCOLS = 4 * C::M;
@@ -1119,7 +1121,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = sm;
-  uint64_t* barmem = reinterpret_cast<uint64_t*>(sA + C::NA * C::SLOT);
+  uint8_t* sP = sA + C::NA * C::SLOT;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sP + (WR ? C::NP * C::PT : 0));
   const Bars b = carve<C>(barmem);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
 
@@ -1151,10 +1154,13 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       prefetch_tmap(&tm_fac);
-      uint32_t ai = 0;
+      if (WR) prefetch_tmap(&tm_w);
+      uint32_t ai = 0, pi = 0;
       bool ok = true;
+      const int pplane = N * Kp;
       for (int t = 0; t < T && ok; ++t) {
         const int i = r0 + t;
+        if (WR) ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
           ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
         if (has_next)
@@ -1165,6 +1171,10 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
         const uint32_t last = ai - 1 - q;
         mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+      for (uint32_t q = 0; q < C::NP && q < pi; ++q) {
+        const uint32_t last = pi - 1 - q;
+        mbar_wait(&b.fullP[last % C::NP], (last / C::NP) & 1);
       }
     }
   } else if (warp == 1) {
@@ -1245,15 +1255,18 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     __syncwarp();
     if (lane == 0) mbar_arrive(&b.yrdy[0]);
     bool ok = true;
+    uint32_t pe = 0;
     for (int t = 0; t < T; ++t) {
       const int i = r0 + t;
       const int bsel = t & 1;
-      uint4 whi[NU], wlo[NU];
-      const uint4* wsrc = reinterpret_cast<const uint4*>(wp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
+      uint4 whi[WR ? 1 : NU], wlo[WR ? 1 : NU];
+      if constexpr (!WR) {
+        const uint4* wsrc = reinterpret_cast<const uint4*>(wp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
 #pragma unroll
-      for (int u = 0; u < NU; ++u) {
-        whi[u] = __ldg(wsrc + u);
-        wlo[u] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(wsrc) + wplane) + u);
+        for (int u = 0; u < NU; ++u) {
+          whi[u] = __ldg(wsrc + u);
+          wlo[u] = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(wsrc) + wplane) + u);
+        }
       }
       if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
@@ -1268,8 +1281,18 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      if constexpr (WR) {
+        const uint32_t ps = pe % C::NP;
+        if (ok) ok = mbar_wait(&b.fullP[ps], (pe / C::NP) & 1);
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) row_add<E, C>(sP + ps * C::PT, nl, m0, v);
+        named_bar_sync(1, 128 * C::EG);
+        if (ok && warp == 2 && lane == 0) mbar_arrive(&b.emptyP[ps]);
+        ++pe;
+      } else {
 #pragma unroll
-      for (int u = 0; u < NU; ++u) unpack16_add<E, 2>(whi[u], wlo[u], &v[u * per16]);
+        for (int u = 0; u < NU; ++u) unpack16_add<E, 2>(whi[u], wlo[u], &v[u * per16]);
+      }
       if (ok) {
         float4* o = reinterpret_cast<float4*>(dp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
 #pragma unroll
@@ -1800,12 +1823,15 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     const int rpc = (rows + chunks - 1) / chunks;
     chunks = (rows + rpc - 1) / rpc;
     if constexpr (CC::SW && CC::SP == 2 && CC::M == 128) {
-      using CT = Cfg<E, 128, 128, 7, 2, 1, true>;  // seven-slot factor ring, interface tiles in TMEM
-      const size_t smem = 1024 + CT::NA * CT::SLOT + kBars(CT::NA, CT::NP) * 8 + 16;
-      BT_CUDA(cudaFuncSetAttribute(k_tc_correct_ta<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      // interface tiles in TMEM, three factor slots, W rows through a two-stage
+      // TMA ring (measured against seven slots with W read by the epilogue
+      // threads: 1.27 against 1.70 ms per two corrections)
+      using CT = Cfg<E, 128, 128, 3, 2, 2, true>;
+      const size_t smem = 1024 + CT::NA * CT::SLOT + CT::NP * CT::PT + kBars(CT::NA, CT::NP) * 8 + 16;
+      BT_CUDA(cudaFuncSetAttribute(k_tc_correct_ta<CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       ProfScope ps(h, st, "tc_correct");
-      k_tc_correct_ta<CT><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(tm_fac_c, (const E*)w, tb.d, N, L, S, Kp,
-                                                                             L > 1 ? rpc : 0, done, status);
+      k_tc_correct_ta<CT, true><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(
+          tm_fac_c, tm_wc, (const E*)w, tb.d, N, L, S, Kp, L > 1 ? rpc : 0, done, status);
     } else {
       const size_t smem = correct_smem<CC>();
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
