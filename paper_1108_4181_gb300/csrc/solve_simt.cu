@@ -304,11 +304,17 @@ struct Plan {
   int CW, CG;
 };
 
+// FP64: issue-bound on the FP64 pipe; 4 columns per thread and about 128
+// threads per CTA keep it busy.  FP32: 60x the FMA rate, so the factor
+// stream becomes the bound; 8 columns per thread and up to 512 threads per
+// CTA give each factor element fetched 16 to 64 uses.
 template <typename T>
 Plan pick_plan(int M, int64_t K) {
   Plan pl;
-  pl.CW = K >= 4 ? 4 : (K >= 2 ? 2 : 1);
-  int CG = (int)std::min<int64_t>((K + pl.CW - 1) / pl.CW, std::max(1, 128 / M));
+  const bool f32 = sizeof(T) == 4;
+  pl.CW = (f32 && K >= 8) ? 8 : (K >= 4 ? 4 : (K >= 2 ? 2 : 1));
+  const int target = f32 ? 512 : 128;
+  int CG = (int)std::min<int64_t>((K + pl.CW - 1) / pl.CW, std::max(1, target / M));
   pl.CG = std::max(1, std::min(CG, 1024 / M));
   return pl;
 }
@@ -367,6 +373,7 @@ bt_status run(bt_handle_s* h, const SimtArgs<T>& a, const T* Fin, T* Wk, double*
               int accumulate, cudaStream_t st) {
   const Plan pl = pick_plan<T>(a.M, a.K);
   switch (pl.CW) {
+    case 8: return launch_all<T, 8>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     case 4: return launch_all<T, 4>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     case 2: return launch_all<T, 2>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     default: return launch_all<T, 1>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
@@ -455,6 +462,7 @@ bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, fl
     return BT_OK;
   };
   switch (CW) {
+    case 8: return go(std::integral_constant<int, 8>());
     case 4: return go(std::integral_constant<int, 4>());
     case 2: return go(std::integral_constant<int, 2>());
     default: return go(std::integral_constant<int, 1>());
