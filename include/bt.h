@@ -23,6 +23,10 @@
  *   - There is no CPU fallback: every arithmetic step runs in this library's
  *     CUDA kernels; a call on a machine without a usable sm_103 GPU fails
  *     with BT_ERR_CUDA.
+ *   - Tuning variable: BT_TC_CLUSTER=2 or 4 makes the tensor-core sweep and
+ *     correction CTAs of neighbouring column tiles share each factor slice
+ *     through a TMA multicast within a thread-block cluster (default 1: each
+ *     CTA loads its own slices; read once per process).
  */
 #ifndef BT_H_
 #define BT_H_

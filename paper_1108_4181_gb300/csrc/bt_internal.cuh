@@ -240,9 +240,6 @@ bt_status ensure_scratch(bt_handle_s* h, size_t bytes, cudaStream_t st);
 // X = (accumulate ? X : 0) + solution.  Returns at once when *done != 0.
 bt_status solve_simt_f32(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, double* X, int accumulate,
                          const int* done, cudaStream_t st);
-// Only the interface steps (F~, series terms, dichotomy) of the FP32 pipeline.
-bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, const int* done,
-                                   cudaStream_t st);
 
 // Buffers of one tensor-core solve: factor copies, block-transposed residual
 // and work panels (leading dimension Kp, a multiple of the column tile), and

@@ -426,48 +426,6 @@ bt_status solve_simt_f32(bt_handle_s* h, const float* r, int64_t K, float* d, fl
   return run<float>(h, a, r, d, X, 3, 1, accumulate, st);
 }
 
-bt_status solve_simt_f32_interface(bt_handle_s* h, const float* r, int64_t K, float* d, float* c, const int* done,
-                                   cudaStream_t st) {
-  // steps 2.2 only (the interface right-hand side and the dichotomy); the
-  // tensor-core kernels do the sweeps and the correction.
-  const LowFactors& f = h->f32;
-  SimtArgs<float> a;
-  a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = (int)h->M;
-  a.Dinv = f.Dinv; a.E = f.E; a.G = f.G; a.U = f.U; a.V = f.V;
-  a.AK = f.AK; a.BK = f.BK; a.R = f.R; a.HL = f.HL; a.HR = f.HR;
-  a.nodes = h->d_nodes; a.mid_level = h->d_mid_level;
-  a.c = c;
-  a.done = done;
-  const Plan pl = pick_plan<float>(a.M, K);
-  const int CW = pl.CW, CG = pl.CG, M = a.M, kt = CW * CG, threads = M * CG;
-  const int64_t ntiles = (K + kt - 1) / kt;
-  const size_t sm2 = 2 * (size_t)M * kt * sizeof(float), sm3 = 3 * (size_t)M * kt * sizeof(float);
-  auto go = [&](auto cw) -> bt_status {
-    constexpr int W = decltype(cw)::value;
-    if (sm3 > 48 * 1024) {
-      BT_CUDA(cudaFuncSetAttribute(k_iface<float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-      BT_CUDA(cudaFuncSetAttribute(k_dichotomy<float, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    }
-    {
-      ProfScope ps(h, st, "f32_iface");
-      k_iface<float, W><<<dim3((unsigned)a.S, (unsigned)ntiles), threads, sm3, st>>>(a, r, d);
-    }
-    BT_CUDA(cudaGetLastError());
-    for (int lev = 0; lev < h->depth; ++lev) {
-      const int n0 = h->level_off[lev], nn = h->level_off[lev + 1] - n0;
-      ProfScope ps(h, st, "f32_dichotomy");
-      k_dichotomy<float, W><<<dim3(nn, (unsigned)ntiles), threads, sm2, st>>>(a, lev, n0, d);
-    }
-    BT_CUDA(cudaGetLastError());
-    return BT_OK;
-  };
-  switch (CW) {
-    case 8: return go(std::integral_constant<int, 8>());
-    case 4: return go(std::integral_constant<int, 4>());
-    case 2: return go(std::integral_constant<int, 2>());
-    default: return go(std::integral_constant<int, 1>());
-  }
-}
 
 }  // namespace bt
 
