@@ -196,7 +196,7 @@ TRAFFIC = {
     # mixed_solve_acoustic_N4096_M128_K512_S64.md); the kernel streams F and X
     # once per pass, so traffic scales with the unknowns
     "residual": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
-                 "sha256": "0804f727524c6369121fb4625c463831c7ba9ad299a72eb0f0c0754baccfcc24",
+                 "sha256": "ad8db417d35cdc1c6ccac754a169260a29a3a941f229f25928cf1271f1aaea30",
                  "bytes_per_unknown": 19.8262},
 }
 
@@ -224,9 +224,12 @@ def _kernel_work(name, prof, steps, info, precision):
         return "alu", 2.0 * M * M * K * rows, "FLOP"
     full = info["iters"] + 1 if info else None      # refinement solves incl. the first
     if name == "residual":
-        # F - P X, five FP64 operations per entry, after every solve; the
-        # first residual (X = 0) is a rounding of F only
+        # F - P X, five FP64 operations per entry, after every solve
         return "alu", 5.0 * NMK * full, "FP64op"
+    if name == "rhs_round":
+        # the first residual (X = 0): F read, rounded into the low-precision panel
+        pb0 = (2 if precision == "bf16x3" else 1) * (4 if precision in ("tf32", "f32") else 2)
+        return "hbm", NMK * (8.0 + pb0), "B"
     if name == "x_update":
         # X = d (first solve), X += d: FP32 d + FP64 X read, FP64 X written
         return "hbm", NMK * (12.0 + 20.0 * (full - 1)), "B"

@@ -318,7 +318,8 @@ template <typename TR>
 bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
                           int sp, int first, int pass, IrState* st, cudaStream_t s) {
   const int M = (int)h->M;
-  ProfScope ps(h, s, "residual");
+  // the first pass (X = 0) only rounds F into the panel: timed under its own name
+  ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
     if (trans) {  // the tensor-core panels: M is 64 or 128
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);

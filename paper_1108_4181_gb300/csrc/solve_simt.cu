@@ -312,7 +312,7 @@ template <typename T>
 Plan pick_plan(int M, int64_t K) {
   Plan pl;
   const bool f32 = sizeof(T) == 4;
-  pl.CW = (f32 && K >= 8) ? 8 : (K >= 4 ? 4 : (K >= 2 ? 2 : 1));
+  pl.CW = (f32 && K >= 16) ? 16 : (f32 && K >= 8) ? 8 : (K >= 4 ? 4 : (K >= 2 ? 2 : 1));
   const int target = f32 ? 512 : 128;
   int CG = (int)std::min<int64_t>((K + pl.CW - 1) / pl.CW, std::max(1, target / M));
   pl.CG = std::max(1, std::min(CG, 1024 / M));
@@ -373,6 +373,7 @@ bt_status run(bt_handle_s* h, const SimtArgs<T>& a, const T* Fin, T* Wk, double*
               int accumulate, cudaStream_t st) {
   const Plan pl = pick_plan<T>(a.M, a.K);
   switch (pl.CW) {
+    case 16: return launch_all<T, 16>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     case 8: return launch_all<T, 8>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     case 4: return launch_all<T, 4>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");
     case 2: return launch_all<T, 2>(h, a, Fin, Wk, Xout, pl.CG, stages, separate, accumulate, st, "");

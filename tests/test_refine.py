@@ -182,3 +182,21 @@ def test_repeated_solves_replay_a_graph(bt):
         X4, info = fac.solve(Fd, precision="bf16x3", tol=1e-10, out=X, return_info=True)
         assert info["converged"]
         assert oracle.rel_res(A, B, C, X4.cpu().numpy(), F2) <= 1e-10
+
+
+def test_graph_cache_follows_argument_changes(bt):
+    # alternating panel widths and tolerances: every call must solve its own
+    # arguments whether it runs directly, captures or replays a graph
+    N, M, S = 32, 64, 4
+    A, B, C = gen.acoustic_system(N, M)
+    Fa = gen.acoustic_rhs(N, M, 96, seed=31)
+    Fb = gen.acoustic_rhs(N, M, 40, seed=32)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        Fa_d, Fb_d = _t(Fa), _t(Fb)
+        Xa, Xb = torch.empty_like(Fa_d), torch.empty_like(Fb_d)
+        for tol, F, Fd, X in [(1e-10, Fa, Fa_d, Xa), (1e-10, Fa, Fa_d, Xa), (1e-10, Fa, Fa_d, Xa),
+                              (1e-12, Fb, Fb_d, Xb), (1e-10, Fa, Fa_d, Xa), (1e-12, Fb, Fb_d, Xb),
+                              (1e-12, Fb, Fb_d, Xb), (1e-12, Fb, Fb_d, Xb)]:
+            _, info = fac.solve(Fd, precision="bf16x3", tol=tol, out=X, return_info=True)
+            assert info["converged"] and info["rel_res"] <= tol
+            assert oracle.rel_res(A, B, C, X.cpu().numpy(), F) <= 2 * tol
