@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
 template <typename TR>
 __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict__ F, const double* __restrict__ X,
                                                       const double* __restrict__ Cd, TR* __restrict__ r, int64_t N,
-                                                      int M, int64_t K, int64_t Kp, int first, int pass, int sp,
+                                                      int M, int64_t K, int64_t Kp, int pass, int sp,
                                                       IrState* st) {
+  constexpr int first = 0;
   if (st->done) return;
   const size_t plane = (size_t)N * Kp * M;
   const size_t MK = (size_t)M * K;
@@ -208,6 +209,67 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
   }
   block_add((double)acc, first ? &st->fn2 : &st->rn2[pass]);
   if (first) block_add((double)acc, &st->rn2[0]);
+}
+
+// The first residual (X = 0): F rounded into the block-transposed panel, one
+// warp per (block row, 16 rows m, 32 columns n); lane n writes 32 contiguous
+// bytes per BF16 plane (a full 32-byte sector) and accumulates ||F||^2.
+// HBM-bound: 8 bytes read and 2 sp (BF16) or 4 sp (FP32) bytes written per entry.
+template <typename TR>
+__global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F, TR* __restrict__ r, int64_t N, int M,
+                                                   int64_t K, int64_t Kp, int sp, IrState* st) {
+  if (st->done) return;
+  const size_t plane = (size_t)N * Kp * M;
+  const int lane = threadIdx.x % 32;
+  const int tn = (int)((Kp + 31) / 32), tm = M / 16;
+  const int64_t nitem = N * tm * tn;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  float acc = 0.f;
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
+    const int n = (int)(it % tn) * 32 + lane;
+    const int m0 = (int)((it / tn) % tm) * 16;
+    const int64_t j = it / ((int64_t)tn * tm);
+    if (n >= Kp) continue;
+    const double* fj = F + ((size_t)j * M + m0) * K + n;
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      v[q] = n < K ? f64_to_f32_rz(fj[(size_t)q * K]) : 0.f;
+      acc = fmaf(v[q], v[q], acc);
+    }
+    TR* o = r + ((size_t)j * Kp + n) * M + m0;
+    if constexpr (sizeof(TR) == 2) {
+      uint32_t h[8], l[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const float2 bf = __bfloat1622float2(b);
+        const __nv_bfloat162 c = __floats2bfloat162_rn(v[2 * q] - bf.x, v[2 * q + 1] - bf.y);
+        h[q] = *reinterpret_cast<const uint32_t*>(&b);
+        l[q] = *reinterpret_cast<const uint32_t*>(&c);
+      }
+      reinterpret_cast<uint4*>(o)[0] = make_uint4(h[0], h[1], h[2], h[3]);
+      reinterpret_cast<uint4*>(o)[1] = make_uint4(h[4], h[5], h[6], h[7]);
+      if (sp == 2) {
+        reinterpret_cast<uint4*>(o + plane)[0] = make_uint4(l[0], l[1], l[2], l[3]);
+        reinterpret_cast<uint4*>(o + plane)[1] = make_uint4(l[4], l[5], l[6], l[7]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hi[e] = sp == 2 ? __uint_as_float(__float_as_uint(v[4 * q + e]) & 0xFFFFE000u) : v[4 * q + e];
+          lo[e] = v[4 * q + e] - hi[e];
+        }
+        reinterpret_cast<float4*>(o)[q] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        if (sp == 2) reinterpret_cast<float4*>(o + plane)[q] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+  }
+  block_add((double)acc, &st->fn2);
+  block_add((double)acc, &st->rn2[0]);
 }
 
 // r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
@@ -322,10 +384,17 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
     if (trans) {  // the tensor-core panels: M is 64 or 128
-      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
-      const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
-      const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
-      k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, first, pass, sp, st);
+      if (first) {
+        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_round_rhs<TR>), 256, 0);
+        const int64_t items = h->N * (M / 16) * ((Kp + 31) / 32);
+        const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
+        k_round_rhs<TR><<<blocks, 256, 0, s>>>(F, r, h->N, M, K, Kp, sp, st);
+      } else {
+        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
+        const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
+        const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
+        k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st);
+      }
     } else {
       const size_t n = (size_t)h->N * M * K;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
