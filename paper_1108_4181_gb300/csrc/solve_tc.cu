@@ -1,31 +1,46 @@
 // Algorithm 2, stage 2 on the tcgen05 tensor cores (BF16 or TF32 operands,
 // FP32 accumulation in TMEM), used as the inner solve of iterative refinement.
 //
-// Internal panels (residual r, work panel holding y, W and X~) are stored
+// Internal panels (residual r, work panel holding y, W, F~ and X~) are stored
 // block-transposed: block row j of a panel is a K x M matrix, element (m, n)
-// at (j * Kp + n) * M + m, Kp = K rounded up to the column tile.  A column
-// tile of a block row is then an NT x M matrix with M contiguous: the K-major
-// B operand of the MMA for both BF16 and TF32.  Factor blocks are row-major
-// M x M: the K-major A operand.  Both are moved by TMA with 128-byte swizzle.
+// at (j * Kp + n) * M + m, Kp = K rounded up to 128.  A column tile of a
+// block row is then an NT x M matrix with M contiguous, and a factor block
+// (row-major M x M) is M rows with M contiguous: both are K-major operands
+// for BF16 and TF32, moved by TMA with 128-byte swizzle.
+//
+// Operand roles.  The default roles put the factor block in the MMA's A
+// operand (M rows) and the panel tile in B (NT columns).  The swapped roles
+// (Cfg SW, used for the split-BF16 precision) put the 128-column panel tile
+// in A and the factor block in B (N = M), so every MMA is 128 x M x 16 and
+// the accumulator holds the transposed product: TMEM lane = panel column,
+// one epilogue thread owns a contiguous column of the result.
 //
 // Split operands (SP = 2): every factor and panel value v is stored as two
 // planes hi = round(v), lo = round(v - hi), and each product is formed as
-// Ahi Bhi + Ahi Blo + Alo Bhi (three MMAs, FP32 accumulation), which carries
+// hi*hi + hi*lo + lo*hi (three MMAs, FP32 accumulation), which carries
 // about twice the operand precision (BF16: ~2^-17 instead of 2^-9) and cuts
 // the number of refinement passes.
 //
-//   k_tc_sweep    eq. sub3 per (segment, column tile), step 2.1:
-//                 forward  y_i = Dinv_i r_i + E_i y_{i-1},
-//                 backward W_i = y_i + G_i W_{i+1}.
-//                 Warp 0 streams factor slices and panel tiles with TMA into
-//                 rings, warp 1 issues the MMAs (one thread), warps 2-5 drain
-//                 the TMEM accumulator, write the next B operand into shared
-//                 memory and store the row with TMA.  Two accumulators let the
-//                 next row's MMA start while the previous one is drained.
-//   k_tc_iface / k_tc_dichotomy   step 2.2 on the CUDA cores in FP32 (a few
-//                 per cent of the flops: S (2 + depth) block products).
-//   k_tc_correct  eq. superposition, step 2.3: d_i = W_i + U_i X~_s +
-//                 V_i X~_{s+1} into an FP32 correction panel (TMA stores);
+//   k_tc_sweep       eq. sub3 per (segment, column tile), step 2.1:
+//                    forward  y_i = Dinv_i r_i + E_i y_{i-1} (with A_i = I:
+//                    Dinv_i (r_i + y_{i-1}) from the same Dinv slices),
+//                    backward W_i = y_i + G_i W_{i+1}.  Warp 0 streams factor
+//                    slices and panel tiles with TMA into rings, warp 1 issues
+//                    the MMAs (one thread), warps 2-9 drain the TMEM
+//                    accumulator, write the next recurrence operand into
+//                    shared memory and store the row with TMA.  Two
+//                    accumulators let the next row's MMAs start while the
+//                    previous row is drained.
+//   k_tc_ifgemm      step 2.2 (split BF16): jobs of up to two block products
+//                    plus an add -- F~ (eq. red1), the series terms R F~, and
+//                    one launch per dichotomy level (Algorithm 1) -- with the
+//                    node sums of the series terms from k_node_sums.
+//   k_tc_iface / k_tc_dichotomy   step 2.2 on the CUDA cores in FP32 for the
+//                    single-plane precisions.
+//   k_tc_correct_ta  eq. superposition, step 2.3 (split BF16, M = 128):
+//                    d_i = W_i + U_i X~_s + V_i X~_{s+1} with the two
+//                    interface tiles as TMEM A operands; k_tc_correct for the
+//                    other configurations.  d goes to an FP32 panel.
 //   k_x_update_warp  X (+)= d into the caller's FP64 solution.
 
 #include <cuda.h>
