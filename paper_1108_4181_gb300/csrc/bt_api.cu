@@ -103,6 +103,7 @@ static void destroy_handle(bt_handle_s* h) {
   if (h->rgraph.exec) cudaGraphExecDestroy(h->rgraph.exec);
   if (h->rgraph.graph) cudaGraphDestroy(h->rgraph.graph);
   if (h->rgraph.cap) cudaStreamDestroy(h->rgraph.cap);
+  if (h->rgraph.cap2) cudaStreamDestroy(h->rgraph.cap2);
   cudaSetDevice(prev);
   delete h;
 }

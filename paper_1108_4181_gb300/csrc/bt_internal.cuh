@@ -172,7 +172,8 @@ struct bt_handle_s {
     bool seen = false;  // the previous call had this key (capture on the next)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;  // private capture stream
+    cudaStream_t cap = nullptr;   // private capture streams (the graph, the loop body)
+    cudaStream_t cap2 = nullptr;
     bool broken = false;         // capture failed once: enqueue directly from then on
   } rgraph;
 

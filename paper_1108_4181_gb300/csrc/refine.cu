@@ -31,6 +31,7 @@ struct IrState {
   int last;                 // index of the last residual computed
   int solves;               // refinement solves performed after the first
   int kstatus;              // non-zero: a tensor-core kernel gave up a bounded wait
+  int cur;                  // slot of the next residual (advanced by every check)
 };
 
 template <typename T>
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
     r[e] = to_lp<TR>(v);
     acc += v * v;
   }
-  block_add(acc, first ? &st->fn2 : &st->rn2[pass]);
+  (void)pass;
+  block_add(acc, first ? &st->fn2 : &st->rn2[st->cur]);
   if (first) block_add(acc, &st->rn2[0]);
 }
 
@@ -207,7 +209,8 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
       }
     }
   }
-  block_add((double)acc, first ? &st->fn2 : &st->rn2[pass]);
+  (void)pass;
+  block_add((double)acc, first ? &st->fn2 : &st->rn2[st->cur]);
   if (first) block_add((double)acc, &st->rn2[0]);
 }
 
@@ -329,21 +332,31 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
       }
     }
   }
-  block_add(part, &st->rn2[pass]);
+  (void)pass;
+  block_add(part, &st->rn2[st->cur]);
 }
 
-__global__ void k_ir_check(IrState* st, int pass, double tol2) {
-  if (st->done) return;
-  st->last = pass;
-  if (pass == 0) return;
-  const double r2 = st->rn2[pass];
-  if (st->kstatus != 0) {
-    st->done = 3;  // a tensor-core kernel gave up: stop, report
-  } else if (r2 <= tol2 * st->fn2) {
-    st->done = 1;
-  } else if (pass >= 3 && r2 >= 0.9 * st->rn2[pass - 1] && st->rn2[pass - 1] >= 0.9 * st->rn2[pass - 2]) {
-    st->done = 2;  // two passes without a 10 % reduction: stalled
+// After every residual: records it, decides convergence (or a stall, or a
+// tensor-core timeout), advances the slot, and -- inside the CUDA graph --
+// sets the condition of the refinement loop: another pass runs while not
+// done and fewer than max_it refinement solves have run.
+__global__ void k_ir_check(IrState* st, double tol2, int max_it, cudaGraphConditionalHandle loop) {
+  const int pass = st->cur;
+  if (!st->done) {
+    st->last = pass;
+    if (pass > 0) {
+      const double r2 = st->rn2[pass];
+      if (st->kstatus != 0) {
+        st->done = 3;  // a tensor-core kernel gave up: stop, report
+      } else if (r2 <= tol2 * st->fn2) {
+        st->done = 1;
+      } else if (pass >= 3 && r2 >= 0.9 * st->rn2[pass - 1] && st->rn2[pass - 1] >= 0.9 * st->rn2[pass - 2]) {
+        st->done = 2;  // two passes without a 10 % reduction: stalled
+      }
+    }
   }
+  st->cur = pass + 1;
+  if (loop) cudaGraphSetConditional(loop, (st->done == 0 && pass >= 1 && pass < max_it + 1) ? 1u : 0u);
 }
 
 __global__ void k_count_solve(IrState* st) {
@@ -484,47 +497,100 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   const int* done = &st->done;
   const double tol2 = tol * tol;
 
-  // The whole refinement on stream q: residual and stage-2 solves for every
-  // pass up to max_it; after convergence the device flag turns the remaining
-  // launches into no-ops.
-  auto enqueue = [&](cudaStream_t q) -> bt_status {
-    BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), q));
-    auto residual = [&](int first, int pass) -> bt_status {
-      if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
-        return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
-                                              first, pass, st, q);
-      return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, pass, st, q);
-    };
-    auto inner = [&](int accumulate) -> bt_status {
-      if (tcore) {
-        TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : prec == BT_PREC_TF32 ? h->tc_fac_tf32 : h->tc_fac_bf16x3,
-                     h->lp_r, h->lp_d, reinterpret_cast<float*>(h->lp_c),
-                     reinterpret_cast<float*>(h->lp_x), Kp};
-        return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, q);
-      }
-      return solve_simt_f32(h, reinterpret_cast<float*>(h->lp_r), K, reinterpret_cast<float*>(h->lp_d),
-                            reinterpret_cast<float*>(h->lp_c), X, accumulate, done, q);
-    };
-    auto check = [&](int pass) {
-      ProfScope ps(h, q, "ir_check");
-      k_ir_check<<<1, 1, 0, q>>>(st, pass, tol2);
-    };
-    BT_TRY(residual(1, 0));
-    check(0);
-    BT_TRY(inner(0));
-    for (int pass = 1; pass <= max_it + 1; ++pass) {
-      BT_TRY(residual(0, pass));
-      check(pass);
-      if (pass <= max_it) {
-        {
-          ProfScope ps(h, q, "ir_check");
-          k_count_solve<<<1, 1, 0, q>>>(st);
-        }
-        BT_TRY(inner(1));
-      }
+  // The refinement as a prologue (F rounded, first solve, first residual and
+  // check) and a body (one refinement pass: solve, update, residual, check).
+  // Launched directly, the body is unrolled max_it times and passes after
+  // convergence return at once; in the CUDA graph it is the body of a
+  // device-side WHILE node whose condition the check kernel sets.
+  auto residual = [&](cudaStream_t q, int first) -> bt_status {
+    if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
+      return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
+                                            first, 0, st, q);
+    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, 0, st, q);
+  };
+  auto inner = [&](cudaStream_t q, int accumulate) -> bt_status {
+    if (tcore) {
+      TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : prec == BT_PREC_TF32 ? h->tc_fac_tf32 : h->tc_fac_bf16x3,
+                   h->lp_r, h->lp_d, reinterpret_cast<float*>(h->lp_c),
+                   reinterpret_cast<float*>(h->lp_x), Kp};
+      return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, q);
     }
+    return solve_simt_f32(h, reinterpret_cast<float*>(h->lp_r), K, reinterpret_cast<float*>(h->lp_d),
+                          reinterpret_cast<float*>(h->lp_c), X, accumulate, done, q);
+  };
+  auto check = [&](cudaStream_t q, cudaGraphConditionalHandle loop) {
+    ProfScope ps(h, q, "ir_check");
+    k_ir_check<<<1, 1, 0, q>>>(st, tol2, max_it, loop);
+  };
+  auto prologue = [&](cudaStream_t q, cudaGraphConditionalHandle loop) -> bt_status {
+    BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), q));
+    BT_TRY(residual(q, 1));
+    check(q, 0);
+    BT_TRY(inner(q, 0));
+    BT_TRY(residual(q, 0));
+    check(q, loop);
+    return BT_OK;
+  };
+  auto body = [&](cudaStream_t q, cudaGraphConditionalHandle loop) -> bt_status {
+    {
+      ProfScope ps(h, q, "ir_check");
+      k_count_solve<<<1, 1, 0, q>>>(st);
+    }
+    BT_TRY(inner(q, 1));
+    BT_TRY(residual(q, 0));
+    check(q, loop);
+    return BT_OK;
+  };
+  auto enqueue = [&](cudaStream_t q) -> bt_status {
+    BT_TRY(prologue(q, 0));
+    for (int it = 0; it < max_it; ++it) BT_TRY(body(q, 0));
     BT_CUDA(cudaGetLastError());
     return BT_OK;
+  };
+  // Captures prologue + WHILE(body) into *out; false (and nothing captured) on failure.
+  auto capture = [&](cudaGraph_t* out) -> bool {
+    bt_handle_s::RefineGraph& g = h->rgraph;
+    if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!g.cap2 && cudaStreamCreateWithFlags(&g.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    bool ok = true;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle loop = 0;
+    ok = ok && cudaStreamGetCaptureInfo(g.cap, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
+    ok = ok && cudaGraphConditionalHandleCreate(&loop, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    ok = ok && prologue(g.cap, loop) == BT_OK;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ok = ok && cudaStreamGetCaptureInfo(g.cap, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn = nullptr;
+    ok = ok && cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp) == cudaSuccess;
+    ok = ok && cudaStreamUpdateCaptureDependencies(g.cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                   cudaSuccess;
+    if (ok) {
+      cudaGraph_t bg = cp.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(g.cap2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+      if (ok) {
+        const bt_status bs = body(g.cap2, loop);
+        cudaGraph_t bg_out = nullptr;
+        ok = cudaStreamEndCapture(g.cap2, &bg_out) == cudaSuccess && bs == BT_OK;
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    const bool ended = cudaStreamEndCapture(g.cap, &graph) == cudaSuccess;
+    if (!(ok && ended && graph)) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return false;
+    }
+    *out = graph;
+    return true;
   };
 
   // CUDA graph: captured on the second consecutive call with the same
@@ -544,13 +610,9 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       if (g.graph) cudaGraphDestroy(g.graph);
       g.exec = nullptr;
       g.graph = nullptr;
-      if (!g.cap) BT_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
       cudaGraph_t graph = nullptr;
-      bool ok = cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      const bt_status qs = ok ? enqueue(g.cap) : BT_ERR_CUDA;
-      const cudaError_t ce = ok ? cudaStreamEndCapture(g.cap, &graph) : cudaErrorUnknown;
-      ok = ok && qs == BT_OK && ce == cudaSuccess && graph != nullptr &&
-           cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+      bool ok = capture(&graph);
+      ok = ok && cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
       if (ok) {
         g.graph = graph;
         BT_CUDA(cudaGraphLaunch(g.exec, s));
