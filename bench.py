@@ -196,7 +196,7 @@ TRAFFIC = {
     # mixed_solve_acoustic_N4096_M128_K512_S64.md); the kernel streams F and X
     # once per pass, so traffic scales with the unknowns
     "residual": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
-                 "sha256": "00933121f77c5aeb2006cbf9f4f3a96b8fc1c7eaa3fff7a7a45f8b7891d101eb",
+                 "sha256": "48b564ed045e2d9a0ef25b010efcf23d2d97023418e10e02598f551cb7941cef",
                  "bytes_per_unknown": 19.8262},
 }
 
