@@ -1127,8 +1127,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 template <class C, bool WR>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_correct_ta(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
-                    const __nv_bfloat16* __restrict__ wp, float* __restrict__ dp, int N, int L, int S, int Kp,
-                    int rows_per_cta, const int* done, int* status) {
+                    const __nv_bfloat16* __restrict__ wp, float* __restrict__ dp, double* __restrict__ Xo, int K,
+                    int N, int L, int S, int Kp, int rows_per_cta, const int* done, int* status) {
   using E = __nv_bfloat16;
   static_assert(C::SW && C::SP == 2 && C::M == 128 && C::MH == 64, "split BF16, M = 128, swapped roles");
   constexpr int TCOLS = 4 * C::M;
@@ -1239,6 +1239,28 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     const int m0 = g * C::MH;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const size_t wplane = (size_t)N * Kp * C::M;
+    // Xo != nullptr (the first solve): the result is the solution itself,
+    // written as FP64 rows of the row-major X (exact widening; for each block
+    // row m the warp's 32 columns are 256 contiguous bytes) instead of the
+    // FP32 correction panel
+    auto store_row = [&](const float (&v)[C::MH], int irow) {
+      if (Xo != nullptr) {
+        const int n = n0 + nl;
+        if (n < K) {
+          double* x = Xo + ((size_t)irow * C::M + m0) * K + n;
+#pragma unroll
+          for (int q0 = 0; q0 < C::MH; q0 += 16) {
+#pragma unroll
+            for (int q = q0; q < q0 + 16; ++q) x[(size_t)q * K] = f32_to_f64(v[q]);
+            asm volatile("" ::: "memory");  // one batch of stores at a time
+          }
+        }
+      } else {
+        float4* o = reinterpret_cast<float4*>(dp + ((size_t)irow * Kp + n0 + nl) * C::M + m0);
+#pragma unroll
+        for (int q = 0; q < C::MH / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    };
     // the A operands: rows s*L and (s+1)*L of the work panel into TMEM
     for (int q = 0; q < 2; ++q) {
       if (q == 1 && !has_next) break;
@@ -1261,9 +1283,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         for (int u = 0; u < NU; ++u)
           unpack16_add<E, 2>(make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]),
                              make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]), &v[u * per16]);
-        float4* o = reinterpret_cast<float4*>(dp + ((size_t)s * L * Kp + n0 + nl) * C::M + m0);
-#pragma unroll
-        for (int e = 0; e < C::MH / 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        store_row(v, s * L);
       }
     }
     tc_fence_before();
@@ -1308,11 +1328,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 #pragma unroll
         for (int u = 0; u < NU; ++u) unpack16_add<E, 2>(whi[u], wlo[u], &v[u * per16]);
       }
-      if (ok) {
-        float4* o = reinterpret_cast<float4*>(dp + ((size_t)i * Kp + n0 + nl) * C::M + m0);
-#pragma unroll
-        for (int q = 0; q < C::MH / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
+      if (ok) store_row(v, i);
     }
     if (!ok && threadIdx.x == 64) atomicExch(status, 6);
   }
@@ -1845,8 +1861,10 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       const size_t smem = 1024 + CT::NA * CT::SLOT + CT::NP * CT::PT + kBars(CT::NA, CT::NP) * 8 + 16;
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct_ta<CT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       ProfScope ps(h, st, "tc_correct");
+      // first solve: X = d written by the correction itself (no FP32 round trip)
       k_tc_correct_ta<CT, true><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(
-          tm_fac_c, tm_wc, (const E*)w, tb.d, N, L, S, Kp, L > 1 ? rpc : 0, done, status);
+          tm_fac_c, tm_wc, (const E*)w, tb.d, accumulate ? nullptr : X, (int)K, N, L, S, Kp, L > 1 ? rpc : 0, done,
+          status);
     } else {
       const size_t smem = correct_smem<CC>();
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1867,7 +1885,8 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
                                  L > 1 ? rpc : 0, cs_corr, done, status));
     }
     BT_CUDA(cudaGetLastError());
-    {  // M is 64 or 128
+    const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && !accumulate;
+    if (!direct_x) {  // M is 64 or 128
       const int64_t nitem = (int64_t)((K + 31) / 32) * (M / 8) * N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update_warp), 256, 0);
       const int blocks = (int)std::min<int64_t>((nitem + 7) / 8, grid);
