@@ -230,9 +230,12 @@ def _kernel_work(name, prof, steps, info, precision):
         # the first residual (X = 0): F read, rounded into the low-precision panel
         pb0 = (2 if precision == "bf16x3" else 1) * (4 if precision in ("tf32", "f32") else 2)
         return "hbm", NMK * (8.0 + pb0), "B"
+    # split BF16 with M = 128: the first solve's correction writes X itself
+    direct_first = precision == "bf16x3" and M == 128
     if name == "x_update":
-        # X = d (first solve), X += d: FP32 d + FP64 X read, FP64 X written
-        return "hbm", NMK * (12.0 + 20.0 * (full - 1)), "B"
+        # X = d (first solve, unless the correction wrote X), X += d: FP32 d and
+        # FP64 X read, FP64 X written
+        return "hbm", NMK * ((0.0 if direct_first else 12.0) + 20.0 * (full - 1)), "B"
     planes = 2 if precision == "bf16x3" else 1
     eb = 4 if precision == "tf32" else 2
     pb = planes * eb  # bytes of one panel entry
@@ -243,8 +246,10 @@ def _kernel_work(name, prof, steps, info, precision):
         # E, G per interior row
         return "hbm", full * (4.0 * pb * NMK + 3.0 * fb * (N - S)), "B"
     if name == "tc_correct":
-        # W in, d (FP32) out, U, V per interior row
-        return "hbm", full * ((pb + 4.0) * NMK + 2.0 * fb * (N - S)), "B"
+        # W in, d (FP32) out -- X (FP64) out in the first solve when the
+        # correction writes it -- U, V per interior row
+        first_out = 8.0 if direct_first else 4.0
+        return "hbm", NMK * ((pb + first_out) + (full - 1) * (pb + 4.0)) + full * 2.0 * fb * (N - S), "B"
     return None
 
 
