@@ -101,7 +101,7 @@ __host__ __device__ constexpr int pow2ceil(int v) {
 // it reads and writes the K-major panel tiles in 16-byte vectors.  Both
 // operands keep the K-major 128-byte-swizzled smem layout of the default
 // roles (factor slice: rows x 128 B; panel tile: NT rows x 128 B per chunk).
-template <typename E, int M_, int NT_, int NA_, int SP_, int NP_ = 2, bool SW_ = false>
+template <typename E, int M_, int NT_, int NA_, int SP_, int NP_ = 2, bool SW_ = false, int EG_ = 2>
 struct Cfg {
   static constexpr int M = M_, NT = NT_, NA = NA_, SP = SP_, NP = NP_;  // NP: panel-ring stages
   static constexpr bool SW = SW_;
@@ -117,7 +117,7 @@ struct Cfg {
   static constexpr int ACC = SW ? M : NT;         // TMEM columns of one accumulator buffer
   static constexpr int TMEM_COLS = pow2ceil(2 * ACC);
   static constexpr uint32_t IDESC = SW ? instr_desc(ET<E>::fmt, 0, NT, M) : instr_desc(ET<E>::fmt, 0, M, NT);
-  static constexpr int EG = 2;                  // epilogue warp groups, each drains ACC/EG columns
+  static constexpr int EG = EG_;                // epilogue warp groups, each drains ACC/EG columns
   static constexpr int NH = NT / EG;            // default roles: tile columns per epilogue thread
   static constexpr int MH = M / EG;             // swapped roles: block rows per epilogue thread
   static constexpr int YB = SW ? 1 : 2;         // recurrence-operand buffers of the sweep
