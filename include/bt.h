@@ -47,7 +47,7 @@ typedef enum {
   BT_ERR_NOCONV = 4,      /* iterative refinement did not reach the requested tolerance */
   BT_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
   BT_ERR_OOM = 6,         /* device memory allocation failed */
-  BT_ERR_UNSUPPORTED = 7  /* valid request that this build does not implement */
+  BT_ERR_UNSUPPORTED = 7  /* valid request that the library does not implement */
 } bt_status;
 
 typedef enum {
