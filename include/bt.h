@@ -67,7 +67,10 @@ typedef struct {
   double tol;         /* target ||F - P X||_F / ||F||_F (0 = default 1e-10) */
   void* stream;       /* cudaStream_t */
   int32_t k_tile;     /* right-hand-side columns per CTA (0 = automatic) */
-  int32_t reserved;
+  int32_t residual;   /* how F - P X is formed: 0 automatic (2 where it applies,
+                         else 1), 1 FP64 on the CUDA cores, 2 exactly on the
+                         tensor cores from BF16 digit slices (dense blocks,
+                         M = 64 or 128; BT_ERR_UNSUPPORTED otherwise) */
 } bt_opts;
 
 /* Result report of bt_solve_ex (filled only when a non-NULL pointer is given;
@@ -137,6 +140,26 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
  * All device pointers, FP64.  Asynchronous on `stream`, except that the first
  * call on a handle factors P^T and synchronises once.
  */
+/*
+ * bt_residual -- r = F - P X for the factored operator (eq. (1) with the
+ * blocks given to bt_factor), the quantity the refinement of bt_solve_ex
+ * drives to zero; the paper has no counterpart.  F, X: device [N][M][K]
+ * (read only); R: device [N][M][K] output (may alias neither).  method:
+ *   0  automatic (2 where it applies, else 1),
+ *   1  FP64 on the CUDA cores,
+ *   2  on the tensor cores: every value of the operator rows and of X is
+ *      split into seven balanced base-128 digits (one power-of-two scale per
+ *      operator row, one per column of X), the digit products are summed
+ *      exactly in FP32, and the sums are combined with F in 64-bit integer
+ *      arithmetic.  Error per entry at most 7.5 M 2^(e_A + e_X - 49), e_A and
+ *      e_X the scales (2^e_A > the row's largest |A|, |B|, |C| entry, 2^e_X >
+ *      the column's largest |X| entry).  Dense blocks with M = 64 or 128 only
+ *      (BT_ERR_UNSUPPORTED otherwise).
+ * norm2 (host, may be NULL) receives ||r||_F^2.  Synchronises `stream`.
+ */
+bt_status bt_residual(bt_handle h, const double* F, const double* X, int64_t K, double* R, int32_t method,
+                      double* norm2, void* stream);
+
 bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF,
                            double* dA, double* dB, double* dC, void* stream);
 

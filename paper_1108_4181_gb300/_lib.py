@@ -19,6 +19,7 @@ STATUS_NAMES = {
     5: "BT_ERR_TIMEOUT", 6: "BT_ERR_OOM", 7: "BT_ERR_UNSUPPORTED",
 }
 PREC = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3, "bf16x3": 4}
+RESIDUAL = {"auto": 0, "fp64": 1, "digits": 2}
 
 # Every symbol declared in include/bt.h, with (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -28,7 +29,7 @@ _i32 = ctypes.c_int32
 
 class BtOpts(ctypes.Structure):
     _fields_ = [("precision", _i32), ("max_it", _i32), ("tol", ctypes.c_double), ("stream", _vp),
-                ("k_tile", _i32), ("reserved", _i32)]
+                ("k_tile", _i32), ("residual", _i32)]
 
 
 class BtInfo(ctypes.Structure):
@@ -45,6 +46,7 @@ SIGNATURES = {
     "bt_solve": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "bt_solve_ex": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(BtOpts), ctypes.POINTER(BtInfo)]),
     "bt_solve_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "bt_residual": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp]),
     "bt_destroy": (None, [_vp]),
     "bt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "bt_last_error": (ctypes.c_char_p, []),

@@ -98,7 +98,8 @@ static void destroy_handle(bt_handle_s* h) {
   h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
-  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam})
+  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam, h->dg_fac,
+                  static_cast<void*>(h->dg_ea), h->dg_x, h->dg_col})
     if (q) cudaFree(q);
   if (h->rgraph.exec) cudaGraphExecDestroy(h->rgraph.exec);
   if (h->rgraph.graph) cudaGraphDestroy(h->rgraph.graph);
@@ -243,6 +244,10 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
     set_error("bt_solve_ex: unknown precision");
     return BT_ERR_ARG;
   }
+  if (o.residual < 0 || o.residual > 2) {
+    set_error("bt_solve_ex: unknown residual method");
+    return BT_ERR_ARG;
+  }
   const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
   const char* f0 = reinterpret_cast<const char*>(F);
   const char* x0 = reinterpret_cast<const char*>(X);
@@ -251,6 +256,28 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
     return BT_ERR_ARG;
   }
   return solve_refined(h, F, K, X, o, info);
+}
+
+bt_status bt_residual(bt_handle h, const double* F, const double* X, int64_t K, double* R, int32_t method,
+                      double* norm2, void* stream) {
+  if (!h || !F || !X || !R || K < 1) {
+    set_error("bt_residual: need a handle, device F, X and R, K >= 1");
+    return BT_ERR_ARG;
+  }
+  if (method < 0 || method > 2) {
+    set_error("bt_residual: unknown method");
+    return BT_ERR_ARG;
+  }
+  const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
+  const char* r0 = reinterpret_cast<const char*>(R);
+  for (const double* p : {F, X}) {
+    const char* q = reinterpret_cast<const char*>(p);
+    if (r0 < q + bytes && q < r0 + bytes) {
+      set_error("bt_residual: R must not overlap F or X");
+      return BT_ERR_ARG;
+    }
+  }
+  return residual_diag(h, F, X, K, R, method, norm2, (cudaStream_t)stream);
 }
 
 bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_t K, double* dF, double* dA,

@@ -161,13 +161,24 @@ struct bt_handle_s {
   void* ir_state = nullptr;
   int lp_gen = 0;  // bumped whenever a refinement buffer is reallocated
 
+  // Exact tensor-core residual (dense blocks, M = 64 or 128): digit slices of
+  // the operator rows [3N][7][M][M] (BF16) and their row scales [N][M], built
+  // on first use; digit slices of X [7][N][Kp][M] and the per-column maxima
+  // and scales [Kp], grown on demand.
+  void* dg_fac = nullptr;
+  int* dg_ea = nullptr;
+  void* dg_x = nullptr;
+  size_t dg_x_bytes = 0;
+  void* dg_col = nullptr;
+  size_t dg_col_bytes = 0;
+
   // The refined solve captured as a CUDA graph: replayed when a call repeats
   // the previous call's arguments (and no buffer moved since the capture).
   struct RefineGraph {
     const double* F = nullptr;
     double* X = nullptr;
     int64_t K = 0;
-    int precision = -1, max_it = 0, gen = -1;
+    int precision = -1, max_it = 0, gen = -1, resid = -1;
     double tol = 0.0;
     bool seen = false;  // the previous call had this key (capture on the next)
     cudaGraph_t graph = nullptr;
@@ -281,6 +292,24 @@ int resident_grid(const void* fn, int threads, size_t smem);
 bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const double* const* F, const int64_t* K,
                       double* const* X, const bt_opts& o);
 bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
+
+// Exact residual on the tensor cores (resid_digits.cu): whether it applies to
+// the handle for K columns; the digit slices of the operator (once) and the
+// scratch for K columns (outside any stream capture); and one residual:
+// out_mode 0 -- the tensor-core panel (planes sp, BF16, or FP32 if tr_float,
+// leading dimension K rounded up to 128), 1 -- row-major FP32, 2 -- row-major
+// FP64; its squared norm is added to rn2[*cur] (rn2[0] if cur is NULL).
+// Every kernel returns at once when *done != 0.
+bool resid_digits_supported(const bt_handle_s* h, int64_t K);
+bt_status resid_digits_prepare(bt_handle_s* h, int64_t K, cudaStream_t st);
+bt_status launch_resid_digits(bt_handle_s* h, const double* F, const double* X, int64_t K, int out_mode,
+                              bool tr_float, void* out, int sp, const int* done, double* rn2, const int* cur,
+                              int* status, cudaStream_t st);
+
+// bt_residual: r = F - P X into R (row-major FP64) by `method` (0 automatic,
+// 1 FP64 CUDA cores, 2 tensor-core digits); ||r||_F^2 to *norm2 if non-NULL.
+bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_t K, double* R, int method,
+                        double* norm2, cudaStream_t st);
 
 // Mixed-precision solve with iterative refinement (bt_solve_ex).
 bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info);

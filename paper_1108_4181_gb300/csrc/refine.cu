@@ -40,6 +40,8 @@ template <>
 __device__ __forceinline__ float to_lp<float>(double v) { return f64_to_f32_rz(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <>
+__device__ __forceinline__ double to_lp<double>(double v) { return v; }
 
 __device__ __forceinline__ void block_add(double v, double* target) {
   __shared__ double red[32];
@@ -90,6 +92,7 @@ __device__ __forceinline__ void put_planes(__nv_bfloat16* r, size_t idx, size_t 
   r[idx] = hi;
   if (sp == 2) r[idx + plane] = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
+__device__ __forceinline__ void put_planes(double* r, size_t idx, size_t, int, float v) { r[idx] = v; }
 __device__ __forceinline__ void put_planes(float* r, size_t idx, size_t plane, int sp, float v) {
   if (sp == 2) {
     const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
@@ -391,8 +394,11 @@ bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
 // block-transposed (ld = Kp) for the tensor-core solve.
 template <typename TR>
 bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
-                          int sp, int first, int pass, IrState* st, cudaStream_t s) {
+                          int sp, int first, int pass, IrState* st, bool digits, cudaStream_t s) {
   const int M = (int)h->M;
+  if (digits && !first)  // dense blocks: the exact residual on the tensor cores
+    return launch_resid_digits(h, F, X, K, trans ? 0 : 1, sizeof(TR) == 4, r, sp, &st->done, st->rn2, &st->cur,
+                               &st->kstatus, s);
   // the first pass (X = 0) only rounds F into the panel: timed under its own name
   ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
@@ -481,7 +487,15 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     Kp = (K + nt - 1) / nt * nt;
     eb = prec == BT_PREC_TF32 ? 4 : 2;
   }
-  const void* before[4] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x};
+  // residual: 0 automatic (the tensor-core digit residual where it applies),
+  // 1 FP64 on the CUDA cores, 2 the tensor-core digit residual
+  const bool dig_ok = resid_digits_supported(h, K);
+  if (o.residual == 2 && !dig_ok) {
+    set_error("bt_solve_ex: the tensor-core residual needs dense blocks with M = 64 or M = 128");
+    return BT_ERR_UNSUPPORTED;
+  }
+  const bool digits = o.residual == 2 || (o.residual == 0 && dig_ok);
+    const void* before[4] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x};
   const size_t panel = (size_t)sp * h->N * M * Kp * eb;
   // series terms [depth][S] and, for the tensor-core step 2.2, one node sum per tree node
   const size_t cbytes = ((size_t)h->depth * h->S + h->nodes.size()) * M * Kp * sizeof(float);
@@ -491,6 +505,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   if (tcore) BT_TRY(grow(&h->lp_x, &h->lp_x_bytes, (size_t)h->N * M * Kp * sizeof(float), s));
   if (before[0] != h->lp_r || before[1] != h->lp_d || before[2] != h->lp_c || before[3] != h->lp_x) ++h->lp_gen;
   if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
+  if (digits) BT_TRY(resid_digits_prepare(h, K, s));
   BT_TRY(make_f32_factors(h, s));
   if (tcore) BT_TRY(make_tc_factors(h, prec, s));
   IrState* st = reinterpret_cast<IrState*>(h->ir_state);
@@ -505,8 +520,9 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   auto residual = [&](cudaStream_t q, int first) -> bt_status {
     if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
       return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
-                                            first, 0, st, q);
-    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, 0, st, q);
+                                            first, 0, st, digits, q);
+    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, 0, st, digits,
+                                  q);
   };
   auto inner = [&](cudaStream_t q, int accumulate) -> bt_status {
     if (tcore) {
@@ -599,7 +615,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   // the launches directly.
   bt_handle_s::RefineGraph& g = h->rgraph;
   const bool same = g.F == F && g.X == X && g.K == K && g.precision == prec && g.tol == tol && g.max_it == max_it &&
-                    g.gen == h->lp_gen;
+                    g.gen == h->lp_gen && g.resid == (digits ? 1 : 0);
   bool launched = false;
   if (!h->prof.on && !g.broken) {
     if (same && g.exec) {
@@ -634,6 +650,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     g.tol = tol;
     g.max_it = max_it;
     g.gen = h->lp_gen;
+    g.resid = digits ? 1 : 0;
     g.seen = true;
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
@@ -658,6 +675,50 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       return BT_ERR_NOCONV;
     }
   }
+  return BT_OK;
+}
+
+bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_t K, double* R, int method,
+                        double* norm2, cudaStream_t s) {
+  const bool dig_ok = resid_digits_supported(h, K);
+  if (method == 0) method = dig_ok ? 2 : 1;
+  if (method == 2 && !dig_ok) {
+    set_error("bt_residual: the tensor-core residual needs dense blocks with M = 64 or M = 128");
+    return BT_ERR_UNSUPPORTED;
+  }
+  if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
+  IrState* st = reinterpret_cast<IrState*>(h->ir_state);
+  BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), s));
+  if (method == 2) {
+    BT_TRY(resid_digits_prepare(h, K, s));
+    BT_TRY(launch_resid_digits(h, F, X, K, 2, false, R, 1, &st->done, st->rn2, nullptr, &st->kstatus, s));
+  } else {
+    const int M = (int)h->M;
+    if (h->stencil) {
+      const size_t n = (size_t)h->N * M * K;
+      k_resid_stencil<double><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+          F, X, h->Cdiag, R, h->N, M, K, 0, 0, st);
+    } else {
+      constexpr int CW = 4;
+      const int CG = std::max(1, std::min(1024 / M, std::max(1, 128 / M)));
+      const int kt = CW * CG;
+      const size_t smem = 3 * (size_t)M * kt * sizeof(double);
+      if (smem > 48 * 1024)
+        BT_CUDA(cudaFuncSetAttribute(k_resid_dense<double, CW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+      k_resid_dense<double, CW, false><<<dim3((unsigned)h->N, (unsigned)((K + kt - 1) / kt)), M * CG, smem, s>>>(
+          F, X, h->A, h->B, h->C, R, h->N, M, K, K, 0, 1, st);
+    }
+    BT_CUDA(cudaGetLastError());
+  }
+  IrState hs;
+  BT_CUDA(cudaMemcpyAsync(&hs, st, sizeof(IrState), cudaMemcpyDeviceToHost, s));
+  BT_CUDA(cudaStreamSynchronize(s));
+  if (hs.kstatus != 0) {
+    set_error("bt_residual: a tensor-core kernel gave up a bounded wait (code " + std::to_string(hs.kstatus) + ")");
+    return BT_ERR_TIMEOUT;
+  }
+  if (norm2) *norm2 = hs.rn2[0];
   return BT_OK;
 }
 

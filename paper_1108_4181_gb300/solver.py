@@ -69,8 +69,12 @@ class Factorization:
     # -- stage 2 -------------------------------------------------------------
     def solve(self, F: torch.Tensor, precision: str = "f64", tol: float = 0.0, max_it: int = 0,
               k_tile: int = 0, out: Optional[torch.Tensor] = None, return_info: bool = False,
-              stream: Optional[torch.cuda.Stream] = None):
+              stream: Optional[torch.cuda.Stream] = None, residual: str = "auto"):
         """X = P^{-1} F.  F: [N, M, K] float64.
+
+        residual (refined precisions): how F - P X is formed -- "fp64" on the
+        CUDA cores, "digits" exactly on the tensor cores (dense blocks, M = 64
+        or 128), "auto" the latter where it applies.
 
         A CUDA tensor is solved in place on the device.  A CPU tensor is the
         end-to-end path: it is copied to the device (through pinned memory when
@@ -86,7 +90,8 @@ class Factorization:
         K = Fd.shape[2]
         X = out if (out is not None and not host) else torch.empty_like(Fd)
         opts = _lib.BtOpts(precision=_lib.PREC[precision], max_it=int(max_it), tol=float(tol),
-                           stream=_stream_ptr(stream, self.device), k_tile=int(k_tile), reserved=0)
+                           stream=_stream_ptr(stream, self.device), k_tile=int(k_tile),
+                           residual=_lib.RESIDUAL[residual])
         info = _lib.BtInfo()
         st = _lib.load().bt_solve_ex(self._h, _ptr(Fd), K, _ptr(X), ctypes.byref(opts),
                                      ctypes.byref(info) if return_info else None)
@@ -99,6 +104,23 @@ class Factorization:
             return X, dict(iters=info.iters, converged=bool(info.converged), rel_res=info.rel_res,
                            rel_res0=info.rel_res0)
         return X
+
+    def residual(self, F: torch.Tensor, X: torch.Tensor, method: str = "auto",
+                 stream: Optional[torch.cuda.Stream] = None):
+        """(R, ||R||_F^2) with R = F - P X ([N, M, K] float64, on the device).
+
+        method: "fp64" (CUDA cores), "digits" (exact digit products on the
+        tensor cores; dense blocks, M = 64 or 128), "auto"."""
+        F = _as_device_f64(self._panel(F, "F"), self.device, "F")
+        X = _as_device_f64(self._panel(X, "X"), self.device, "X")
+        if F.shape != X.shape:
+            raise ValueError("F and X must have the same shape")
+        R = torch.empty_like(F)
+        n2 = ctypes.c_double()
+        st = _lib.load().bt_residual(self._h, _ptr(F), _ptr(X), F.shape[2], _ptr(R), _lib.RESIDUAL[method],
+                                     ctypes.byref(n2), _stream_ptr(stream, self.device))
+        _lib.check(st, "bt_residual")
+        return R, n2.value
 
     def solve_stages(self, F: torch.Tensor, stages: int, X: Optional[torch.Tensor] = None,
                      stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
@@ -195,7 +217,7 @@ class BatchPlan:
         self.facs, self.Fs, self.Xs = list(facs), list(Fs), list(Xs)  # keep alive
         self.device = self.facs[0].device
         H, Fp, K, Xp = _batch_arrays(self.facs, self.Fs, self.Xs)
-        opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=None, k_tile=int(k_tile), reserved=0)
+        opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=None, k_tile=int(k_tile), residual=0)
         self._b = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(_lib.load().bt_batch_create(len(self.facs), H, Fp, K, Xp, ctypes.byref(opts),
@@ -230,7 +252,7 @@ def solve_batched(facs, Fs, Xs=None, k_tile: int = 0, stream: Optional[torch.cud
     H, Fp, K, Xp = _batch_arrays(facs, Fs, Xs)
     dev = facs[0].device
     opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=_stream_ptr(stream, dev), k_tile=int(k_tile),
-                       reserved=0)
+                       residual=0)
     with torch.cuda.device(dev):
         _lib.check(_lib.load().bt_solve_batched(len(facs), H, Fp, K, Xp, ctypes.byref(opts)), "bt_solve_batched")
     return Xs
