@@ -531,7 +531,8 @@ def run_batched(args):
                    "launch": f"one persistent cooperative launch per step ({plan.ctas} CTAs, {plan.items} items, "
                              f"{plan.stages} stages), CUDA graph replay: {bool(plan.graph)}"},
         "mixed_bf16x3": {"value": unknowns / (msmx * 1e-3), "ms_per_step": msmx, "steps": k_mixed,
-                         "path": "bt_solve_ex per set (split-BF16 tensor cores, dense FP64 residual, tol 1e-10)"},
+                         "path": "bt_solve_ex per set (split-BF16 tensor cores; residual exact on the tensor "
+                                 "cores from BF16 digit slices; tol 1e-10)"},
         "speedup_mixed_vs_fp64": ms64 / msmx,
         "accuracy_sampled_columns": worst,
         "clocks": clk.summary(),

@@ -37,9 +37,9 @@
 // operands and the dropped pairs) plus half a unit u.
 //
 //   k_fac_digits    factor digits [3N][7][M][M] and e_A (once per handle)
-//   k_colmax        largest |X| of every column
+//   k_colmax        largest |X| of every column (its exponent)
 //   k_x_digits      X digits, block-transposed [7][N][Kp][M], and e_X
-//   k_resid_digits  persistent: TMA warp, MMA warp, 8 epilogue warps
+//   k_resid_digits  persistent: TMA warp, MMA warp, 16 epilogue warps
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -63,7 +63,9 @@ constexpr int NX = 4;           // X-digit tile ring slots
 constexpr int XT = 128 * 128;   // one X-digit tile: 128 columns x 64 contraction values (BF16)
 constexpr int FSL = 64 * 128;   // one factor digit slice: 64 rows x 64 contraction values
 constexpr int FST = ND * FSL;   // the 7 slices of one factor block and contraction chunk
-constexpr int THREADS = 320;    // TMA warp, MMA warp, 8 epilogue warps
+constexpr int EGW = 4;          // epilogue warps per TMEM lane quarter (rows of an output half split EGW ways)
+constexpr int RPT = 64 / EGW;   // output rows per epilogue thread
+constexpr int THREADS = 64 + 128 * EGW;  // TMA warp, MMA warp, 4 EGW epilogue warps
 constexpr int ACC = 64;         // TMEM columns of one accumulator
 constexpr int TMEM_COLS = 512;  // 7 accumulators (448 columns)
 constexpr int NBARS = 4 + 2 * NX + 3;
@@ -191,25 +193,35 @@ __global__ void k_fac_digits(const double* __restrict__ A, const double* __restr
   }
 }
 
-__global__ void k_zero_u64(unsigned long long* p, int64_t n, const int* done) {
+__global__ void k_zero_u32(unsigned* p, int64_t n, const int* done) {
   if (done != nullptr && *(volatile const int*)done != 0) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0ull;
+    p[i] = 0u;
 }
 
-// Largest |X| of every column (bit pattern, sign cleared) over the N*M rows:
+// Largest |X| of every column over the N*M rows, as the high word of its bit
+// pattern with the sign cleared (the exponent field is all the scale needs):
 // lanes on consecutive columns, the 8 warps of a CTA and the CTAs of grid.y on
-// interleaved rows, one atomic per column and CTA.
+// interleaved rows, four loads in flight per lane, one atomic per column and
+// CTA.  32-bit integer maxima only (64-bit ones occupy the FP64 pipe).
 __global__ void __launch_bounds__(256) k_colmax(const double* __restrict__ X, int64_t rows, int64_t K,
-                                                unsigned long long* __restrict__ cm, const int* done) {
+                                                unsigned* __restrict__ cm, const int* done) {
   if (done != nullptr && *(volatile const int*)done != 0) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t col = (int64_t)blockIdx.x * 32 + lane;
-  unsigned long long mx = 0;
-  if (col < K)
-    for (int64_t r = (int64_t)blockIdx.y * 8 + w; r < rows; r += (int64_t)gridDim.y * 8)
-      mx = max(mx, (unsigned long long)__double_as_longlong(__ldg(X + r * K + col)) & 0x7FFFFFFFFFFFFFFFull);
-  __shared__ unsigned long long s[8][32];
+  const unsigned* xh = reinterpret_cast<const unsigned*>(X) + 1;  // high words
+  unsigned mx = 0;
+  if (col < K) {
+    const int64_t stride = (int64_t)gridDim.y * 8;
+    int64_t r = (int64_t)blockIdx.y * 8 + w;
+    for (; r + 3 * stride < rows; r += 4 * stride) {
+      const unsigned a = __ldg(xh + 2 * (r * K + col)), b = __ldg(xh + 2 * ((r + stride) * K + col));
+      const unsigned c = __ldg(xh + 2 * ((r + 2 * stride) * K + col)), d = __ldg(xh + 2 * ((r + 3 * stride) * K + col));
+      mx = max(mx, max(max(a & 0x7FFFFFFFu, b & 0x7FFFFFFFu), max(c & 0x7FFFFFFFu, d & 0x7FFFFFFFu)));
+    }
+    for (; r < rows; r += stride) mx = max(mx, __ldg(xh + 2 * (r * K + col)) & 0x7FFFFFFFu);
+  }
+  __shared__ unsigned s[8][32];
   s[w][lane] = mx;
   __syncthreads();
   if (w == 0 && col < K) {
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(256) k_colmax(const double* __restrict__ X, in
 // e_X(n) to ex[n].
 template <int M>
 __global__ void __launch_bounds__(256) k_x_digits(const double* __restrict__ X, int64_t N, int64_t K, int64_t Kp,
-                                                  const unsigned long long* __restrict__ cm,
+                                                  const unsigned* __restrict__ cm,
                                                   __nv_bfloat16* __restrict__ xd, int* __restrict__ ex,
                                                   const int* done) {
   if (done != nullptr && *(volatile const int*)done != 0) return;
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(256) k_x_digits(const double* __restrict__ X, 
     const int64_t j = b / nblk;
     const int64_t n0 = (b % nblk) * CB;
     const int64_t n = n0 + c;
-    const int e = n < K ? scale_of(cm[n]) : 0;
+    const int e = n < K ? scale_of((unsigned long long)cm[n] << 32) : 0;
     const bool zero = n >= K || e == kBadScale;
     if (j == 0 && kg == 0) ex[n] = e;
     const double* src = X + ((size_t)j * M + kg * 8) * K + n;
@@ -312,8 +324,9 @@ __device__ __forceinline__ void store8(float* o, const float* v, int sp, size_t 
 enum { OUT_PANEL = 0, OUT_ROWS = 1, OUT_F64 = 2 };
 
 // Items (block row j, 128-column tile, 64-row half h of the output block),
-// j fastest so that the CTAs at work at one time share the X-digit tiles of
-// neighbouring block rows in L2.  Per item: for each of the (up to) three
+// the tiles of a block row consecutive: the CTAs at work at one time share the
+// factor digit slices of their block rows and the X-digit tiles of
+// neighbouring block rows in L2, so each is read from HBM about once.  Per item: for each of the (up to) three
 // blocks and each 64-value contraction chunk, the 7 factor digit slices (one
 // 4-D TMA box) and the 7 X-digit tiles; 40 MMAs per chunk.
 template <int M, int OUT, typename TR>
@@ -354,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&emptyX[i], 1);
     }
     mbar_init(accFull, 1);
-    mbar_init(accEmpty, 8);
+    mbar_init(accEmpty, 4 * EGW);
     mbar_init(drain, 1);
     fence_mbar_init();
   }
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int h = (int)(it % MH);
         const int64_t t = it / MH;
-        const int j = (int)(t % N), tile = (int)(t / N);
+        const int tile = (int)(t % tiles), j = (int)(t / tiles);
         for (int b = 0; b < 3 && ok; ++b) {
           if ((b == 0 && j == 0) || (b == 1 && j == N - 1)) continue;
           const int jx = b == 0 ? j - 1 : b == 1 ? j + 1 : j;
@@ -419,8 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t fi = 0, xi = 0, n = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++n) {
-        const int64_t t = it / MH;
-        const int j = (int)(t % N);
+        const int j = (int)(it / MH / tiles);
         if (n > 0 && !mbar_wait(accEmpty, (n - 1) & 1)) {
           ok = false;
           break;
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_wait(drain, 0);
     }
   } else {
-    const int qd = warp & 3, g = (warp - 2) >> 2;
+    const int qd = warp & 3, g = (warp - 2) >> 2;  // lane quarter, row group
     const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
     const size_t plane = (size_t)N * Kp * M;
     uint32_t n = 0;
@@ -479,11 +491,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++n) {
       const int h = (int)(it % MH);
       const int64_t t = it / MH;
-      const int j = (int)(t % N), tile = (int)(t / N);
+      const int tile = (int)(t % tiles), j = (int)(t / tiles);
       const int64_t col = (int64_t)tile * 128 + 32 * qd + lane;
-      const int m0 = h * 64 + g * 32;
+      const int m0 = h * 64 + g * RPT;
       const bool colok = col < K;
-      const double* Fc = F + ((size_t)j * M + m0) * K + col;  // this thread's 32 rows, stride K
+      const double* Fc = F + ((size_t)j * M + m0) * K + col;  // this thread's RPT rows, stride K
       // the first chunk of F, fetched before the wait so its latency overlaps the MMAs
       double Fn[8];
 #pragma unroll
@@ -492,13 +504,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
       if (!ok) break;
       tc_fence_after();
-      // phase 1: drain the 7 accumulators of this thread's 32 rows into T (int64,
+      // phase 1: drain the 7 accumulators of this thread's RPT rows into T (int64,
       // modulo 2^64) and Th ~ T / 2^35 (FP32, from the two leading sums)
-      uint64_t T[32];
-      float Th[32];
+      uint64_t T[RPT];
+      float Th[RPT];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t a = tmem + lane_base + g * 32 + c * 8;
+      for (int c = 0; c < RPT / 8; ++c) {
+        const uint32_t a = tmem + lane_base + g * RPT + c * 8;
         uint32_t r0[32], r1[24];
         tmem_ld8x4(a, a + ACC, a + 2 * ACC, a + 3 * ACC, r0);
         tmem_ld8x3(a + 4 * ACC, a + 5 * ACC, a + 6 * ACC, r1);
@@ -525,11 +537,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int* ear = ea + (size_t)j * M + m0;
       int eam = -100000;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) eam = max(eam, __ldg(ear + i));
+      for (int i = 0; i < RPT; ++i) eam = max(eam, __ldg(ear + i));
       float nf = 0.f;
       double nbig = 0.0;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < RPT / 8; ++c) {
         double Fv[8];
         int eav[8];
 #pragma unroll
@@ -537,7 +549,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           Fv[i] = Fn[i];
           eav[i] = __ldg(ear + 8 * c + i);
         }
-        if (c < 3) {
+        if (c + 1 < RPT / 8) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) Fn[i] = colok ? __ldg(Fc + (size_t)(8 * (c + 1) + i) * K) : 0.0;
         }
@@ -710,7 +722,7 @@ bt_status resid_digits_prepare(bt_handle_s* h, int64_t K, cudaStream_t s) {
     h->dg_ea = reinterpret_cast<int*>(e);
   }
   BT_TRY(grow_buf(h, &h->dg_x, &h->dg_x_bytes, (size_t)ND * N * Kp * M * sizeof(__nv_bfloat16), s));
-  BT_TRY(grow_buf(h, &h->dg_col, &h->dg_col_bytes, (size_t)Kp * (sizeof(unsigned long long) + sizeof(int)), s));
+  BT_TRY(grow_buf(h, &h->dg_col, &h->dg_col_bytes, (size_t)Kp * (sizeof(unsigned) + sizeof(int)), s));
   return BT_OK;
 }
 
@@ -722,12 +734,12 @@ bt_status launch_resid_digits(bt_handle_s* h, const double* F, const double* X, 
                               bool tr_float, void* out, int sp, const int* done, double* rn2, const int* cur,
                               int* status, cudaStream_t s) {
   const int64_t N = h->N, M = h->M, Kp = (K + 127) / 128 * 128;
-  unsigned long long* cm = reinterpret_cast<unsigned long long*>(h->dg_col);
+  unsigned* cm = reinterpret_cast<unsigned*>(h->dg_col);
   int* ex = reinterpret_cast<int*>(cm + Kp);
   __nv_bfloat16* xd = reinterpret_cast<__nv_bfloat16*>(h->dg_x);
   {
     ProfScope ps(h, s, "resid_prep");
-    k_zero_u64<<<(unsigned)std::min<int64_t>((Kp + 255) / 256, 1024), 256, 0, s>>>(cm, Kp, done);
+    k_zero_u32<<<(unsigned)std::min<int64_t>((Kp + 255) / 256, 1024), 256, 0, s>>>(cm, Kp, done);
     const int64_t rows = N * M;
     const unsigned gx = (unsigned)((K + 31) / 32);
     const unsigned gy =
