@@ -544,6 +544,140 @@ def run_batched(args):
     return 0
 
 
+# Tables 1-2 of the paper: (Pre s, Exe s per right-hand side) by processor count NP, for each
+# (block rows N, block size M); shapes and counts the paper could not run are absent.  The
+# entry 2^12 x 150 at NP = 256 (Exe 2.6e-3) breaks the table's monotonicity (likely 2.6e-2):
+# quoted as printed, left out of the "best" comparison.
+PAPER_TABLES = {
+    (2 ** 11, 60): {16: (1.8, 3e-2), 32: (1, 1.5e-2), 64: (1.32, 2.7e-3), 128: (2, 8.7e-4), 256: (3.2, 4.7e-4),
+                    512: (5.6, 4.9e-4), 1024: (10, 4.6e-4), 2048: (48.8, 1.1e-3)},
+    (2 ** 11, 150): {16: (30, 0.18), 32: (17, 9.4e-2), 64: (15, 4.8e-2), 128: (19, 2.6e-2), 256: (32, 1.2e-2),
+                     512: (62, 6.7e-3), 1024: (124, 4e-3)},
+    (2 ** 12, 60): {16: (3.5, 5.6e-2), 32: (1.9, 2.9e-2), 64: (2.7, 1.4e-2), 128: (2.1, 5.5e-3), 256: (3.2, 1e-3),
+                    512: (5.7, 6.3e-4), 1024: (9.9, 6.7e-4), 2048: (19.44, 1.3e-4)},
+    (2 ** 12, 150): {16: (56, 0.35), 32: (32, 0.18), 64: (22, 9.4e-2), 128: (22, 4.8e-2), 256: (34.7, 2.6e-3),
+                     512: (61, 1.3e-2), 1024: (126, 7.6e-3)},
+    (2 ** 13, 60): {16: (7, 0.12), 32: (3.8, 6e-2), 64: (3, 3e-2), 128: (3, 1.6e-2), 256: (3.36, 4e-3),
+                    512: (5.6, 1e-3), 1024: (9.9, 1.1e-3), 2048: (47, 1e-3)},
+    (2 ** 13, 150): {16: (115, 0.74), 32: (60, 0.37), 64: (36, 0.19), 128: (30, 9.5e-2), 256: (38, 5e-2),
+                     512: (65, 2.7e-2), 1024: (123, 1.4e-2)},
+    (2 ** 14, 60): {16: (15, 0.23), 32: (7.5, 0.12), 64: (4.3, 6e-2), 128: (4.2, 3.2e-2), 256: (4.1, 1.7e-2),
+                    512: (5.6, 5.5e-3), 1024: (14.4, 8.8e-4), 2048: (47, 1e-3)},
+    (2 ** 14, 150): {16: (220, 1.4), 32: (117, 0.73), 64: (64, 0.37), 128: (44, 0.18), 256: (45, 9.5e-2),
+                     512: (68, 5.1e-2), 1024: (126, 2.7e-2)},
+    (2 ** 15, 60): {16: (28, 0.45), 32: (15, 0.24), 64: (8.75, 0.12), 128: (5.15, 6e-2), 256: (5, 3.2e-2),
+                    512: (14.6, 3.6e-2), 1024: (25, 5.4e-2), 2048: (48, 2e-3)},
+    (2 ** 15, 150): {32: (231, 1.5), 64: (121, 0.74), 128: (72, 0.38), 256: (60, 0.19), 512: (75, 0.1),
+                     1024: (130, 5.5e-2)},
+    (2 ** 16, 60): {16: (60, 0.95), 32: (29, 0.47), 64: (15, 0.22), 128: (8.5, 0.11), 256: (6.9, 6e-2),
+                    512: (7.0, 3e-2), 1024: (10.3, 1.8e-2), 2048: (48, 6.6e-3)},
+    (2 ** 16, 150): {64: (235, 1.48), 128: (129, 0.75), 256: (89, 0.4), 512: (89, 0.2), 1024: (136, 0.1)},
+}
+PAPER_SUSPECT = {((2 ** 12, 150), 256)}
+
+
+def run_paper(args):
+    """The shapes of the paper's Tables 1-2 on one GPU (FP64 path, diagonally dominant dense
+    blocks drawn on the device): Pre = bt_factor wall time (allocation and one synchronisation
+    included), Exe = bt_solve time for one right-hand side (CUDA events, median of repeats) and
+    per right-hand side in a 256-column panel, for several segment counts S; beside them the
+    paper's best Pre and best Exe over its processor counts."""
+    import statistics
+
+    import torch
+
+    import oracle
+    import paper_1108_4181_gb300 as bt
+    from workloads import gen
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    # a small factorisation first, so that context and library set-up are not in any Pre
+    with bt.factor(*(t.contiguous() for t in gen.dominant_blocks_device(64, 8, 0, dev)), 4) as f0:
+        f0.solve(torch.ones((64, 8, 1), dtype=torch.float64, device=dev))
+    torch.cuda.synchronize(dev)
+    reps = max(5, args.steps)
+    shapes = []
+    only = [tuple(int(v) for v in x.split("x")) for x in args.paper_shapes.split(",")] if args.paper_shapes else None
+    for (Nn, Mm), table in PAPER_TABLES.items():
+        if only is not None and (Nn, Mm) not in only:
+            continue
+        A, B, C = gen.dominant_blocks_device(Nn, Mm, 1000 + Nn + Mm, dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        F1 = torch.rand((Nn, Mm, 1), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        F256 = torch.rand((Nn, Mm, 256), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+        runs = []
+        for Sv in (64, 256, 1024):
+            if Sv > Nn // 2:
+                continue
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            fac = bt.factor(A, B, C, Sv)
+            torch.cuda.synchronize(dev)
+            pre = time.perf_counter() - t0
+            X1 = torch.empty_like(F1)
+            X256 = torch.empty_like(F256)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            t1 = []
+            for r in range(reps + 3):
+                ev[0].record()
+                fac.solve(F1, out=X1)
+                ev[1].record()
+                torch.cuda.synchronize(dev)
+                if r >= 3:
+                    t1.append(ev[0].elapsed_time(ev[1]) * 1e-3)
+            tk = []
+            for r in range(5):
+                ev[0].record()
+                fac.solve(F256, out=X256)
+                ev[1].record()
+                torch.cuda.synchronize(dev)
+                if r >= 2:
+                    tk.append(ev[0].elapsed_time(ev[1]) * 1e-3)
+            R, n2 = fac.residual(F256, X256, method="fp64")
+            rel_res = float((n2 / float((F256 ** 2).sum())) ** 0.5)
+            del R
+            runs.append({"S": Sv, "pre_s": pre, "exe_s": statistics.median(t1),
+                         "exe_s_per_rhs_k256": statistics.median(tk) / 256, "rel_res_k256": rel_res})
+            fac.close()
+        check = None
+        if Nn * Mm * Mm <= 2 ** 11 * 150 * 150:  # the CPU oracle on the smallest shapes
+            An, Bn, Cn = (t.cpu().numpy() for t in (A, B, C))
+            fac = bt.factor(A, B, C, 64)
+            Xc = fac.solve(F1).cpu().numpy()
+            fac.close()
+            Xr = oracle.solve_block_thomas(An, Bn, Cn, F1.cpu().numpy())
+            check = {"rel_err_vs_oracle": oracle.rel_err(Xc, Xr),
+                     "rel_res_oracle": oracle.rel_res(An, Bn, Cn, Xc, F1.cpu().numpy())}
+        best = min(runs, key=lambda r: r["exe_s"])
+        pp = [(npv, pe) for npv, pe in table.items() if ((Nn, Mm), npv) not in PAPER_SUSPECT]
+        np_pre, (ppre, _) = min(pp, key=lambda t: t[1][0])
+        np_exe, (_, pexe) = min(pp, key=lambda t: t[1][1])
+        shapes.append({"N": Nn, "M": Mm, "runs": runs, "best_S": best["S"], "exe_s": best["exe_s"],
+                       "pre_s": min(r["pre_s"] for r in runs),
+                       "paper_best_pre_s": ppre, "paper_best_pre_NP": np_pre,
+                       "paper_best_exe_s": pexe, "paper_best_exe_NP": np_exe,
+                       "exe_speedup_vs_paper_best": pexe / best["exe_s"],
+                       "pre_speedup_vs_paper_best": ppre / min(r["pre_s"] for r in runs),
+                       "oracle_check": check})
+        print(f"paper shape {Nn}x{Mm}: {json.dumps(shapes[-1])}", file=sys.stderr, flush=True)
+        del A, B, C, F1, F256, X1, X256
+        torch.cuda.empty_cache()
+    sp = [s_["exe_speedup_vs_paper_best"] for s_ in shapes]
+    line = {
+        "metric": "Exe per right-hand side on the paper's Table 1-2 shapes: paper's best cluster time / ours (median)",
+        "value": statistics.median(sp) if sp else None, "unit": "x", "higher_is_better": True, "n_gpus": 1,
+        "steps": reps, "warmup": 3, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (diagonally dominant dense blocks drawn on the device; F ~ U[-1,1])",
+        "config": {"workload": "paper Tables 1-2 shapes: N = 2^11..2^16 block rows, M = 60 and 150, K = 1 "
+                               "(and 256 per right-hand side), S in {64, 256, 1024}"},
+        "shapes": shapes,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,12 +691,14 @@ def main():
                     help="refinement target ||F - P X|| / ||F|| (default 1e-10)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path beside")
-    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson"], default="acoustic",
+    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson", "paper"], default="acoustic",
                     help="acoustic (the headline), the batched uneven-set workload, or the Poisson workload "
                          "(N=1024, M=256, K=64, S=64)")
     ap.add_argument("--rows", type=int, default=N,
                     help="block rows N (smaller values only for profiler captures; the bench workload is 4096)")
     ap.add_argument("--segments", type=int, default=S, help="segments S (default 64)")
+    ap.add_argument("--paper-shapes", default="",
+                    help="with --workload paper: a comma list of NxM shapes to run (default: every shape)")
     args = ap.parse_args()
     global WORKLOAD, KIND
     KIND = args.workload
@@ -583,6 +719,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_ours(args)
 
 

@@ -69,6 +69,23 @@ def test_random_shapes(bt, N, M, K, S):
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
 
 
+@pytest.mark.parametrize("N,M,S", [(256, 60, 64), (128, 150, 32), (2048, 60, 256)])
+def test_paper_block_sizes(bt, N, M, S):
+    # the block sizes of the paper's Tables 1-2 (M = 60, 150; not multiples of
+    # the tensor-core tile), one right-hand side as there and a 256-column panel;
+    # the last case at the tables' smallest N = 2^11, matrices drawn on the device
+    # as the paper-shape bench draws them
+    if N <= 256:
+        A, B, C = gen.dominant_blocks(N, M, seed=N + M)
+    else:
+        A, B, C = (t.cpu().numpy() for t in gen.dominant_blocks_device(N, M, 1000 + N + M, DEV))
+    for K in (1, 256):
+        F = gen.uniform_rhs(N, M, K, seed=K)
+        X = _solve(bt, A, B, C, F, S)
+        assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
+        assert oracle.rel_res(A, B, C, X, F) <= TOL
+
+
 def test_unused_corner_blocks_are_ignored(bt):
     N, M, K, S = 32, 4, 2, 4
     A, B, C = gen.dominant_blocks(N, M, seed=3)

@@ -72,6 +72,29 @@ def dominant_blocks(N: int, M: int, seed: int):
     return A, B, C
 
 
+def dominant_blocks_device(N: int, M: int, seed: int, device):
+    """The distribution of `dominant_blocks`, drawn on a torch device (for the
+    paper-sized shapes, whose blocks reach tens of GB): A_j, B_j ~ U[0,1),
+    C_j off-diagonal ~ U[-0.5,0.5), diag(C_j) = row sums of |A_j|, |B_j| and
+    |offdiag C_j| + 1 + U[0,1); A_1 and B_N zeroed.  Draw order as there, from
+    one torch generator seeded with `seed` (values differ from the numpy draw)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    kw = dict(dtype=torch.float64, device=device, generator=g)
+    A = torch.rand((N, M, M), **kw)
+    B = torch.rand((N, M, M), **kw)
+    C = torch.rand((N, M, M), **kw) - 0.5
+    noise = torch.rand((N, M), **kw)
+    A[0] = 0.0
+    B[N - 1] = 0.0
+    idx = torch.arange(M, device=device)
+    C[:, idx, idx] = 0.0
+    C[:, idx, idx] = A.abs().sum(dim=2) + B.abs().sum(dim=2) + C.abs().sum(dim=2) + 1.0 + noise
+    return A, B, C
+
+
 def uniform_rhs(N: int, M: int, K: int, seed: int,
                 columns: Optional[Sequence[int]] = None, lo=-1.0, hi=1.0) -> np.ndarray:
     cols = range(K) if columns is None else columns
