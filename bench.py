@@ -494,12 +494,15 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
     plan.status()
     ms64 = e0.elapsed_time(e1) / args.steps
-    # refined split-BF16 solves of the same sets (one bt_solve_ex per set)
+    # refined split-BF16 solves of the same sets (one bt_solve_ex per set), with the
+    # segment count chosen for this path by its own tuner
+    tuned_mx = tune.tune_batched_refined(mats, sets, precision="bf16x3", tol=1e-10)
+    facs_mx = tuned_mx.factors
     Xm = [torch.empty_like(F) for F in Fs]
 
     def mixed_step():
         for (i, F), X in zip(sets, Xm):
-            facs[i].solve(F, precision="bf16x3", tol=1e-10, out=X)
+            facs_mx[i].solve(F, precision="bf16x3", tol=1e-10, out=X)
 
     for _ in range(2):
         mixed_step()
@@ -531,6 +534,7 @@ def run_batched(args):
                    "launch": f"one persistent cooperative launch per step ({plan.ctas} CTAs, {plan.items} items, "
                              f"{plan.stages} stages), CUDA graph replay: {bool(plan.graph)}"},
         "mixed_bf16x3": {"value": unknowns / (msmx * 1e-3), "ms_per_step": msmx, "steps": k_mixed,
+                         "S": tuned_mx.S, "tuned_ms": {f"S={a}": v for (a, _), v in tuned_mx.table.items()},
                          "path": "bt_solve_ex per set (split-BF16 tensor cores; residual exact on the tensor "
                                  "cores from BF16 digit slices; tol 1e-10)"},
         "speedup_mixed_vs_fp64": ms64 / msmx,
@@ -539,7 +543,7 @@ def run_batched(args):
     }
     print(json.dumps(line), flush=True)
     plan.close()
-    for f in facs:
+    for f in list(facs) + list(facs_mx):
         f.close()
     return 0
 

@@ -65,3 +65,22 @@ def test_tune_solve_mixed(bt):
     assert info["converged"]
     assert oracle.rel_res(A, B, C, X.cpu().numpy(), F) <= 1e-10
     res.factors[0].close()
+
+
+def test_tune_batched_refined_picks_a_timed_candidate(bt):
+    from paper_1108_4181_gb300 import tune
+
+    N, M = 128, 64
+    mats_np = [gen.dominant_blocks(N, M, s) for s in (3, 4)]
+    mats = [tuple(_t(a) for a in m) for m in mats_np]
+    sets_np = [gen.RhsSet(matrix=i % 2, K=k, F=gen.uniform_rhs(N, M, k, seed=20 + i)) for i, k in enumerate((5, 130))]
+    sets = [(s.matrix, _t(s.F)) for s in sets_np]
+    res = tune.tune_batched_refined(mats, sets, tol=1e-11, S_candidates=(8, 16, 3), reps=1)
+    assert res.S in (8, 16) and res.ms == min(res.table.values())
+    assert {S for S, _ in res.table} == {8, 16}
+    for st in sets_np:
+        A, B, C = mats_np[st.matrix]
+        X = res.factors[st.matrix].solve(_t(st.F), precision="bf16x3", tol=1e-11).cpu().numpy()
+        assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, st.F)) <= 1e-10
+    for f in res.factors:
+        f.close()
