@@ -39,7 +39,7 @@
 //   k_fac_digits    factor digits [3N][7][M][M] and e_A (once per handle)
 //   k_colmax        largest |X| of every column (its exponent)
 //   k_x_digits      X digits, block-transposed [7][N][Kp][M], and e_X
-//   k_resid_digits  persistent: TMA warp, MMA warp, 16 epilogue warps
+//   k_resid_digits  persistent: TMA warp, MMA warp, 8 epilogue warps
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -63,7 +63,7 @@ constexpr int NX = 4;           // X-digit tile ring slots
 constexpr int XT = 128 * 128;   // one X-digit tile: 128 columns x 64 contraction values (BF16)
 constexpr int FSL = 64 * 128;   // one factor digit slice: 64 rows x 64 contraction values
 constexpr int FST = ND * FSL;   // the 7 slices of one factor block and contraction chunk
-constexpr int EGW = 4;          // epilogue warps per TMEM lane quarter (rows of an output half split EGW ways)
+constexpr int EGW = 2;          // epilogue warps per TMEM lane quarter (rows of an output half split EGW ways)
 constexpr int RPT = 64 / EGW;   // output rows per epilogue thread
 constexpr int THREADS = 64 + 128 * EGW;  // TMA warp, MMA warp, 4 EGW epilogue warps
 constexpr int ACC = 64;         // TMEM columns of one accumulator
@@ -431,6 +431,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       uint32_t fi = 0, xi = 0, n = 0;
       bool ok = true;
+      // descriptors of the ring bases; a tile or slice at byte offset o is base + o / 16
+      const uint64_t xdesc0 = smem_desc(smem_u32(sX), 16, 1024);
+      const uint64_t fdesc0 = smem_desc(smem_u32(sF), 16, 1024);
       for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++n) {
         const int j = (int)(it / MH / tiles);
         if (n > 0 && !mbar_wait(accEmpty, (n - 1) & 1)) {
@@ -448,24 +451,26 @@ __global__ void __launch_bounds__(THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t fb = smem_u32(sF + fs * FST);
-            for (int q = 0; q < ND && ok; ++q) {
+            const uint64_t fd = fdesc0 + (uint64_t)((fs * FST) >> 4);
+            // fully unrolled: every instruction's shape (N = 64 np) is a constant
+#pragma unroll
+            for (int q = 0; q < ND; ++q) {
+              if (!ok) break;
               const uint32_t xs = xi % NX;
               if (!mbar_wait(&fullX[xs], (xi / NX) & 1)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t xb = smem_u32(sX + xs * XT);
+              const uint64_t xd = xdesc0 + (uint64_t)((xs * XT) >> 4);
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks) {
-                const uint64_t ad = smem_desc(xb + ks * 32, 16, 1024);
-                // slices p = 0 .. 6 - q, at most four per instruction
+                // slices p = 0 .. 6 - q, at most four per instruction (16-element K steps: 32 bytes)
+#pragma unroll
                 for (int p0 = 0; p0 < ND - q; p0 += 4) {
                   const int np = min(4, ND - q - p0);
-                  const uint64_t bd = smem_desc(fb + p0 * FSL + ks * 32, 16, 1024);
-                  mma_f16(tmem + ACC * (q + p0), ad, bd, instr_desc(1, 0, 128, 64 * np),
-                          (first && q == 0 && ks == 0) ? 0u : 1u);
+                  mma_f16(tmem + ACC * (q + p0), xd + 2 * ks, fd + (uint64_t)((p0 * FSL) >> 4) + 2 * ks,
+                          instr_desc(1, 0, 128, 64 * np), (first && q == 0 && ks == 0) ? 0u : 1u);
                 }
               }
               mma_commit(&emptyX[xs]);
@@ -496,10 +501,6 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int m0 = h * 64 + g * RPT;
       const bool colok = col < K;
       const double* Fc = F + ((size_t)j * M + m0) * K + col;  // this thread's RPT rows, stride K
-      // the first chunk of F, fetched before the wait so its latency overlaps the MMAs
-      double Fn[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) Fn[i] = colok ? __ldg(Fc + (size_t)i * K) : 0.0;
       if (ok) ok = mbar_wait(accFull, n & 1);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
       if (!ok) break;
@@ -546,12 +547,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         int eav[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          Fv[i] = Fn[i];
+          Fv[i] = colok ? __ldg(Fc + (size_t)(8 * c + i) * K) : 0.0;
           eav[i] = __ldg(ear + 8 * c + i);
-        }
-        if (c + 1 < RPT / 8) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) Fn[i] = colok ? __ldg(Fc + (size_t)(8 * (c + 1) + i) * K) : 0.0;
         }
         float rs[8];
 #pragma unroll
