@@ -96,15 +96,6 @@ __device__ __forceinline__ Dec decode(double v) {
   return d;
 }
 
-// mant * 2^sh modulo 2^64, rounded to nearest when sh < 0 (mant < 2^53).
-__device__ __forceinline__ uint64_t scale_mant(uint64_t mant, int sh) {
-  if (sh >= 64) return 0ull;
-  if (sh >= 0) return mant << sh;
-  if (sh < -54) return 0ull;
-  const int r = -sh;
-  return (mant + (1ull << (r - 1))) >> r;
-}
-
 // 64-bit shifts whose amounts saturate at 64 (result 0), as PTX defines them.
 __device__ __forceinline__ uint64_t shl64(uint64_t v, uint32_t n) {
   uint64_t r;
@@ -127,23 +118,41 @@ __device__ __forceinline__ int scale_of(uint64_t mx) {
 }
 
 // Balanced base-128 digits of round(v 2^(49-e)), |v| < 2^e; d[0] the most
-// significant (|d[0]| <= 128, |d[p]| <= 64 otherwise).
+// significant (|d[0]| <= 128, |d[p]| <= 64 otherwise).  The fixed-point value
+// f is split once into f = hi 2^21 + lo (0 <= lo < 2^21); the three low digits
+// come from lo, the borrow or carry they leave (0 or 1) moves into hi, and the
+// four high digits come from hi -- 32-bit arithmetic throughout.
 __device__ __forceinline__ void digits(double v, int e, int (&d)[ND]) {
-  const Dec x = decode(v);
-  int64_t f = (int64_t)scale_mant(x.mant, x.ex + FB - e);
-  if (x.neg) f = -f;
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7FF);
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (be ? (1ull << 52) : 0ull);
+  const int r = e - (max(be, 1) - 1075) - FB;  // right shift that makes f (>= 4 for normal v)
+  const uint64_t f = r <= 0 ? shl64(mant, (uint32_t)(-r))
+                            : shr64(mant + shl64(1ull, (uint32_t)(r - 1)), (uint32_t)r);  // rounded
+  const int64_t fs = (b >> 63) ? -(int64_t)f : (int64_t)f;
+  int lo = (int)((uint64_t)fs & 0x1FFFFFull);
+  int hi = (int)(fs >> 21);  // |f| <= 2^49
 #pragma unroll
-  for (int p = ND - 1; p > 0; --p) {
-    int t = (int)(f & 127);
-    t -= (t & 64) << 1;
+  for (int p = ND - 1; p > ND - 4; --p) {
+    const int t = ((lo + 64) & 127) - 64;
     d[p] = t;
-    f = (f - t) >> 7;
+    lo = (lo - t) >> 7;
   }
-  d[0] = (int)f;
+  hi += lo;
+#pragma unroll
+  for (int p = ND - 4; p > 0; --p) {
+    const int t = ((hi + 64) & 127) - 64;
+    d[p] = t;
+    hi = (hi - t) >> 7;
+  }
+  d[0] = hi;
 }
 
+// An integer |a| < 2^22 as FP32, exactly, without a conversion instruction.
+__device__ __forceinline__ float small_int_f32(int a) { return __int_as_float(0x4B400000 + a) - 12582912.f; }
+
 __device__ __forceinline__ uint32_t bf2(int a, int b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn((float)a, (float)b);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(small_int_f32(a), small_int_f32(b));
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
