@@ -101,10 +101,12 @@ static void destroy_handle(bt_handle_s* h) {
   for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam, h->dg_fac,
                   static_cast<void*>(h->dg_ea), h->dg_x, h->dg_col})
     if (q) cudaFree(q);
-  if (h->rgraph.exec) cudaGraphExecDestroy(h->rgraph.exec);
-  if (h->rgraph.graph) cudaGraphDestroy(h->rgraph.graph);
-  if (h->rgraph.cap) cudaStreamDestroy(h->rgraph.cap);
-  if (h->rgraph.cap2) cudaStreamDestroy(h->rgraph.cap2);
+  for (auto& g : h->rgraphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  if (h->rg_cap) cudaStreamDestroy(h->rg_cap);
+  if (h->rg_cap2) cudaStreamDestroy(h->rg_cap2);
   cudaSetDevice(prev);
   delete h;
 }

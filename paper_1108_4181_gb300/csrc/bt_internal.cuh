@@ -172,21 +172,27 @@ struct bt_handle_s {
   void* dg_col = nullptr;
   size_t dg_col_bytes = 0;
 
-  // The refined solve captured as a CUDA graph: replayed when a call repeats
-  // the previous call's arguments (and no buffer moved since the capture).
+  // The refined solve captured as CUDA graphs, one per argument key: a key's
+  // second call captures, later calls replay (other calls may come between;
+  // the calls on a handle run in order on one stream, so the graphs may share
+  // the handle's buffers).  Graphs of buffers that have moved since are
+  // dropped; at most kMaxRefineGraphs are kept, least recently used out.
   struct RefineGraph {
     const double* F = nullptr;
     double* X = nullptr;
     int64_t K = 0;
     int precision = -1, max_it = 0, gen = -1, resid = -1;
     double tol = 0.0;
-    bool seen = false;  // the previous call had this key (capture on the next)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;   // private capture streams (the graph, the loop body)
-    cudaStream_t cap2 = nullptr;
-    bool broken = false;         // capture failed once: enqueue directly from then on
-  } rgraph;
+    uint64_t used = 0;  // last use (handle-local clock)
+  };
+  static constexpr size_t kMaxRefineGraphs = 64;
+  std::vector<RefineGraph> rgraphs;
+  uint64_t rg_clock = 0;
+  cudaStream_t rg_cap = nullptr;  // private capture streams (the graph, the loop body)
+  cudaStream_t rg_cap2 = nullptr;
+  bool rg_broken = false;  // a capture failed once: enqueue directly from then on
 
   bt::Profiler prof;
 };

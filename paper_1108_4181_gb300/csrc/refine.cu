@@ -565,20 +565,21 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   };
   // Captures prologue + WHILE(body) into *out; false (and nothing captured) on failure.
   auto capture = [&](cudaGraph_t* out) -> bool {
-    bt_handle_s::RefineGraph& g = h->rgraph;
-    if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return false;
-    if (!g.cap2 && cudaStreamCreateWithFlags(&g.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
-    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    cudaStream_t& cap = h->rg_cap;
+    cudaStream_t& cap2 = h->rg_cap2;
+    if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!cap2 && cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
     bool ok = true;
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     cudaGraphConditionalHandle loop = 0;
-    ok = ok && cudaStreamGetCaptureInfo(g.cap, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
+    ok = ok && cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
     ok = ok && cudaGraphConditionalHandleCreate(&loop, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
-    ok = ok && prologue(g.cap, loop) == BT_OK;
+    ok = ok && prologue(cap, loop) == BT_OK;
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
-    ok = ok && cudaStreamGetCaptureInfo(g.cap, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
+    ok = ok && cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = loop;
@@ -586,20 +587,20 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     cp.conditional.size = 1;
     cudaGraphNode_t cn = nullptr;
     ok = ok && cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp) == cudaSuccess;
-    ok = ok && cudaStreamUpdateCaptureDependencies(g.cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+    ok = ok && cudaStreamUpdateCaptureDependencies(cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
                    cudaSuccess;
     if (ok) {
       cudaGraph_t bg = cp.conditional.phGraph_out[0];
-      ok = cudaStreamBeginCaptureToGraph(g.cap2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+      ok = cudaStreamBeginCaptureToGraph(cap2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
            cudaSuccess;
       if (ok) {
-        const bt_status bs = body(g.cap2, loop);
+        const bt_status bs = body(cap2, loop);
         cudaGraph_t bg_out = nullptr;
-        ok = cudaStreamEndCapture(g.cap2, &bg_out) == cudaSuccess && bs == BT_OK;
+        ok = cudaStreamEndCapture(cap2, &bg_out) == cudaSuccess && bs == BT_OK;
       }
     }
     cudaGraph_t graph = nullptr;
-    const bool ended = cudaStreamEndCapture(g.cap, &graph) == cudaSuccess;
+    const bool ended = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
     if (!(ok && ended && graph)) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
@@ -609,40 +610,63 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     return true;
   };
 
-  // CUDA graph: captured on the second consecutive call with the same
-  // arguments (the first has grown every buffer and built every factor copy),
-  // replayed from then on.  Profiling records events per launch, so it runs
-  // the launches directly.
-  bt_handle_s::RefineGraph& g = h->rgraph;
-  const bool same = g.F == F && g.X == X && g.K == K && g.precision == prec && g.tol == tol && g.max_it == max_it &&
-                    g.gen == h->lp_gen && g.resid == (digits ? 1 : 0);
+  // CUDA graphs: a key's second call captures (the first has grown every
+  // buffer and built every factor copy), later calls replay.  Profiling
+  // records events per launch, so it runs the launches directly.
+  auto& cache = h->rgraphs;
+  auto drop = [](bt_handle_s::RefineGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+  };
+  for (size_t i = 0; i < cache.size();) {  // graphs of buffers that have moved
+    if (cache[i].gen != h->lp_gen) {
+      drop(cache[i]);
+      cache.erase(cache.begin() + (std::ptrdiff_t)i);
+    } else {
+      ++i;
+    }
+  }
+  const int rkey = digits ? 1 : 0;
+  bt_handle_s::RefineGraph* e = nullptr;
+  for (auto& g : cache)
+    if (g.F == F && g.X == X && g.K == K && g.precision == prec && g.tol == tol && g.max_it == max_it &&
+        g.resid == rkey) {
+      e = &g;
+      break;
+    }
   bool launched = false;
-  if (!h->prof.on && !g.broken) {
-    if (same && g.exec) {
-      BT_CUDA(cudaGraphLaunch(g.exec, s));
-      launched = true;
-    } else if (same && g.seen) {
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-      if (g.graph) cudaGraphDestroy(g.graph);
-      g.exec = nullptr;
-      g.graph = nullptr;
+  if (e != nullptr && !h->prof.on && !h->rg_broken) {
+    if (!e->exec) {
       cudaGraph_t graph = nullptr;
       bool ok = capture(&graph);
-      ok = ok && cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+      ok = ok && cudaGraphInstantiate(&e->exec, graph, 0) == cudaSuccess;
       if (ok) {
-        g.graph = graph;
-        BT_CUDA(cudaGraphLaunch(g.exec, s));
-        launched = true;
+        e->graph = graph;
       } else {
         if (graph) cudaGraphDestroy(graph);
-        g.exec = nullptr;
-        g.broken = true;
+        e->exec = nullptr;
+        h->rg_broken = true;
         cudaGetLastError();
       }
     }
+    if (e->exec) {
+      BT_CUDA(cudaGraphLaunch(e->exec, s));
+      launched = true;
+    }
   }
   if (!launched) BT_TRY(enqueue(s));
-  if (!same) {
+  if (e == nullptr) {
+    if (cache.size() >= bt_handle_s::kMaxRefineGraphs) {
+      auto lru = std::min_element(cache.begin(), cache.end(),
+                                  [](const bt_handle_s::RefineGraph& a, const bt_handle_s::RefineGraph& b) {
+                                    return a.used < b.used;
+                                  });
+      drop(*lru);
+      cache.erase(lru);
+    }
+    bt_handle_s::RefineGraph g;
     g.F = F;
     g.X = X;
     g.K = K;
@@ -650,13 +674,11 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     g.tol = tol;
     g.max_it = max_it;
     g.gen = h->lp_gen;
-    g.resid = digits ? 1 : 0;
-    g.seen = true;
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (g.graph) cudaGraphDestroy(g.graph);
-    g.exec = nullptr;
-    g.graph = nullptr;
+    g.resid = rkey;
+    cache.push_back(g);
+    e = &cache.back();
   }
+  e->used = ++h->rg_clock;
   BT_CUDA(cudaGetLastError());
   if (info) {
     IrState hs;
