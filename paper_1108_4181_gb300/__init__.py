@@ -8,6 +8,6 @@ marshals arguments to it.
 """
 
 from ._lib import BtError, load  # noqa: F401
-from .solver import BatchPlan, Factorization, factor, solve_batched  # noqa: F401
+from .solver import BatchPlan, Factorization, factor, solve_batched, solve_refined_sets  # noqa: F401
 from .autograd import BTSolve, bt_solve  # noqa: F401,E402
 from . import tune  # noqa: F401,E402

@@ -256,3 +256,36 @@ def solve_batched(facs, Fs, Xs=None, k_tile: int = 0, stream: Optional[torch.cud
     with torch.cuda.device(dev):
         _lib.check(_lib.load().bt_solve_batched(len(facs), H, Fp, K, Xp, ctypes.byref(opts)), "bt_solve_batched")
     return Xs
+
+
+def solve_refined_sets(facs, Fs, Xs=None, precision: str = "bf16x3", tol: float = 0.0, max_it: int = 0,
+                       residual: str = "auto"):
+    """Refined solves of many right-hand-side sets, X_b = P_{facs[b]}^{-1} F_b.
+
+    The sets of one factorization run in order on one stream (calls on a handle
+    must), different factorizations concurrently, each on a stream of its own;
+    every solve is one ``solve`` call (replayed from its CUDA graph when the
+    handle has seen its arguments before).  Returns the outputs; the work is
+    ordered before later work on the current stream."""
+    if Xs is None:
+        Xs = [torch.empty_like(F) for F in Fs]
+    if not (len(facs) == len(Fs) == len(Xs)):
+        raise ValueError("facs, Fs and Xs must have the same length")
+    if not facs:
+        return Xs
+    dev = Fs[0].device
+    cur = torch.cuda.current_stream(dev)
+    used = {}
+    for fac, F, X in zip(facs, Fs, Xs):
+        st = used.get(id(fac))
+        if st is None:
+            st = getattr(fac, "_side_stream", None)
+            if st is None:
+                st = torch.cuda.Stream(dev)
+                fac._side_stream = st
+            st.wait_stream(cur)  # the inputs are ready on the current stream
+            used[id(fac)] = st
+        fac.solve(F, precision=precision, tol=tol, max_it=max_it, out=X, stream=st, residual=residual)
+    for st in used.values():
+        cur.wait_stream(st)
+    return Xs

@@ -90,9 +90,9 @@ def tune_batched(mats, sets, S_candidates: Sequence[int] = S_CANDIDATES,
 
 def tune_batched_refined(mats, sets, precision: str = "bf16x3", tol: float = 0.0,
                          S_candidates: Sequence[int] = (32, 64, 128), reps: int = 2) -> TuneResult:
-    """Best S for the refined (mixed-precision) path over a batch of sets: one
-    ``solve`` per set, each replayed as its CUDA graph after the first two calls
-    (capture happens on a call that repeats the previous arguments).  Same
+    """Best S for the refined (mixed-precision) path over a batch of sets, run by
+    ``solver.solve_refined_sets`` (one ``solve`` per set, each replayed from its
+    CUDA graph after the first two calls; one stream per matrix).  Same
     arguments and result as ``tune_batched`` (k_tile 0: the tensor-core tile)."""
     N = mats[0][0].shape[0]
     device = mats[0][0].device
@@ -103,8 +103,8 @@ def tune_batched_refined(mats, sets, precision: str = "bf16x3", tol: float = 0.0
         facs = [solver.factor(A, B, C, S) for A, B, C in mats]
 
         def step():
-            for (i, F), X in zip(sets, Xs):
-                facs[i].solve(F, precision=precision, tol=tol, out=X)
+            solver.solve_refined_sets([facs[i] for i, _ in sets], [F for _, F in sets], Xs,
+                                      precision=precision, tol=tol)
 
         step()  # first call per set: buffers and factor copies; the timed warm-up captures the graphs
         ms = _time(step, reps, device)

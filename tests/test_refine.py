@@ -200,3 +200,27 @@ def test_graph_cache_follows_argument_changes(bt):
             _, info = fac.solve(Fd, precision="bf16x3", tol=tol, out=X, return_info=True)
             assert info["converged"] and info["rel_res"] <= tol
             assert oracle.rel_res(A, B, C, X.cpu().numpy(), F) <= 2 * tol
+
+
+def test_refined_sets_on_concurrent_streams(bt):
+    # sets of two factorizations: each factorization's sets in order on its own
+    # stream, the two concurrently; three rounds (direct, capture, replay) with
+    # new values in one set's F before the last round
+    N, M = 64, 64
+    mats = [gen.dominant_blocks(N, M, seed=s) for s in (41, 42)]
+    Ks = [3, 130, 17, 64, 1]
+    Fs_np = [gen.uniform_rhs(N, M, k, seed=60 + i) for i, k in enumerate(Ks)]
+    with bt.factor(*(_t(a) for a in mats[0]), 8) as f0, bt.factor(*(_t(a) for a in mats[1]), 16) as f1:
+        facs = [f0, f1, f0, f1, f0]
+        Fs = [_t(F) for F in Fs_np]
+        Xs = [torch.empty_like(F) for F in Fs]
+        for rnd in range(3):
+            if rnd == 2:
+                Fs_np[1] = gen.uniform_rhs(N, M, Ks[1], seed=99)
+                Fs[1].copy_(_t(Fs_np[1]))
+            bt.solve_refined_sets(facs, Fs, Xs, precision="bf16x3", tol=1e-11)
+            torch.cuda.synchronize()
+            for i, X in enumerate(Xs):
+                A, B, C = mats[i % 2]
+                Xr = oracle.solve_block_thomas(A, B, C, Fs_np[i])
+                assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10, (rnd, i)
