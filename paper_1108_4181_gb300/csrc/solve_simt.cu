@@ -55,7 +55,7 @@ template <typename T, int CW>
 __device__ __forceinline__ void acc_blk(T (&acc)[CW], const T* __restrict__ blk, int M, int m, const T* pan,
                                         int kt, int c0) {
   const T* row = blk + (size_t)m * M;
-#pragma unroll 4
+#pragma unroll 16
   for (int k = 0; k < M; ++k) {
     const T a = __ldg(row + k);
     const T* q = pan + k * kt + c0;
@@ -209,6 +209,7 @@ __device__ __forceinline__ void dichotomy_item(const SimtArgs<T>& p, int lev, in
   T acc[CW];
 #pragma unroll
   for (int c = 0; c < CW; ++c) acc[c] = T(0);
+#pragma unroll 8
   for (int j = l; j <= r; ++j) {
     const T* cj = p.c + ((size_t)lev * p.S + j) * MK + (size_t)m * p.K + col;
 #pragma unroll
