@@ -119,12 +119,18 @@ bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* str
  * bt_solve.  BT_PREC_TF32 / BT_PREC_BF16 run the panel products of steps
  * 2.1-2.3 on tcgen05 tensor cores with FP32 accumulation against rounded
  * copies of the factors (BT_PREC_F32: FP32 on the CUDA cores), and recover
- * FP64 accuracy by iterative refinement
- * against the FP64 residual F - P X (not in the paper): X_0 = S~ F,
+ * FP64 accuracy by iterative refinement against the residual F - P X formed
+ * to FP64 accuracy (not in the paper): X_0 = S~ F,
  * X_{k+1} = X_k + S~ (F - P X_k), until ||F - P X||_F <= tol ||F||_F or
  * max_it passes.  F, X, K as for bt_solve.  When `info` is non-NULL the call
  * synchronises the stream and fills it; with info == NULL it is asynchronous
- * and never returns BT_ERR_NOCONV.
+ * and never returns BT_ERR_NOCONV.  The residual is formed per opts->residual
+ * (see bt_opts; for dense blocks with M = 64 or 128 exactly on the tensor
+ * cores by default).  The handle keeps the refinement as CUDA graphs, one per
+ * argument key (F, X, K, precision, tol, max_it, residual method; at most 64,
+ * least recently used out, dropped when a refinement buffer is reallocated): a
+ * key's second call captures, later calls replay.  Calls on one handle must be
+ * ordered on one stream; different handles may run concurrently.
  */
 bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts,
                       bt_info* info);
