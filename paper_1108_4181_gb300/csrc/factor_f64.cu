@@ -36,16 +36,19 @@ namespace bt {
 namespace {
 
 // ---------------------------------------------------------------------------
-// Batched FP64 GEMM on square M x M blocks: 64 x 64 output tile per CTA,
-// 256 threads with a 4 x 4 register tile each, K staged through shared memory
-// 16 at a time.  Operands come from a device table of pointers, 4 per batch
-// entry: X, Y, Z (may be null when beta == 0), D (may alias Z).
+// Batched FP64 GEMM on square M x M blocks: GT x GT output tile per CTA (GT =
+// 64 or 32), 256 threads with a (GT/16) x (GT/16) register tile each, K staged
+// through shared memory 16 at a time.  The tile is chosen per M to limit the
+// padding (M = 150: 64-tiles compute 192 x 192, 32-tiles 160 x 160).
+// Operands come from a device table of pointers, 4 per batch entry: X, Y, Z
+// (may be null when beta == 0), D (may alias Z).
 // ---------------------------------------------------------------------------
-constexpr int GT = 64;
 constexpr int GK = 16;
 
+template <int GT>
 __global__ void __launch_bounds__(256) k_gemm_batched(const double* const* __restrict__ tab, int M,
                                                       double alpha, double beta) {
+  constexpr int R = GT / 16;  // register tile R x R
   const double* X = tab[4 * blockIdx.z + 0];
   const double* Y = tab[4 * blockIdx.z + 1];
   const double* Z = tab[4 * blockIdx.z + 2];
@@ -54,44 +57,44 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const double* const* __res
   __shared__ double ys[GK][GT];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
   for (int k0 = 0; k0 < M; k0 += GK) {
-    // X tile: rows row0..+64, cols k0..+16 (stored transposed); Y tile: rows k0..+16, cols col0..+64.
+    // X tile: rows row0..+GT, cols k0..+16 (stored transposed); Y tile: rows k0..+16, cols col0..+GT.
     for (int e = threadIdx.x; e < GT * GK; e += 256) {
-      int r = e / GK, c = e % GK;
-      int gr = row0 + r, gc = k0 + c;
+      const int r = e / GK, c = e % GK;
+      const int gr = row0 + r, gc = k0 + c;
       xs[c][r] = (gr < M && gc < M) ? X[(size_t)gr * M + gc] : 0.0;
-      int yr = k0 + e / GT, yc = col0 + e % GT;
+      const int yr = k0 + e / GT, yc = col0 + e % GT;
       ys[e / GT][e % GT] = (yr < M && yc < M) ? Y[(size_t)yr * M + yc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double xv[4], yv[4];
+      double xv[R], yv[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xv[i] = xs[kk][ty * 4 + i];
+      for (int i = 0; i < R; ++i) xv[i] = xs[kk][ty * R + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) yv[j] = ys[kk][tx * 4 + j];
+      for (int j = 0; j < R; ++j) yv[j] = ys[kk][tx * R + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int gr = row0 + ty * 4 + i;
+  for (int i = 0; i < R; ++i) {
+    const int gr = row0 + ty * R + i;
     if (gr >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int gc = col0 + tx * 4 + j;
+    for (int j = 0; j < R; ++j) {
+      const int gc = col0 + tx * R + j;
       if (gc >= M) continue;
-      size_t o = (size_t)gr * M + gc;
+      const size_t o = (size_t)gr * M + gc;
       double v = alpha * acc[i][j];
       if (beta != 0.0) v = fma(beta, Z[o], v);
       D[o] = v;
@@ -123,6 +126,10 @@ __global__ void __launch_bounds__(1024) k_inverse_batched(const double* const* _
   __shared__ double s_pval;
   const int nt = blockDim.x;
   const int MM = M * M;
+  // elimination mapping: thread -> (row offset it0, column jt); rstep thread rows
+  const int rstep = max(1, nt / M);
+  const int jt = threadIdx.x < rstep * M ? threadIdx.x % M : M;
+  const int it0 = threadIdx.x / M;
   for (int e = threadIdx.x; e < MM; e += nt) a[e] = src[e];
   __syncthreads();
   for (int k = 0; k < M; ++k) {
@@ -173,12 +180,16 @@ __global__ void __launch_bounds__(1024) k_inverse_batched(const double* const* _
       a[(size_t)k * M + j] = v / pv;
     }
     __syncthreads();
-    // 4. eliminate column k from every other row.
-    for (int e = threadIdx.x; e < MM; e += nt) {
-      int i = e / M, j = e % M;
-      if (i == k) continue;
-      double base = (j == k) ? 0.0 : a[e];
-      a[e] = fma(-fcol[i], a[(size_t)k * M + j], base);
+    // 4. eliminate column k from every other row: thread -> column j (fixed),
+    //    rows strided by the number of thread rows (no per-element division).
+    if (jt < M) {
+      const double pk = a[(size_t)k * M + jt];
+      for (int i = it0; i < M; i += rstep) {
+        if (i == k) continue;
+        const size_t e = (size_t)i * M + jt;
+        const double base = (jt == k) ? 0.0 : a[e];
+        a[e] = fma(-fcol[i], pk, base);
+      }
     }
     __syncthreads();
   }
@@ -232,20 +243,26 @@ __global__ void k_set_identity(double* I, int M) {
     I[e] = (e / M == e % M) ? 1.0 : 0.0;
 }
 
-// Stencil detection: A_j = B_j = I (where used) and C_j tridiagonal.
+// Stencil detection: A_j = B_j = I (where used) and C_j tridiagonal.  A
+// thread stops at its first violation and leaves the scan once another has
+// reported one; each warp reports with one vote and one atomic (a dense
+// operator fails almost everywhere, and one atomic per element serialised).
 __global__ void k_detect_stencil(const double* A, const double* B, const double* C, int64_t N, int M,
                                  int* not_stencil) {
-  size_t n = (size_t)N * M * M;
+  const size_t n = (size_t)N * M * M;
+  bool bad = false;
+  int poll = 0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    int64_t j = e / ((size_t)M * M);
-    int r = (e / M) % M, c = e % M;
-    double id = (r == c) ? 1.0 : 0.0;
-    bool ok = true;
-    if (j > 0 && A[e] != id) ok = false;
-    if (j < N - 1 && B[e] != id) ok = false;
-    if ((c > r + 1 || r > c + 1) && C[e] != 0.0) ok = false;
-    if (!ok) atomicExch(not_stencil, 1);
+    const int64_t j = e / ((size_t)M * M);
+    const int r = (e / M) % M, c = e % M;
+    const double id = (r == c) ? 1.0 : 0.0;
+    if ((j > 0 && A[e] != id) || (j < N - 1 && B[e] != id) || ((c > r + 1 || r > c + 1) && C[e] != 0.0)) {
+      bad = true;
+      break;
+    }
+    if ((++poll & 15) == 0 && *(volatile const int*)not_stencil != 0) break;
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(not_stencil, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -521,6 +538,9 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
                                    : M * sizeof(double) + M * sizeof(int);
   BT_CUDA(cudaFuncSetAttribute(k_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
   const int inv_threads = (int)std::min<size_t>(1024, std::max<size_t>(32, ((MM + 31) / 32) * 32));
+  // GEMM tile: 32 when 64-tiles would pad the block by more than about 15 % in area
+  const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
+  const int GT = (double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64;
   const int tiles = (M + GT - 1) / GT;
   for (const Op& o : sc.ops) {
     // grid.z / grid.x limits: split very large batches
@@ -528,7 +548,10 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
       int nb = std::min(65535, o.batch - b0);
       if (o.kind == 0) {
         dim3 grid(tiles, tiles, nb);
-        k_gemm_batched<<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta);
+        if (GT == 32)
+          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta);
+        else
+          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta);
       } else {
         k_inverse_batched<<<nb, inv_threads, inv_smem, st>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
       }
