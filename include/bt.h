@@ -136,6 +136,18 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
                       bt_info* info);
 
 /*
+ * bt_solve_host -- bt_solve_ex for right-hand sides in host memory (not in the
+ * paper): F and X are HOST [N][M][K] FP64 arrays (page-locked for the copies
+ * to overlap; pageable memory works, synchronously).  The columns go through
+ * the device in chunks of 128 (at least about four chunks per call): the upload
+ * of a chunk, the solve of the previous one (on opts->stream) and the download
+ * of the one before run concurrently, in two device panel pairs owned by the
+ * handle (grown on demand; each pair keeps its own CUDA graph).  Synchronous:
+ * X is complete on return.  No bt_info (as bt_solve_ex with info == NULL).
+ */
+bt_status bt_solve_host(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts);
+
+/*
  * bt_solve_adjoint -- gradients of a loss through X = P^{-1} F (not in the
  * paper).  With G = dL/dX, solves P^T lambda = G by the same stage-2 machinery
  * on the factors of P^T (built on first use and kept in the handle) and forms

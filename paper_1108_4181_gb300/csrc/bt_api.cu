@@ -105,6 +105,11 @@ static void destroy_handle(bt_handle_s* h) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
   }
+  if (h->hp_buf) cudaFree(h->hp_buf);
+  if (h->hp_h2d) cudaStreamDestroy(h->hp_h2d);
+  if (h->hp_d2h) cudaStreamDestroy(h->hp_d2h);
+  for (cudaEvent_t e : h->hp_ev)
+    if (e) cudaEventDestroy(e);
   if (h->rg_cap) cudaStreamDestroy(h->rg_cap);
   if (h->rg_cap2) cudaStreamDestroy(h->rg_cap2);
   cudaSetDevice(prev);
@@ -217,6 +222,65 @@ bt_status bt_solve_noalloc(bt_handle h, const double* F, int64_t K, double* X, v
     return BT_ERR_ARG;
   }
   return solve_f64_noalloc(h, F, K, X, (cudaStream_t)stream);
+}
+
+bt_status bt_solve_host(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts) {
+  if (!h || !F || !X || K < 1) {
+    set_error("bt_solve_host: need a handle, host F and X, K >= 1");
+    return BT_ERR_ARG;
+  }
+  bt_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  const cudaStream_t cs = (cudaStream_t)o.stream;
+  const int64_t NM = h->N * h->M;
+  // column chunks: the tensor-core tile (128), at least about four chunks per call
+  const int64_t KC = K <= 128 ? K : std::max<int64_t>(128, ((K + 3) / 4 + 127) / 128 * 128);
+  const size_t panel = (size_t)NM * KC * sizeof(double);
+  if (4 * panel > h->hp_bytes) {
+    BT_CUDA(cudaDeviceSynchronize());
+    if (h->hp_buf) BT_CUDA(cudaFree(h->hp_buf));
+    h->hp_buf = nullptr;
+    h->hp_bytes = 0;
+    const cudaError_t e = cudaMalloc((void**)&h->hp_buf, 4 * panel);
+    if (e != cudaSuccess) {
+      h->hp_buf = nullptr;
+      set_error(std::string("bt_solve_host: panel allocation failed: ") + cudaGetErrorString(e));
+      return BT_ERR_OOM;
+    }
+    h->hp_bytes = 4 * panel;
+  }
+  if (!h->hp_h2d) BT_CUDA(cudaStreamCreateWithFlags(&h->hp_h2d, cudaStreamNonBlocking));
+  if (!h->hp_d2h) BT_CUDA(cudaStreamCreateWithFlags(&h->hp_d2h, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : h->hp_ev)
+    if (!e) BT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* ev_in = h->hp_ev;       // chunk uploaded into pair b
+  cudaEvent_t* ev_sol = h->hp_ev + 2;  // chunk solved
+  cudaEvent_t* ev_out = h->hp_ev + 4;  // chunk downloaded: pair b free again
+  // the inputs may have been written on the compute stream
+  BT_CUDA(cudaEventRecord(ev_sol[0], cs));
+  BT_CUDA(cudaStreamWaitEvent(h->hp_h2d, ev_sol[0], 0));
+  const size_t pitch = (size_t)K * sizeof(double);
+  const int64_t nch = (K + KC - 1) / KC;
+  for (int64_t c = 0; c < nch; ++c) {
+    const int b = (int)(c & 1);
+    const int64_t c0 = c * KC, kc = std::min<int64_t>(KC, K - c0);
+    double* Fd = h->hp_buf + (size_t)(2 * b) * NM * KC;
+    double* Xd = h->hp_buf + (size_t)(2 * b + 1) * NM * KC;
+    const size_t w = (size_t)kc * sizeof(double);
+    if (c >= 2) BT_CUDA(cudaStreamWaitEvent(h->hp_h2d, ev_out[b], 0));
+    BT_CUDA(cudaMemcpy2DAsync(Fd, w, F + c0, pitch, w, (size_t)NM, cudaMemcpyHostToDevice, h->hp_h2d));
+    BT_CUDA(cudaEventRecord(ev_in[b], h->hp_h2d));
+    BT_CUDA(cudaStreamWaitEvent(cs, ev_in[b], 0));
+    BT_TRY(bt_solve_ex(h, Fd, kc, Xd, &o, nullptr));
+    BT_CUDA(cudaEventRecord(ev_sol[b], cs));
+    BT_CUDA(cudaStreamWaitEvent(h->hp_d2h, ev_sol[b], 0));
+    BT_CUDA(cudaMemcpy2DAsync(X + c0, pitch, Xd, w, w, (size_t)NM, cudaMemcpyDeviceToHost, h->hp_d2h));
+    BT_CUDA(cudaEventRecord(ev_out[b], h->hp_d2h));
+  }
+  BT_CUDA(cudaStreamSynchronize(h->hp_d2h));
+  BT_CUDA(cudaStreamSynchronize(cs));
+  return BT_OK;
 }
 
 bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* stream) {

@@ -172,6 +172,13 @@ struct bt_handle_s {
   void* dg_col = nullptr;
   size_t dg_col_bytes = 0;
 
+  // Host-buffer solves (bt_solve_host): two device panel pairs (F, X) of
+  // N*M*kc doubles each, their copy streams and events (grown on demand).
+  double* hp_buf = nullptr;
+  size_t hp_bytes = 0;
+  cudaStream_t hp_h2d = nullptr, hp_d2h = nullptr;
+  cudaEvent_t hp_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
   // The refined solve captured as CUDA graphs, one per argument key: a key's
   // second call captures, later calls replay (other calls may come between;
   // the calls on a handle run in order on one stream, so the graphs may share

@@ -77,10 +77,26 @@ class Factorization:
         or 128), "auto" the latter where it applies.
 
         A CUDA tensor is solved in place on the device.  A CPU tensor is the
-        end-to-end path: it is copied to the device (through pinned memory when
-        F is pinned), solved, and the result copied back to a CPU tensor."""
+        end-to-end path (bt_solve_host): its columns go through the device in
+        chunks whose uploads, solves and downloads overlap (page-locked F and
+        out for the overlap); with return_info the whole panel is copied,
+        solved and copied back instead."""
         F = self._panel(F, "F")
         host = F.device.type == "cpu"
+        if host and not return_info:
+            # columns through the device in overlapped chunks (bt_solve_host)
+            if F.dtype != torch.float64:
+                raise TypeError("F must be float64")
+            Fh = F.contiguous()
+            Xh = out if out is not None else torch.empty(F.shape, dtype=torch.float64, pin_memory=F.is_pinned())
+            if Xh.device.type != "cpu" or Xh.dtype != torch.float64 or not Xh.is_contiguous() or Xh.shape != F.shape:
+                raise ValueError("out must be a contiguous float64 CPU tensor of F's shape")
+            opts = _lib.BtOpts(precision=_lib.PREC[precision], max_it=int(max_it), tol=float(tol),
+                               stream=_stream_ptr(stream, self.device), k_tile=int(k_tile),
+                               residual=_lib.RESIDUAL[residual])
+            st = _lib.load().bt_solve_host(self._h, _ptr(Fh), Fh.shape[2], _ptr(Xh), ctypes.byref(opts))
+            _lib.check(st, "bt_solve_host")
+            return Xh
         if host:
             if F.dtype != torch.float64:
                 raise TypeError("F must be float64")

@@ -224,3 +224,23 @@ def test_refined_sets_on_concurrent_streams(bt):
                 A, B, C = mats[i % 2]
                 Xr = oracle.solve_block_thomas(A, B, C, Fs_np[i])
                 assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10, (rnd, i)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_in_overlapped_chunks(bt, pinned):
+    # bt_solve_host: K = 300 host columns in chunks of 128, 128 and 44 whose
+    # uploads, solves and downloads overlap; FP64 and refined, three calls each
+    # (the device panel pairs replay their CUDA graphs from the third)
+    N, M, K, S = 64, 64, 300, 8
+    A, B, C = gen.dominant_blocks(N, M, seed=51)
+    F = gen.uniform_rhs(N, M, K, seed=52)
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    Fh = torch.from_numpy(F)
+    if pinned:
+        Fh = Fh.pin_memory()
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        for prec, bar in (("f64", 1e-12), ("bf16x3", 1e-10)):
+            for _ in range(3):
+                X = fac.solve(Fh, precision=prec, tol=1e-11)
+                assert X.device.type == "cpu" and X.shape == F.shape
+                assert oracle.rel_err(X.numpy(), Xr) <= bar, prec
