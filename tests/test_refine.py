@@ -244,3 +244,24 @@ def test_host_buffers_in_overlapped_chunks(bt, pinned):
                 X = fac.solve(Fh, precision=prec, tol=1e-11)
                 assert X.device.type == "cpu" and X.shape == F.shape
                 assert oracle.rel_err(X.numpy(), Xr) <= bar, prec
+
+
+def test_graph_cache_evicts_beyond_its_capacity(bt):
+    # 70 argument keys on one handle (more than the 64 graphs a handle keeps),
+    # each solved twice (the second call captures): the least recently used
+    # graphs are dropped and every solve still returns its own solution
+    N, M, S, K = 16, 64, 4, 3
+    A, B, C = gen.dominant_blocks(N, M, seed=61)
+    F = gen.uniform_rhs(N, M, K, seed=62)
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        Fd = _t(F)
+        outs = [torch.empty_like(Fd) for _ in range(70)]
+        for rnd in range(2):
+            for X in outs:
+                X.zero_()
+                fac.solve(Fd, precision="bf16x3", tol=1e-11, out=X)
+        fac.solve(Fd, precision="bf16x3", tol=1e-11, out=outs[0])  # evicted key: runs directly again
+        torch.cuda.synchronize()
+        for X in outs:
+            assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10

@@ -197,3 +197,18 @@ def test_refined_solve_with_digit_residual(bt, prec):
     Xr = oracle.solve_block_thomas(A, B, C, F)
     assert oracle.rel_err(X, Xr) <= 1e-10
     assert oracle.rel_err(X2.cpu().numpy(), Xr) <= 1e-10
+
+
+def test_residual_rejects_bad_arguments(bt):
+    N, M = 8, 64
+    A, B, C = gen.dominant_blocks(N, M, seed=1)
+    F = _t(gen.uniform_rhs(N, M, 2, seed=2))
+    with bt.factor(_t(A), _t(B), _t(C), 2) as fac:
+        lib = bt._lib.load()
+        R = torch.empty_like(F)
+        for args in [(F, F, F), (F, R, R)]:  # R aliasing F or X
+            st = lib.bt_residual(fac._h, bt.solver._ptr(args[0]), bt.solver._ptr(args[1]), 2,
+                                 bt.solver._ptr(args[2]), 2, None, None)
+            assert bt._lib.STATUS_NAMES.get(st) == "BT_ERR_ARG"
+        st = lib.bt_residual(fac._h, bt.solver._ptr(F), bt.solver._ptr(F), 2, bt.solver._ptr(R), 5, None, None)
+        assert bt._lib.STATUS_NAMES.get(st) == "BT_ERR_ARG"  # unknown method
