@@ -34,7 +34,7 @@
 // entries -- r large against the product scale (X far from a solution), or F
 // non-finite -- take an FP64 path.  Error against the exact residual, per
 // entry: at most 3M * 2.5 * 2^(e_A + e_X - 49) (fixed-point rounding of both
-// operands and the dropped pairs) plus half a unit u.
+// operands and the dropped pairs) plus one unit u (F truncated to the unit).
 //
 //   k_fac_digits    factor digits [3N][7][M][M] and e_A (once per handle)
 //   k_colmax        largest |X| of every column (its exponent)
