@@ -103,6 +103,40 @@ bt_status bt_factor(int64_t N, int64_t M, const double* A, const double* B, cons
                     int64_t S, void* stream, bt_handle* out);
 
 /*
+ * bt_factor_band -- bt_factor for a band matrix (Section 3.3.1, item c: the PML
+ * operator A_44, a band matrix solved by the dichotomy as a block-tridiagonal
+ * matrix with triangular off-diagonal blocks).
+ * Q: order n, kl sub-diagonals and ku super-diagonals (0 <= kl, ku <= M), in
+ *   diagonal-ordered storage: ab is a DEVICE (kl + ku + 1) x n row-major FP64
+ *   array with ab[(ku + i - j) * n + j] = Q[i][j] for -ku <= i - j <= kl
+ *   (the other positions of ab are not read).  Read only; may be freed when
+ *   the call returns.
+ * M: block size; S: segments.  The system is cut into N = S ceil(ceil(n/M)/S)
+ *   block rows of M rows (rows and columns n .. N M - 1 padded with the
+ *   identity), so that C_j = Q[jM.., jM..], A_j = -Q[jM.., (j-1)M..] (upper
+ *   triangular) and B_j = -Q[jM.., (j+1)M..] (lower triangular) in the sign
+ *   convention of bt_factor.  Needs 1 <= S <= ceil(n / M).
+ * The factorisation detects the bands of A_j and B_j (any bt_factor does) and
+ * runs its products with A_j and B_j over the nonzero diagonals only.
+ * Temporary device memory: the three block arrays (3 N M^2 doubles), released
+ * before return.  Errors as bt_factor.  Solve with bt_solve_band (or, when
+ * n = N M, with any bt_solve* call on (n x K) panels).
+ */
+bt_status bt_factor_band(int64_t n, int64_t kl, int64_t ku, const double* ab, int64_t M, int64_t S,
+                         void* stream, bt_handle* out);
+
+/*
+ * bt_solve_band -- bt_solve_ex on a handle of bt_factor_band: F and X are
+ * DEVICE n x K row-major FP64 panels (X must not overlap F); opts and info as
+ * bt_solve_ex (opts->stream carries the work).  When n < N M the call pads F
+ * with zero rows into a panel pair owned by the handle (grown on demand) and
+ * copies the first n rows of the solution to X.  BT_ERR_ARG on a handle not
+ * made by bt_factor_band; BT_ERR_NOCONV still writes the last iterate to X.
+ */
+bt_status bt_solve_band(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts,
+                        bt_info* info);
+
+/*
  * bt_solve -- Algorithm 2, stage 2 (Section 2.2, steps 2.1-2.3) in FP64:
  *   2.1  per-segment sweeps of eq. sub3 (W),
  *   2.2  Algorithm 1 on the reduced system eq. red1 (interface unknowns),
@@ -259,6 +293,15 @@ const char* bt_last_error(void);
  * operator), else 0, out[5] = device bytes held by the handle.
  */
 bt_status bt_handle_query(bt_handle h, int64_t out[6]);
+
+/*
+ * bt_handle_band -- the diagonal bands the factorisation found and used:
+ * out[0..1] = smallest and largest c - r over the nonzero entries (r, c) of
+ * A_j (j > 1), out[2..3] the same for B_j (j < N) (0, 0 for an all-zero
+ * operator; -(M-1), M-1 for a dense one), out[4] = n for a handle of
+ * bt_factor_band, else 0.
+ */
+bt_status bt_handle_band(bt_handle h, int64_t out[5]);
 
 /*
  * bt_factor_export -- copies one FP64 array of the factorisation into a

@@ -16,6 +16,9 @@ writes out):
   out by definition: the responses of eqs. sub1-sub3, the reduced system of
   eq. red1, Algorithm 1 applied to it, and the superposition of eq.
   superposition.  Used to pin the GPU path's intermediate products.
+* ``band``      -- a band matrix in diagonal-ordered storage and its cut into
+  the block-tridiagonal form (Section 3.3.1, item c: the PML operator solved
+  by the dichotomy with triangular off-diagonal blocks), identity-padded.
 * ``adjoint``   -- gradients of a loss through X = P^{-1} F (not in the paper;
   the standard adjoint identity dL/dP = -lambda X^T with P^T lambda = dL/dX).
 
@@ -44,3 +47,4 @@ from .alg2 import (  # noqa: F401
     alg2_solve,
 )
 from .adjoint import transpose_blocks, adjoint_grads  # noqa: F401
+from .band import band_dense, band_blocks, pad_rows  # noqa: F401

@@ -8,6 +8,7 @@ marshals arguments to it.
 """
 
 from ._lib import BtError, load  # noqa: F401
-from .solver import BatchPlan, Factorization, factor, solve_batched, solve_refined_sets  # noqa: F401
+from .solver import (BandFactorization, BatchPlan, Factorization, factor, factor_band,  # noqa: F401
+                     solve_batched, solve_refined_sets)
 from .autograd import BTSolve, bt_solve  # noqa: F401,E402
 from . import tune  # noqa: F401,E402

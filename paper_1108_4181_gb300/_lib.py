@@ -46,6 +46,9 @@ SIGNATURES = {
     "bt_solve": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "bt_solve_ex": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(BtOpts), ctypes.POINTER(BtInfo)]),
     "bt_solve_host": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(BtOpts)]),
+    "bt_factor_band": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, ctypes.POINTER(_vp)]),
+    "bt_solve_band": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(BtOpts), ctypes.POINTER(BtInfo)]),
+    "bt_handle_band": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "bt_solve_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "bt_residual": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp]),
     "bt_destroy": (None, [_vp]),

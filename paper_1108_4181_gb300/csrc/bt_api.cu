@@ -106,6 +106,7 @@ static void destroy_handle(bt_handle_s* h) {
     if (g.graph) cudaGraphDestroy(g.graph);
   }
   if (h->hp_buf) cudaFree(h->hp_buf);
+  if (h->band_buf) cudaFree(h->band_buf);
   if (h->hp_h2d) cudaStreamDestroy(h->hp_h2d);
   if (h->hp_d2h) cudaStreamDestroy(h->hp_d2h);
   for (cudaEvent_t e : h->hp_ev)
@@ -192,6 +193,82 @@ bt_status bt_factor(int64_t N, int64_t M, const double* A, const double* B, cons
   }
   BT_TRY(check_device());
   return make_handle(N, M, A, B, C, S, (cudaStream_t)stream, out);
+}
+
+bt_status bt_factor_band(int64_t n, int64_t kl, int64_t ku, const double* ab, int64_t M, int64_t S, void* stream,
+                         bt_handle* out) {
+  if (!out) {
+    set_error("bt_factor_band: out is NULL");
+    return BT_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n < 1 || M < 1 || M > 1024 || kl < 0 || ku < 0 || kl > M || ku > M || S < 1 || S > (n + M - 1) / M) {
+    set_error("bt_factor_band: need n >= 1, 1 <= M <= 1024, 0 <= kl, ku <= M and 1 <= S <= ceil(n / M)");
+    return BT_ERR_ARG;
+  }
+  if (!ab) {
+    set_error("bt_factor_band: ab must be a device pointer");
+    return BT_ERR_ARG;
+  }
+  BT_TRY(check_device());
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = ((n + M - 1) / M + S - 1) / S * S;
+  const size_t bytes = (size_t)N * M * M * sizeof(double);
+  double* blocks = nullptr;
+  BT_CUDA(cudaMallocAsync((void**)&blocks, 3 * bytes, st));
+  double *A = blocks, *B = blocks + (size_t)N * M * M, *C = blocks + 2 * (size_t)N * M * M;
+  bt_status s = band_to_blocks(ab, n, kl, ku, N, M, A, B, C, st);
+  if (s == BT_OK) s = make_handle(N, M, A, B, C, S, st, out);
+  // make_handle has synchronised the stream (or failed): the blocks are free to go
+  const cudaError_t e = cudaFreeAsync(blocks, st);
+  if (s != BT_OK) return s;
+  if (e != cudaSuccess) {
+    bt_destroy(*out);
+    *out = nullptr;
+    return cuda_fail(e, "cudaFreeAsync");
+  }
+  (*out)->band_n = n;
+  return BT_OK;
+}
+
+bt_status bt_solve_band(bt_handle h, const double* F, int64_t K, double* X, const bt_opts* opts, bt_info* info) {
+  if (!h || !F || !X || K < 1 || h->band_n < 1) {
+    set_error("bt_solve_band: need a handle of bt_factor_band, device F and X, K >= 1");
+    return BT_ERR_ARG;
+  }
+  const int64_t n = h->band_n, NM = h->N * h->M;
+  if (n == NM) return bt_solve_ex(h, F, K, X, opts, info);
+  const size_t bytes = (size_t)n * K * sizeof(double);
+  const char* f0 = reinterpret_cast<const char*>(F);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  if (f0 < x0 + bytes && x0 < f0 + bytes) {
+    set_error("bt_solve_band: X must not overlap F");
+    return BT_ERR_ARG;
+  }
+  const cudaStream_t st = (cudaStream_t)(opts ? opts->stream : nullptr);
+  const size_t panel = (size_t)NM * K * sizeof(double);
+  if (2 * panel > h->band_bytes) {
+    BT_CUDA(cudaDeviceSynchronize());
+    if (h->band_buf) BT_CUDA(cudaFree(h->band_buf));
+    h->band_buf = nullptr;
+    h->band_bytes = 0;
+    const cudaError_t e = cudaMalloc((void**)&h->band_buf, 2 * panel);
+    if (e != cudaSuccess) {
+      h->band_buf = nullptr;
+      set_error(std::string("bt_solve_band: panel allocation failed: ") + cudaGetErrorString(e));
+      return BT_ERR_OOM;
+    }
+    h->band_bytes = 2 * panel;
+  }
+  // rows n .. N*M-1 of the padded system are identity rows with zero right-hand side
+  double* Fp = h->band_buf;
+  double* Xp = h->band_buf + (size_t)NM * K;
+  BT_CUDA(cudaMemcpyAsync(Fp, F, bytes, cudaMemcpyDeviceToDevice, st));
+  BT_CUDA(cudaMemsetAsync(Fp + (size_t)n * K, 0, panel - bytes, st));
+  const bt_status s = bt_solve_ex(h, Fp, K, Xp, opts, info);
+  if (s != BT_OK && s != BT_ERR_NOCONV) return s;  // NOCONV still leaves the last iterate
+  BT_CUDA(cudaMemcpyAsync(X, Xp, bytes, cudaMemcpyDeviceToDevice, st));
+  return s;
 }
 
 bt_status bt_solve_stages(bt_handle h, const double* F, int64_t K, double* X, int32_t stages, void* stream) {
@@ -544,6 +621,16 @@ bt_status bt_handle_query(bt_handle h, int64_t out[6]) {
   out[3] = h->depth;
   out[4] = h->stencil;
   out[5] = (int64_t)(h->arena.bytes + h->scratch_bytes);
+  return BT_OK;
+}
+
+bt_status bt_handle_band(bt_handle h, int64_t out[5]) {
+  if (!h || !out) {
+    set_error("bt_handle_band: NULL argument");
+    return BT_ERR_ARG;
+  }
+  for (int k = 0; k < 4; ++k) out[k] = h->band[k];
+  out[4] = h->band_n;
   return BT_OK;
 }
 

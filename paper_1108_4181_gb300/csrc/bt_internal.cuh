@@ -88,6 +88,10 @@ struct bt_handle_s {
   int64_t N = 0, M = 0, S = 0, L = 0;
   int depth = 0;
   int stencil = 0;  // A_j = B_j = I, C_j tridiagonal
+  int band[4] = {0, 0, 0, 0};  // nonzero diagonals c - r of A_j: [lo, hi]; of B_j: [lo, hi]
+  int64_t band_n = 0;          // handles of bt_factor_band: rows n of the band matrix
+  double* band_buf = nullptr;  // padded F and X panels of bt_solve_band
+  size_t band_bytes = 0;
 
   bt::DevArena arena;
 
@@ -326,5 +330,9 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
 
 // Mixed-precision solve with iterative refinement (bt_solve_ex).
 bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info);
+
+// Band storage -> block arrays A, B, C of N block rows (band.cu).
+bt_status band_to_blocks(const double* ab, int64_t n, int64_t kl, int64_t ku, int64_t N, int64_t M, double* A,
+                         double* B, double* C, cudaStream_t st);
 
 }  // namespace bt

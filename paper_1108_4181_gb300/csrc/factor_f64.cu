@@ -26,6 +26,7 @@
 //   HL = R_ml At_l (l > 0),  HR = R_mr Bt_r (r < S-1).
 // The recurrences for R follow from R P_node = [0 .. I .. 0] column by column.
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 
@@ -42,12 +43,18 @@ namespace {
 // padding (M = 150: 64-tiles compute 192 x 192, 32-tiles 160 x 160).
 // Operands come from a device table of pointers, 4 per batch entry: X, Y, Z
 // (may be null when beta == 0), D (may alias Z).
+// bp = (xlo, xhi, ylo, yhi) bounds the diagonals that may hold nonzeros:
+// X[r][k] only where xlo <= k - r <= xhi, Y[k][c] only where ylo <= c - k <=
+// yhi, for every matrix of the batch.  The contraction of a tile runs over the
+// k that both bands admit for its rows and columns (a triangular or banded
+// operand A_j, B_j halves or shortens it); the skipped terms are exact zeros,
+// so the result is the same as the full contraction.  (-M, M, -M, M) = dense.
 // ---------------------------------------------------------------------------
 constexpr int GK = 16;
 
 template <int GT>
 __global__ void __launch_bounds__(256) k_gemm_batched(const double* const* __restrict__ tab, int M,
-                                                      double alpha, double beta) {
+                                                      double alpha, double beta, int4 bp) {
   constexpr int R = GT / 16;  // register tile R x R
   const double* X = tab[4 * blockIdx.z + 0];
   const double* Y = tab[4 * blockIdx.z + 1];
@@ -62,7 +69,9 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const double* const* __res
   for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < M; k0 += GK) {
+  const int kb = max(0, max(row0 + bp.x, col0 - bp.w)) / GK * GK;
+  const int ke = min(M, min(row0 + GT + bp.y, col0 + GT - bp.z));
+  for (int k0 = kb; k0 < ke; k0 += GK) {
     // X tile: rows row0..+GT, cols k0..+16 (stored transposed); Y tile: rows k0..+16, cols col0..+GT.
     for (int e = threadIdx.x; e < GT * GK; e += 256) {
       const int r = e / GK, c = e % GK;
@@ -265,6 +274,32 @@ __global__ void k_detect_stencil(const double* A, const double* B, const double*
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(not_stencil, 1);
 }
 
+// Diagonal bands of the coupling blocks: the smallest and largest c - r over
+// the nonzero (or non-finite) entries (r, c) of A_j, j >= 1, into prof[0..1]
+// and of B_j, j <= N - 2, into prof[2..3] (prof preset to INT_MAX, INT_MIN).
+// A block matrix made from a band matrix of half-bandwidths kl, ku <= M has
+// upper triangular A_j (c - r >= M - kl) and lower triangular B_j.
+__global__ void k_band_profile(const double* A, const double* B, int64_t N, int M, int* prof) {
+  const size_t MM = (size_t)M * M, n = (size_t)N * MM;
+  int alo = INT_MAX, ahi = INT_MIN, blo = INT_MAX, bhi = INT_MIN;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int64_t j = (int64_t)(e / MM);
+    const size_t w = e - (size_t)j * MM;
+    const int d = (int)(w % M) - (int)(w / M);
+    const double a = A[e], b = B[e];
+    if (j > 0 && a != 0.0) { alo = min(alo, d); ahi = max(ahi, d); }
+    if (j < N - 1 && b != 0.0) { blo = min(blo, d); bhi = max(bhi, d); }
+  }
+  alo = __reduce_min_sync(0xffffffffu, alo);
+  ahi = __reduce_max_sync(0xffffffffu, ahi);
+  blo = __reduce_min_sync(0xffffffffu, blo);
+  bhi = __reduce_max_sync(0xffffffffu, bhi);
+  if ((threadIdx.x & 31) == 0) {
+    if (alo <= ahi) { atomicMin(prof + 0, alo); atomicMax(prof + 1, ahi); }
+    if (blo <= bhi) { atomicMin(prof + 2, blo); atomicMax(prof + 3, bhi); }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Schedule builder
 // ---------------------------------------------------------------------------
@@ -273,16 +308,18 @@ struct Op {
   int batch;
   size_t off;  // into the pointer table
   double alpha, beta;
+  int4 bp;     // operand bands of a GEMM (see k_gemm_batched)
 };
 
 struct Schedule {
   std::vector<const double*> tab;
   std::vector<Op> ops;
   // GEMM batch under construction
-  void gemm(double alpha, double beta, const std::vector<const double*>& X, const std::vector<const double*>& Y,
-            const std::vector<const double*>& Z, const std::vector<double*>& D) {
+  void gemm(double alpha, double beta, int4 bp, const std::vector<const double*>& X,
+            const std::vector<const double*>& Y, const std::vector<const double*>& Z,
+            const std::vector<double*>& D) {
     if (D.empty()) return;
-    Op o{0, (int)D.size(), tab.size(), alpha, beta};
+    Op o{0, (int)D.size(), tab.size(), alpha, beta, bp};
     for (size_t b = 0; b < D.size(); ++b) {
       tab.push_back(X[b]);
       tab.push_back(Y[b]);
@@ -293,7 +330,7 @@ struct Schedule {
   }
   void inv(const std::vector<const double*>& X, const std::vector<double*>& Y) {
     if (Y.empty()) return;
-    Op o{1, (int)Y.size(), tab.size(), 0.0, 0.0};
+    Op o{1, (int)Y.size(), tab.size(), 0.0, 0.0, make_int4(0, 0, 0, 0)};
     for (size_t b = 0; b < Y.size(); ++b) {
       tab.push_back(X[b]);
       tab.push_back(Y[b]);
@@ -312,8 +349,10 @@ struct GemmBatch {
     Z.push_back(z);
     D.push_back(d);
   }
-  void flush(Schedule& s, double alpha, double beta) {
-    s.gemm(alpha, beta, X, Y, Z, D);
+  int4 dense = make_int4(-1024, 1024, -1024, 1024);
+  void flush(Schedule& s, double alpha, double beta) { flush(s, alpha, beta, dense); }
+  void flush(Schedule& s, double alpha, double beta, int4 bp) {
+    s.gemm(alpha, beta, bp, X, Y, Z, D);
     X.clear(); Y.clear(); Z.clear(); D.clear();
   }
 };
@@ -372,6 +411,23 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_CUDA(cudaMemsetAsync(h->A, 0, MM * sizeof(double), st));
   BT_CUDA(cudaMemsetAsync(h->B + (N - 1) * MM, 0, MM * sizeof(double), st));
 
+  // -- diagonal bands of A_j and B_j (structure the GEMMs below skip) -------
+  {
+    int* dprof = nullptr;
+    int hprof[4] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN};
+    BT_CUDA(cudaMallocAsync((void**)&dprof, sizeof(hprof), st));
+    BT_CUDA(cudaMemcpyAsync(dprof, hprof, sizeof(hprof), cudaMemcpyHostToDevice, st));
+    k_band_profile<<<1024, 256, 0, st>>>(h->A, h->B, N, M, dprof);
+    BT_CUDA(cudaGetLastError());
+    BT_CUDA(cudaMemcpyAsync(hprof, dprof, sizeof(hprof), cudaMemcpyDeviceToHost, st));
+    BT_CUDA(cudaStreamSynchronize(st));
+    BT_CUDA(cudaFreeAsync(dprof, st));
+    // an all-zero operand lies in any band: take the main diagonal
+    for (int k = 0; k < 4; k += 2)
+      if (hprof[k] > hprof[k + 1]) hprof[k] = hprof[k + 1] = 0;
+    for (int k = 0; k < 4; ++k) h->band[k] = hprof[k];
+  }
+
   // -- factor arrays --------------------------------------------------------
   for (double** p : {&h->Dinv, &h->E, &h->G, &h->U, &h->V}) {
     BT_TRY(ar.alloc((void**)p, N * MM * sizeof(double)));
@@ -404,6 +460,14 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   Schedule sc;
   GemmBatch g;
   InvBatch iv;
+  // GEMM operand bands: A_j or B_j on the left (onX) or on the right (onY)
+  const int4 dense = g.dense;
+  auto onX = [&](int lo, int hi) { return make_int4(lo, hi, dense.z, dense.w); };
+  auto onY = [&](int lo, int hi) { return make_int4(dense.x, dense.y, lo, hi); };
+  const int4 xA = onX(h->band[0], h->band[1]), xB = onX(h->band[2], h->band[3]);
+  const int4 yA = onY(h->band[0], h->band[1]), yB = onY(h->band[2], h->band[3]);
+  // one batch for A and B operands together when their bands coincide
+  const bool split = h->band[0] != h->band[2] || h->band[1] != h->band[3];
 
   // ---- step 1.1: block sweep factorisation of every segment interior ------
   for (int64_t t = 1; t < L; ++t) {
@@ -412,18 +476,16 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
         int64_t i = s * L + t;
         g.add(Aj(i), blk(h->G, i - 1), blk(h->C, i), blk(Dw, s));
       }
-      g.flush(sc, -1.0, 1.0);  // D = C_i - A_i G_{i-1}
+      g.flush(sc, -1.0, 1.0, xA);  // D = C_i - A_i G_{i-1}
       for (int64_t s = 0; s < S; ++s) iv.add(blk(Dw, s), blk(h->Dinv, s * L + t));
     } else {
       for (int64_t s = 0; s < S; ++s) iv.add(blk(h->C, s * L + t), blk(h->Dinv, s * L + t));
     }
     iv.flush(sc);
-    for (int64_t s = 0; s < S; ++s) {
-      int64_t i = s * L + t;
-      g.add(blk(h->Dinv, i), Bj(i), nullptr, blk(h->G, i));
-      g.add(blk(h->Dinv, i), Aj(i), nullptr, blk(h->E, i));
-    }
-    g.flush(sc, 1.0, 0.0);
+    for (int64_t s = 0; s < S; ++s) g.add(blk(h->Dinv, s * L + t), Bj(s * L + t), nullptr, blk(h->G, s * L + t));
+    if (split) g.flush(sc, 1.0, 0.0, yB);
+    for (int64_t s = 0; s < S; ++s) g.add(blk(h->Dinv, s * L + t), Aj(s * L + t), nullptr, blk(h->E, s * L + t));
+    g.flush(sc, 1.0, 0.0, yA);
   }
   // V (eq. sub2): backward products of G
   for (int64_t t = L - 1; t >= 1; --t) {
@@ -458,12 +520,13 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   auto Ur = [&](int64_t s) -> const double* { return s * L + 1 >= N ? Zw : (L == 1 ? Zw : blk(h->U, s * L + 1)); };
   auto Vr = [&](int64_t s) -> const double* { return s * L + 1 >= N ? Zw : (L == 1 ? Iw : blk(h->V, s * L + 1)); };
   for (int64_t s = 0; s < S; ++s) g.add(Aj(s * L), Ul(s), nullptr, blk(h->At, s));
+  if (split) g.flush(sc, 1.0, 0.0, xA);
   for (int64_t s = 0; s < S; ++s) g.add(Bj(s * L), Vr(s), nullptr, blk(h->Bt, s));
-  g.flush(sc, 1.0, 0.0);
+  g.flush(sc, 1.0, 0.0, xB);
   for (int64_t s = 0; s < S; ++s) g.add(Aj(s * L), Vl(s), blk(h->C, s * L), blk(h->Ct, s));
-  g.flush(sc, -1.0, 1.0);
+  g.flush(sc, -1.0, 1.0, xA);
   for (int64_t s = 0; s < S; ++s) g.add(Bj(s * L), Ur(s), blk(h->Ct, s), blk(h->Ct, s));
-  g.flush(sc, -1.0, 1.0);
+  g.flush(sc, -1.0, 1.0, xB);
 
   // ---- step 1.3: rows of the inverses for Algorithm 1 on P~ ---------------
   // Pw holds DL_j^{-1} / DR_j^{-1}; Dw holds DL_j / DR_j / Sigma; Tw products.
@@ -549,9 +612,9 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
       if (o.kind == 0) {
         dim3 grid(tiles, tiles, nb);
         if (GT == 32)
-          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta);
+          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
         else
-          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta);
+          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
       } else {
         k_inverse_batched<<<nb, inv_threads, inv_smem, st>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
       }

@@ -149,6 +149,14 @@ class Factorization:
         _lib.check(st, "bt_solve_stages")
         return X
 
+    def band(self) -> dict:
+        """Diagonal bands of A_j and B_j found at factorisation (c - r of their
+        nonzero entries), which the factor GEMMs contract over, and the order n
+        of a band-matrix handle (0 otherwise)."""
+        q = (ctypes.c_int64 * 5)()
+        _lib.check(_lib.load().bt_handle_band(self._h, q), "bt_handle_band")
+        return dict(A=(int(q[0]), int(q[1])), B=(int(q[2]), int(q[3])), n=int(q[4]))
+
     def export(self, what: str) -> torch.Tensor:
         """FP64 factor arrays: 'U', 'V' ([N, M, M]) or 'At', 'Ct', 'Bt' ([S, M, M])."""
         code = {"U": 0, "V": 1, "At": 2, "Ct": 3, "Bt": 4}[what]
@@ -203,6 +211,57 @@ def factor(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, S: int,
                                    ctypes.byref(h))
     _lib.check(st, "bt_factor")
     return Factorization(h, dev)
+
+
+class BandFactorization(Factorization):
+    """A factored band matrix of order n (Section 3.3.1, item c), held as the
+    block-tridiagonal system of bt_factor_band."""
+
+    def __init__(self, handle: ctypes.c_void_p, device: torch.device):
+        super().__init__(handle, device)
+        self.n = self.band()["n"]
+
+    def solve(self, F: torch.Tensor, precision: str = "f64", tol: float = 0.0, max_it: int = 0,
+              k_tile: int = 0, out: Optional[torch.Tensor] = None, return_info: bool = False,
+              stream: Optional[torch.cuda.Stream] = None, residual: str = "auto"):
+        """x = Q^{-1} F for F of shape [n] or [n, K] (float64, on the device)."""
+        vec = F.dim() == 1
+        Fd = _as_device_f64(F.reshape(-1, 1) if vec else F, self.device, "F")
+        if Fd.dim() != 2 or Fd.shape[0] != self.n:
+            raise ValueError(f"F must be [n] or [n, K] with n = {self.n}, got {tuple(F.shape)}")
+        X = out.reshape(Fd.shape) if out is not None else torch.empty_like(Fd)
+        if X.shape != Fd.shape or X.dtype != torch.float64 or not X.is_contiguous() or X.device != Fd.device:
+            raise ValueError("out must be a contiguous float64 tensor of F's shape on F's device")
+        opts = _lib.BtOpts(precision=_lib.PREC[precision], max_it=int(max_it), tol=float(tol),
+                           stream=_stream_ptr(stream, self.device), k_tile=int(k_tile),
+                           residual=_lib.RESIDUAL[residual])
+        info = _lib.BtInfo()
+        st = _lib.load().bt_solve_band(self._h, _ptr(Fd), Fd.shape[1], _ptr(X), ctypes.byref(opts),
+                                       ctypes.byref(info) if return_info else None)
+        _lib.check(st, "bt_solve_band")
+        X = X.reshape(-1) if vec else X
+        if return_info:
+            return X, dict(iters=info.iters, converged=bool(info.converged), rel_res=info.rel_res,
+                           rel_res0=info.rel_res0)
+        return X
+
+
+def factor_band(ab: torch.Tensor, kl: int, ku: int, M: int, S: int,
+                stream: Optional[torch.cuda.Stream] = None) -> BandFactorization:
+    """Factor a band matrix given in diagonal-ordered storage ab [kl + ku + 1, n]
+    (ab[ku + i - j, j] = Q[i, j]; the layout of LAPACK's and SciPy's banded
+    solvers) as a block-tridiagonal matrix of block size M >= kl, ku with S
+    segments (S <= ceil(n / M))."""
+    if ab.dim() != 2 or ab.shape[0] != kl + ku + 1:
+        raise ValueError(f"ab must be [kl + ku + 1, n] = [{kl + ku + 1}, n], got {tuple(ab.shape)}")
+    dev = ab.device
+    ab = _as_device_f64(ab, dev, "ab")
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        st = _lib.load().bt_factor_band(ab.shape[1], int(kl), int(ku), _ptr(ab), int(M), int(S),
+                                        _stream_ptr(stream, dev), ctypes.byref(h))
+    _lib.check(st, "bt_factor_band")
+    return BandFactorization(h, dev)
 
 
 def _batch_arrays(facs, Fs, Xs):

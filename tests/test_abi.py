@@ -55,3 +55,19 @@ def test_strerror_and_argument_errors_without_gpu(lib):
     # NULL handle / K = 0 rejected
     assert L.bt_solve(None, ctypes.c_void_p(8), 1, ctypes.c_void_p(16), None) == 1
     assert L.bt_solve_stages(None, ctypes.c_void_p(8), 0, ctypes.c_void_p(16), 3, None) == 1
+
+
+def test_band_argument_errors_without_gpu(lib):
+    from paper_1108_4181_gb300 import _lib
+
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    p = ctypes.c_void_p(8)
+    # kl > M, ku > M, S > ceil(n / M), n = 0, NULL storage: rejected on the host
+    for args in [(100, 9, 3, p, 8, 1), (100, 3, 9, p, 8, 1), (100, 3, 3, p, 8, 14), (0, 1, 1, p, 8, 1),
+                 (100, 3, 3, None, 8, 1)]:
+        assert L.bt_factor_band(*args, None, ctypes.byref(h)) == 1
+        assert not h.value
+    assert L.bt_solve_band(None, p, 1, ctypes.c_void_p(16), None, None) == 1
+    out = (ctypes.c_int64 * 5)()
+    assert L.bt_handle_band(None, out) == 1

@@ -439,3 +439,71 @@ def test_pins_catch_planted_dichotomy_mistake():
 
     assert np.abs(oracle.dichotomy_solve(At, Ct, Bt, Ft) - ref).max() < 1e-13
     assert np.abs(mutant() - ref).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# band matrices as block-tridiagonal systems (Section 3.3.1, item c)
+# ---------------------------------------------------------------------------
+from oracle import band as band_mod  # noqa: E402
+import scipy.sparse  # noqa: E402
+
+
+@pytest.mark.parametrize("n,kl,ku", [(11, 2, 3), (40, 0, 4), (33, 5, 0), (17, 1, 1), (6, 5, 5)])
+def test_band_dense_matches_scipy_dia(n, kl, ku):
+    # SciPy's DIA format stores diagonal `offset` column-aligned, the same
+    # convention as LAPACK band storage: an independent reading of ab
+    ab = gen.band_matrix(n, kl, ku, seed=n)
+    D = scipy.sparse.dia_matrix((ab, list(range(ku, -kl - 1, -1))), shape=(n, n)).toarray()
+    assert np.array_equal(band_mod.band_dense(ab, kl, ku), D)
+
+
+BAND_CASES = [(64, 8, 8, 8, 2, 2), (61, 3, 7, 8, 2, 3), (100, 12, 5, 16, 3, 1), (29, 1, 1, 1, 4, 2),
+              (50, 0, 6, 6, 3, 2), (45, 9, 9, 9, 5, 1)]
+
+
+@pytest.mark.parametrize("n,kl,ku,M,S,K", BAND_CASES)
+def test_band_blocks_solve_matches_lapack_banded(n, kl, ku, M, S, K):
+    # the block form, solved by block Thomas, against LAPACK's banded LU (gbsv)
+    ab = gen.band_matrix(n, kl, ku, seed=n + M)
+    F = np.random.default_rng(n).uniform(-1, 1, (n, K))
+    A, B, C, N = band_mod.band_blocks(ab, kl, ku, M, S)
+    assert N % S == 0 and N * M >= n and (N - S) * M < n  # fewest block rows S allows
+    X = oracle.solve_block_thomas(A, B, C, band_mod.pad_rows(F, N, M)).reshape(N * M, K)
+    Xl = scipy.linalg.solve_banded((kl, ku), ab, F)
+    assert oracle.rel_err(X[:n], Xl) < 1e-13
+    assert np.abs(X[n:]).max(initial=0.0) == 0.0  # identity rows, zero right-hand side
+
+
+@pytest.mark.parametrize("n,kl,ku,M,S,K", BAND_CASES)
+def test_band_blocks_product_and_triangular_structure(n, kl, ku, M, S, K):
+    ab = gen.band_matrix(n, kl, ku, seed=n + M)
+    X = np.random.default_rng(n + 1).uniform(-1, 1, (n, K))
+    A, B, C, N = band_mod.band_blocks(ab, kl, ku, M, S)
+    Q = scipy.sparse.dia_matrix((ab, list(range(ku, -kl - 1, -1))), shape=(n, n)).toarray()
+    Y = oracle.apply_P(A, B, C, band_mod.pad_rows(X, N, M)).reshape(N * M, K)
+    np.testing.assert_allclose(Y[:n], Q @ X, rtol=0, atol=1e-13 * np.abs(Q).sum(axis=1).max())
+    # the structure the paper notes: A_j upper triangular (nonzero only where
+    # c - r >= M - kl), B_j lower triangular (c - r <= ku - M)
+    d = np.arange(M)[None, :] - np.arange(M)[:, None]
+    assert (A[:, d < M - kl] == 0).all() and (B[:, d > ku - M] == 0).all()
+
+
+def test_band_mutations_are_caught():
+    n, kl, ku, M, S = 61, 3, 7, 8, 2
+    ab = gen.band_matrix(n, kl, ku, seed=4)
+    F = np.random.default_rng(4).uniform(-1, 1, (n, 2))
+    Xl = scipy.linalg.solve_banded((kl, ku), ab, F)
+    D = scipy.sparse.dia_matrix((ab, list(range(ku, -kl - 1, -1))), shape=(n, n)).toarray()
+    # storage read transposed (ab[ku + j - i, i]): the DIA pin fails
+    Qt = np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - ku), min(n, i + kl + 1)):
+            Qt[i, j] = ab[ku + j - i, i] if 0 <= ku + j - i <= kl + ku else 0.0
+    assert not np.array_equal(Qt, D)
+    # sign slip on the coupling blocks (A_j = +Q[jM.., (j-1)M..]): the gbsv pin fails
+    A, B, C, N = band_mod.band_blocks(ab, kl, ku, M, S)
+    X = oracle.solve_block_thomas(-A, B, C, band_mod.pad_rows(F, N, M)).reshape(N * M, 2)
+    assert oracle.rel_err(X[:n], Xl) > 1e-6
+    # off-by-one block row in the cut: the gbsv pin fails
+    X = oracle.solve_block_thomas(np.roll(A, 1, axis=0), B, C, band_mod.pad_rows(F, N, M)).reshape(N * M, 2)
+    assert oracle.rel_err(X[:n], Xl) > 1e-6

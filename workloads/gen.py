@@ -72,6 +72,26 @@ def dominant_blocks(N: int, M: int, seed: int):
     return A, B, C
 
 
+def band_matrix(n: int, kl: int, ku: int, seed: int):
+    """Diagonally dominant band matrix of order n in diagonal-ordered storage
+    ab [kl + ku + 1, n], ab[ku + i - j, j] = Q[i, j]: off-diagonal entries
+    ~ U[-1, 1), Q[i, i] = sum of |off-diagonal| of row i + 1 + U[0, 1).  The
+    positions of ab outside the matrix are zero."""
+    rng = np.random.default_rng(seed)
+    ab = rng.random((kl + ku + 1, n)) * 2.0 - 1.0
+    noise = rng.random(n)
+    cols = np.arange(n)
+    rowsum = np.zeros(n)
+    for d in range(kl + ku + 1):
+        rows = cols + d - ku  # row i of entry ab[d, j]
+        ok = (rows >= 0) & (rows < n)
+        ab[d, ~ok] = 0.0
+        if d != ku:
+            rowsum[rows[ok]] += np.abs(ab[d, ok])  # distinct rows within one diagonal
+    ab[ku] = rowsum + 1.0 + noise
+    return ab
+
+
 def dominant_blocks_device(N: int, M: int, seed: int, device):
     """The distribution of `dominant_blocks`, drawn on a torch device (for the
     paper-sized shapes, whose blocks reach tens of GB): A_j, B_j ~ U[0,1),
