@@ -19,10 +19,16 @@ writes out):
 * ``band``      -- a band matrix in diagonal-ordered storage and its cut into
   the block-tridiagonal form (Section 3.3.1, item c: the PML operator solved
   by the dichotomy with triangular off-diagonal blocks), identity-padded.
+* ``schur``     -- the Schur-complement CG of Section 3.3 on a strip
+  decomposition of the five-point grid operator: the product with S (each
+  strip inverted as a block-tridiagonal system), the reduced right-hand side,
+  the recovery of eq. domains_equation, the probing band preconditioner of
+  Section 3.3.2 and textbook preconditioned CG.
 * ``adjoint``   -- gradients of a loss through X = P^{-1} F (not in the paper;
   the standard adjoint identity dL/dP = -lambda X^T with P^T lambda = dL/dX).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(``schur`` by ``tests/test_schur_oracle.py``)
 against values fixed independently of this code (closed forms, library
 routines, invariants, brute force).  No function is "parity unpinned".
 """
