@@ -295,6 +295,67 @@ const char* bt_last_error(void);
 bt_status bt_handle_query(bt_handle h, int64_t out[6]);
 
 /*
+ * Schur-complement CG with a probing band preconditioner (Section 3.3: the
+ * interface system of eq. schur_decomp solved by CG without forming S, the
+ * interiors by eq. domains_equation; Section 3.3.2: the probing band
+ * preconditioner B, inverted by the dichotomy).
+ * Model problem: the five-point operator (4 + shift) x_{z,r} - x_{z-1,r} -
+ * x_{z+1,r} - x_{z,r-1} - x_{z,r+1} (zero values outside) on an nz x nr grid,
+ * cut by p - 1 interface grid rows into p strips of h rows: nz = p h + p - 1,
+ * strip i holds rows i (h + 1) .. i (h + 1) + h - 1, interface line k is row
+ * k (h + 1) + h.  Each strip operator, unknowns ordered by grid column, is a
+ * block-tridiagonal system with N = nr blocks of M = h (A_j = B_j = I,
+ * C_j = tridiag(-1, 4 + shift, -1)); the strips share one factorisation (S
+ * segments) and are solved together, p K columns per dichotomy solve.
+ * Panels: grid F, X [nz][nr][K]; interface v, g [p - 1][nr][K] (ng = (p-1) nr
+ * rows); all FP64 device arrays, K contiguous.
+ */
+typedef struct bt_schur_s* bt_schur;
+
+/*
+ * bt_schur_create -- factors the strip operator and builds the preconditioner:
+ * one product of S with the 2d+1 probing vectors (1 on the interface indices
+ * congruent to l modulo 2d+1), B[i][j] = (S p_{j mod (2d+1)})[i] for
+ * |i - j| <= d, symmetrised ((B + B^T) / 2; S is symmetric), factored by
+ * bt_factor_band with blocks of max(16, d) rows.  d = -1: no preconditioner.
+ * Needs nr >= 1, 1 <= h <= 1024, p >= 2, nr % S == 0, shift >= 0 and
+ * -1 <= d < min(1025, ng).  Synchronises `stream`.  Errors as bt_factor.
+ */
+bt_status bt_schur_create(int64_t nr, int64_t h, int64_t p, double shift, int64_t d, int64_t S, void* stream,
+                          bt_schur* out);
+
+/* S v for an interface panel v (K columns) into out (distinct from v); asynchronous. */
+bt_status bt_schur_apply(bt_schur s, const double* v, int64_t K, double* out, void* stream);
+
+/* g = f_G - sum_i A_Gi A_ii^{-1} f_i for a grid panel F (eq. schur_decomp); asynchronous. */
+bt_status bt_schur_rhs(bt_schur s, const double* F, int64_t K, double* g, void* stream);
+
+/*
+ * bt_schur_solve -- X = A^{-1} F for a grid panel F: g, then preconditioned CG
+ * (Saad, Algorithm 9.1) on S x_G = g for all K columns at once from x_G = 0,
+ * a column stopping once ||g - S x_G|| <= tol ||g|| (the recursively updated
+ * residual), at most max_it iterations; then the interiors (eq.
+ * domains_equation) and X.  Each iteration: one product with S (one
+ * dichotomy solve of p K columns), one solve with B, four column dot products;
+ * the host reads the number of unconverged columns once per iteration
+ * (synchronous).  X must not overlap F.  info (may be NULL): iterations,
+ * converged, rel_res = the largest relative residual over the columns,
+ * rel_res0 = 1.  BT_ERR_NOCONV if a column did not converge (X is then the
+ * solution for the last iterate).
+ */
+bt_status bt_schur_solve(bt_schur s, const double* F, int64_t K, double* X, double tol, int32_t max_it,
+                         void* stream, bt_info* info);
+
+/* Copies B (band storage [2d+1][ng], ab[d + i - j][j] = B[i][j]) to a device buffer; synchronous. */
+bt_status bt_schur_band(bt_schur s, double* ab);
+
+/* out = {nr, h, p, nz, ng, d, block size of B, segments of B}. */
+bt_status bt_schur_query(bt_schur s, int64_t out[8]);
+
+/* Releases the handle (synchronises the device). */
+void bt_schur_destroy(bt_schur s);
+
+/*
  * bt_handle_band -- the diagonal bands the factorisation found and used:
  * out[0..1] = smallest and largest c - r over the nonzero entries (r, c) of
  * A_j (j > 1), out[2..3] the same for B_j (j < N) (0, 0 for an all-zero

@@ -173,3 +173,13 @@ def pcg(apply_S, solve_B, g, tol: float, max_it: int):
         pdir = z + beta * pdir
         rz = rz_new
     return x, it, np.sqrt((r * r).sum(axis=0)) / np.where(gn > 0, gn, 1.0)
+
+
+def grid_apply(X, shift: float):
+    """A X for the five-point grid operator on a panel X [nz, nr, K] (zero outside the grid)."""
+    Y = (4.0 + shift) * X
+    Y[1:] -= X[:-1]
+    Y[:-1] -= X[1:]
+    Y[:, 1:] -= X[:, :-1]
+    Y[:, :-1] -= X[:, 1:]
+    return Y

@@ -12,3 +12,4 @@ from .solver import (BandFactorization, BatchPlan, Factorization, factor, factor
                      solve_batched, solve_refined_sets)
 from .autograd import BTSolve, bt_solve  # noqa: F401,E402
 from . import tune  # noqa: F401,E402
+from .schur import SchurPCG  # noqa: F401,E402

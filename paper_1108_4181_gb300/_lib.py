@@ -49,6 +49,13 @@ SIGNATURES = {
     "bt_factor_band": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _i64, _vp, ctypes.POINTER(_vp)]),
     "bt_solve_band": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.POINTER(BtOpts), ctypes.POINTER(BtInfo)]),
     "bt_handle_band": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "bt_schur_create": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_double, _i64, _i64, _vp, ctypes.POINTER(_vp)]),
+    "bt_schur_apply": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "bt_schur_rhs": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "bt_schur_solve": (ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_double, _i32, _vp, ctypes.POINTER(BtInfo)]),
+    "bt_schur_band": (ctypes.c_int, [_vp, _vp]),
+    "bt_schur_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "bt_schur_destroy": (None, [_vp]),
     "bt_solve_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     "bt_residual": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp]),
     "bt_destroy": (None, [_vp]),

@@ -71,3 +71,17 @@ def test_band_argument_errors_without_gpu(lib):
     assert L.bt_solve_band(None, p, 1, ctypes.c_void_p(16), None, None) == 1
     out = (ctypes.c_int64 * 5)()
     assert L.bt_handle_band(None, out) == 1
+
+
+def test_schur_argument_errors_without_gpu(lib):
+    from paper_1108_4181_gb300 import _lib
+
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    # p < 2, nr % S != 0, d >= ng, negative shift, h > 1024: rejected on the host
+    for args in [(16, 4, 1, 0.0, 1, 1), (16, 4, 2, 0.0, 1, 3), (16, 4, 2, 0.0, 16, 1), (16, 4, 2, -1.0, 1, 1),
+                 (16, 1025, 2, 0.0, 1, 1), (16, 4, 2, 0.0, -2, 1)]:
+        assert L.bt_schur_create(*args, None, ctypes.byref(h)) == 1
+        assert not h.value
+    assert L.bt_schur_solve(None, ctypes.c_void_p(8), 1, ctypes.c_void_p(16), 1e-8, 10, None, None) == 1
+    assert L.bt_schur_apply(None, ctypes.c_void_p(8), 1, ctypes.c_void_p(16), None) == 1

@@ -139,3 +139,10 @@ def test_planted_mistakes_fail():
         pd = r + rzn / rz * pd
         rz = rzn
     assert np.abs(x - np.linalg.solve(S2, g)).max() > 1e-3
+
+
+def test_grid_apply_matches_the_assembled_matrix():
+    nz, nr, K = 11, 7, 3
+    X = np.random.default_rng(5).uniform(-1, 1, (nz, nr, K))
+    Y = _grid_matrix(nz, nr, 0.5) @ X.reshape(nz * nr, K)
+    np.testing.assert_allclose(schur.grid_apply(X, 0.5), Y.reshape(nz, nr, K), rtol=0, atol=1e-14)
