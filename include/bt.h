@@ -324,10 +324,11 @@ typedef struct bt_schur_s* bt_schur;
 bt_status bt_schur_create(int64_t nr, int64_t h, int64_t p, double shift, int64_t d, int64_t S, void* stream,
                           bt_schur* out);
 
-/* S v for an interface panel v (K columns) into out (distinct from v); asynchronous. */
+/* S v for an interface panel v (K columns) into out (must not overlap v); asynchronous. */
 bt_status bt_schur_apply(bt_schur s, const double* v, int64_t K, double* out, void* stream);
 
-/* g = f_G - sum_i A_Gi A_ii^{-1} f_i for a grid panel F (eq. schur_decomp); asynchronous. */
+/* g = f_G - sum_i A_Gi A_ii^{-1} f_i for a grid panel F (eq. schur_decomp) into an interface
+ * panel g (must not overlap F); asynchronous. */
 bt_status bt_schur_rhs(bt_schur s, const double* F, int64_t K, double* g, void* stream);
 
 /*

@@ -214,6 +214,12 @@ __global__ void k_pcg_p(double* __restrict__ pd, const double* __restrict__ z, c
   }
 }
 
+// [a, a + na) and [b, b + nb) (doubles) share an element
+bool overlap(const double* a, const double* b, size_t na, size_t nb = 0) {
+  if (nb == 0) nb = na;
+  return a < b + nb && b < a + na;
+}
+
 int grid_for(const void* fn, size_t tot) {
   return (int)std::max<size_t>(1, std::min<size_t>((tot + 255) / 256, (size_t)resident_grid(fn, 256, 0)));
 }
@@ -406,8 +412,8 @@ bt_status bt_schur_band(bt_schur s, double* ab) {
 }
 
 bt_status bt_schur_apply(bt_schur s, const double* v, int64_t K, double* out, void* stream) {
-  if (!s || !v || !out || K < 1 || v == out) {
-    set_error("bt_schur_apply: need a handle, distinct device v and out, K >= 1");
+  if (!s || !v || !out || K < 1 || overlap(v, out, (size_t)s->ng * K)) {
+    set_error("bt_schur_apply: need a handle, non-overlapping device v and out, K >= 1");
     return BT_ERR_ARG;
   }
   const cudaStream_t st = (cudaStream_t)stream;
@@ -416,8 +422,8 @@ bt_status bt_schur_apply(bt_schur s, const double* v, int64_t K, double* out, vo
 }
 
 bt_status bt_schur_rhs(bt_schur s, const double* F, int64_t K, double* g, void* stream) {
-  if (!s || !F || !g || K < 1) {
-    set_error("bt_schur_rhs: need a handle, device F and g, K >= 1");
+  if (!s || !F || !g || K < 1 || overlap(F, g, (size_t)s->nz * s->nr * K, (size_t)s->ng * K)) {
+    set_error("bt_schur_rhs: need a handle, non-overlapping device F and g, K >= 1");
     return BT_ERR_ARG;
   }
   const cudaStream_t st = (cudaStream_t)stream;
@@ -431,10 +437,7 @@ bt_status bt_schur_solve(bt_schur s, const double* F, int64_t K, double* X, doub
     set_error("bt_schur_solve: need a handle, device F and X, K >= 1, tol > 0, max_it >= 0");
     return BT_ERR_ARG;
   }
-  const size_t bytes = (size_t)s->nz * s->nr * K * sizeof(double);
-  const char* f0 = reinterpret_cast<const char*>(F);
-  const char* x0 = reinterpret_cast<const char*>(X);
-  if (f0 < x0 + bytes && x0 < f0 + bytes) {
+  if (overlap(F, X, (size_t)s->nz * s->nr * K)) {
     set_error("bt_schur_solve: X must not overlap F");
     return BT_ERR_ARG;
   }
