@@ -229,9 +229,10 @@ class BandFactorization(Factorization):
         Fd = _as_device_f64(F.reshape(-1, 1) if vec else F, self.device, "F")
         if Fd.dim() != 2 or Fd.shape[0] != self.n:
             raise ValueError(f"F must be [n] or [n, K] with n = {self.n}, got {tuple(F.shape)}")
-        X = out.reshape(Fd.shape) if out is not None else torch.empty_like(Fd)
-        if X.shape != Fd.shape or X.dtype != torch.float64 or not X.is_contiguous() or X.device != Fd.device:
+        if out is not None and (out.shape != F.shape or out.dtype != torch.float64 or not out.is_contiguous()
+                                or out.device != Fd.device):
             raise ValueError("out must be a contiguous float64 tensor of F's shape on F's device")
+        X = out.view(Fd.shape) if out is not None else torch.empty_like(Fd)
         opts = _lib.BtOpts(precision=_lib.PREC[precision], max_it=int(max_it), tol=float(tol),
                            stream=_stream_ptr(stream, self.device), k_tile=int(k_tile),
                            residual=_lib.RESIDUAL[residual])
