@@ -682,6 +682,53 @@ def run_paper(args):
     return 0
 
 
+def run_schur(args):
+    """Schur-complement CG with the probing band preconditioner (Section 3.3) on the
+    five-point grid cut into strips: for each probing band d, the wall time of building the
+    solver (strip factorisation, the probing product, B and its factorisation: the paper's
+    Gen), of one PCG solve of K right-hand sides to tol 1e-10 (Total) and the iteration
+    count -- the quantities of the paper's Table 3 on this model problem."""
+    import torch
+
+    import paper_1108_4181_gb300 as bt
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nr, h, p, K, Sg, tol = 2048, 64, 4, 8, 32, 1e-10
+    nz = p * h + p - 1
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    F = torch.rand((nz, nr, K), dtype=torch.float64, device=dev, generator=g) * 2 - 1
+    with bt.SchurPCG(256, 8, 2, 0.0, d=2, S=8) as sp0:  # library and context set-up outside the timings
+        sp0.solve(torch.ones((17, 256, 1), dtype=torch.float64, device=dev))
+    rows = []
+    for d in [int(v) for v in args.schur_bands.split(",")]:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sp = bt.SchurPCG(nr, h, p, 0.0, d=d, S=Sg)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        _, info = sp.solve(F, tol=tol, max_it=5000, return_info=True, check=False)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        sp.close()
+        rows.append({"d": d, "gen_s": t1 - t0, "total_s": t2 - t1, **info})
+        print(f"schur d={d}: {json.dumps(rows[-1])}", file=sys.stderr, flush=True)
+    base = next((r for r in rows if r["d"] < 0), None)
+    best = min(rows, key=lambda r: r["total_s"])
+    line = {
+        "metric": "PCG solve time without preconditioner / with the best probing band",
+        "value": base["total_s"] / best["total_s"] if base else None, "unit": "x", "higher_is_better": True,
+        "n_gpus": 1, "steps": 1, "warmup": 1, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (F ~ U[-1,1])",
+        "config": {"workload": f"Schur-complement CG: five-point operator on a {nz} x {nr} grid, {p} strips of "
+                               f"{h} rows, K={K}, strip solves S={Sg}, tol {tol}"},
+        "bands": rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -695,9 +742,12 @@ def main():
                     help="refinement target ||F - P X|| / ||F|| (default 1e-10)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path beside")
-    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson", "paper"], default="acoustic",
-                    help="acoustic (the headline), the batched uneven-set workload, or the Poisson workload "
-                         "(N=1024, M=256, K=64, S=64)")
+    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson", "paper", "schur"], default="acoustic",
+                    help="acoustic (the headline), the batched uneven-set workload, the Poisson workload "
+                         "(N=1024, M=256, K=64, S=64), the paper's Table 1-2 shapes, or the Schur-complement "
+                         "CG with probing")
+    ap.add_argument("--schur-bands", default="-1,1,2,4,8,16,32",
+                    help="with --workload schur: probing half-bandwidths d (-1 = no preconditioner)")
     ap.add_argument("--rows", type=int, default=N,
                     help="block rows N (smaller values only for profiler captures; the bench workload is 4096)")
     ap.add_argument("--segments", type=int, default=S, help="segments S (default 64)")
@@ -725,6 +775,8 @@ def main():
         return run_batched(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "schur":
+        return run_schur(args)
     return run_ours(args)
 
 
