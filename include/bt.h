@@ -94,7 +94,11 @@ typedef struct {
  * A, B, C  device pointers as described above; they are only read, and may be
  *     freed once this call returns.
  * out receives a handle that owns all factor memory on the current device.
- * The call synchronises `stream` once to read the pivot status:
+ * The products with A_j and B_j run over the diagonals that hold their
+ * nonzero entries only (found by a scan of A and B; see bt_handle_band), which
+ * gives the same values as full products.
+ * The call synchronises `stream` twice: to read those bands before the
+ * factorisation is scheduled, and to read the pivot status at the end:
  *   BT_ERR_SINGULAR if any pivot block is singular or non-finite (no handle
  *   is returned), BT_ERR_ARG for invalid sizes or NULL pointers,
  *   BT_ERR_OOM / BT_ERR_CUDA on device failures.
