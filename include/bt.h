@@ -89,7 +89,7 @@ typedef struct {
  *        the coupling responses U, V of eqs. sub1 / sub2;
  *   1.2  the reduced (interface) system of eq. red1;
  *   1.3  the stored block rows of the inverses needed by Algorithm 1 on it.
- * N   block rows (>= 1); M block size (1..256); S segments, 1 <= S <= N and
+ * N   block rows (>= 1); M block size (1..1024; tested up to 256); S segments, 1 <= S <= N and
  *     N % S == 0 (the paper's L = N/p); interface rows are 1, L+1, ..., (S-1)L+1.
  * A, B, C  device pointers as described above; they are only read, and may be
  *     freed once this call returns.
