@@ -23,10 +23,6 @@
  *   - There is no CPU fallback: every arithmetic step runs in this library's
  *     CUDA kernels; a call on a machine without a usable sm_103 GPU fails
  *     with BT_ERR_CUDA.
- *   - Tuning variable: BT_TC_CLUSTER=2 or 4 makes the tensor-core sweep and
- *     correction CTAs of neighbouring column tiles share each factor slice
- *     through a TMA multicast within a thread-block cluster (default 1: each
- *     CTA loads its own slices; read once per process).
  */
 #ifndef BT_H_
 #define BT_H_
@@ -268,10 +264,14 @@ bt_status bt_solve_batched(int32_t n, const bt_handle* h, const double* const* F
  * until the process exits.
  *   - F, K, X, stream: as for bt_solve (the caller owns inputs and outputs).
  *   - The scratch needed is depth * S * M * K * 8 bytes (depth from
- *     bt_handle_query); larger requests return BT_ERR_ARG and do nothing.
+ *     bt_handle_query); larger requests (and K < 1) return BT_ERR_ARG and do
+ *     nothing.  The check divides instead of multiplying, so no K wraps it.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) for that device; make that first call before any
- *     stream capture.  The device of the handle must be current.
+ *     stream capture.  The device of the handle must be current.  The address
+ *     is kept per device together with the CUDA context it was found in; a
+ *     call in another context (after a device reset) looks it up again -- and
+ *     should again come before any stream capture.
  *   - All calls share the one array per device: calls whose work overlaps on
  *     the GPU (other streams, other threads) race on it and give wrong results.
  *     The array keeps the previous call's contents; this solve overwrites

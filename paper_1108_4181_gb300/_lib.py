@@ -18,6 +18,8 @@ STATUS_NAMES = {
     0: "BT_OK", 1: "BT_ERR_ARG", 2: "BT_ERR_SINGULAR", 3: "BT_ERR_CUDA", 4: "BT_ERR_NOCONV",
     5: "BT_ERR_TIMEOUT", 6: "BT_ERR_OOM", 7: "BT_ERR_UNSUPPORTED",
 }
+# bytes of the fixed scratch array of bt_solve_noalloc (BT_NOALLOC_SCRATCH_BYTES in bt.h)
+NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 PREC = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3, "bf16x3": 4}
 RESIDUAL = {"auto": 0, "fp64": 1, "digits": 2}
 

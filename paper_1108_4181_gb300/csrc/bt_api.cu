@@ -291,6 +291,10 @@ bt_status bt_solve_noalloc(bt_handle h, const double* F, int64_t K, double* X, v
     set_error("bt_solve_noalloc: need a handle, device F and X, K >= 1");
     return BT_ERR_ARG;
   }
+  if ((uint64_t)K > (uint64_t)INT64_MAX / ((uint64_t)h->N * h->M * sizeof(double))) {
+    set_error("bt_solve_noalloc: K too large for the scratch array");
+    return BT_ERR_ARG;
+  }
   const size_t bytes = (size_t)h->N * h->M * K * sizeof(double);
   const char* f0 = reinterpret_cast<const char*>(F);
   const char* x0 = reinterpret_cast<const char*>(X);

@@ -445,14 +445,41 @@ static __device__ __align__(256) double g_noalloc_scratch[BT_NOALLOC_SCRATCH_BYT
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// Per device: the context the address was looked up in, and the address.  A
+// device reset creates a new primary context in which the module (and the
+// array) may sit elsewhere, so the address is looked up again when the
+// current context differs from the recorded one.
+struct NoAllocAddr {
+  void* ctx;
+  double* addr;
+};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// The current driver context (cuCtxGetCurrent through the runtime's driver
+// entry point table; the library links only the runtime).
+bool current_context(void** ctx) {
+  using Fn = int (*)(void**);
+  static Fn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (Fn) nullptr;
+    return reinterpret_cast<Fn>(p);
+  }();
+  *ctx = nullptr;
+  return fn != nullptr && fn(ctx) == 0 && *ctx != nullptr;
+}
 }  // namespace
 
 bt_status solve_f64_noalloc(bt_handle_s* h, const double* F, int64_t K, double* X, cudaStream_t st) {
-  const size_t need = (size_t)h->depth * h->S * h->M * K * sizeof(double);
-  if (need > (size_t)BT_NOALLOC_SCRATCH_BYTES) {
-    set_error("bt_solve_noalloc: needs " + std::to_string(need) + " bytes of scratch (depth*S*M*K*8), more than " +
-              "the " + std::to_string((size_t)BT_NOALLOC_SCRATCH_BYTES) + " bytes compiled into the library");
+  // refuse before multiplying by K, so that a huge K cannot wrap the product
+  const size_t per_col = (size_t)h->depth * h->S * h->M * sizeof(double);
+  const size_t max_cols = per_col > 0 ? (size_t)BT_NOALLOC_SCRATCH_BYTES / per_col : 0;
+  if (per_col == 0 || K <= 0 || (uint64_t)K > max_cols) {
+    set_error("bt_solve_noalloc: needs depth*S*M*K*8 = " + std::to_string(per_col) + " * " + std::to_string(K) +
+              " bytes of scratch, more than the " + std::to_string((size_t)BT_NOALLOC_SCRATCH_BYTES) +
+              " bytes compiled into the library (at most K = " + std::to_string(max_cols) + " for this handle)");
     return BT_ERR_ARG;
   }
   int dev = 0;
@@ -461,16 +488,23 @@ bt_status solve_f64_noalloc(bt_handle_s* h, const double* F, int64_t K, double* 
     set_error("bt_solve_noalloc: the handle's device must be current (and below device index 64)");
     return BT_ERR_ARG;
   }
+  void* ctx = nullptr;
+  if (!current_context(&ctx)) {
+    set_error("bt_solve_noalloc: no current CUDA context on the handle's device");
+    return BT_ERR_CUDA;
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocAddr& slot = g_noalloc_addr[dev];
+    if (!slot.addr || slot.ctx != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "bt_solve_noalloc: cudaGetSymbolAddress");
-      g_noalloc_addr[dev] = static_cast<double*>(p);
+      slot.addr = static_cast<double*>(p);
+      slot.ctx = ctx;
     }
-    scratch = g_noalloc_addr[dev];
+    scratch = slot.addr;
   }
   SimtArgs<double> a;
   a.N = h->N; a.S = h->S; a.L = h->L; a.K = K; a.M = (int)h->M;

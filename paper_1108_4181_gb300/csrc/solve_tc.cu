@@ -290,12 +290,11 @@ __device__ __forceinline__ Bars carve(uint64_t* b) {
 
 __host__ __device__ constexpr int kBars(int na, int np) { return 2 * na + 2 * np + 8; }
 
-// csize: CTAs of the cluster that consume every A slice (each releases it).
 template <class C>
-__device__ __forceinline__ void init_bars(const Bars& b, int csize) {
+__device__ __forceinline__ void init_bars(const Bars& b) {
   for (int i = 0; i < C::NA; ++i) {
     mbar_init(&b.fullA[i], 1);
-    mbar_init(&b.emptyA[i], csize);
+    mbar_init(&b.emptyA[i], 1);
   }
   for (int i = 0; i < C::NP; ++i) {
     mbar_init(&b.fullP[i], 1);
@@ -310,33 +309,16 @@ __device__ __forceinline__ void init_bars(const Bars& b, int csize) {
   fence_mbar_init();
 }
 
-// Cluster sharing of the A slices: the `csize` CTAs of a cluster work on the
-// same segment (different column tiles) and need the same factor slices.  Each
-// loads rows [rank*M/csize, (rank+1)*M/csize) of every slice and multicasts
-// them to all; every CTA's MMA releases a slot in all of them, so a slot is
-// refilled only when the whole cluster has consumed it.
-struct Share {
-  int csize, crank;
-  uint16_t mask;
-};
-
 // Producer helper: one A slice (every plane) into the ring; waits for the slot.
 // fplane: tensor-map rows between factor planes.
 template <class C>
 __device__ __forceinline__ bool load_slice(uint8_t* sA, const Bars& b, uint32_t& ai, const CUtensorMap* tm, int x,
-                                           int y, int fplane, const Share& sh) {
+                                           int y, int fplane) {
   const uint32_t slot = ai % C::NA, use = ai / C::NA;
   if (use > 0 && !mbar_wait(&b.emptyA[slot], (use - 1) & 1)) return false;
-  mbar_arrive_expect_tx(&b.fullA[slot], C::SLOT);  // the whole slot, from every CTA of the cluster
-  const int rs = C::M / sh.csize;
+  mbar_arrive_expect_tx(&b.fullA[slot], C::SLOT);
 #pragma unroll
-  for (int p = 0; p < C::SP; ++p) {
-    uint8_t* dst = sA + slot * C::SLOT + p * C::SLICE + sh.crank * rs * 128;
-    if (sh.csize == 1)
-      tma_load_2d(dst, tm, x, y + p * fplane, &b.fullA[slot]);
-    else
-      tma_load_2d_mc(dst, tm, x, y + p * fplane + sh.crank * rs, &b.fullA[slot], sh.mask);
-  }
+  for (int p = 0; p < C::SP; ++p) tma_load_2d(sA + slot * C::SLOT + p * C::SLICE, tm, x, y + p * fplane, &b.fullA[slot]);
   ++ai;
   return true;
 }
@@ -399,16 +381,13 @@ __device__ __forceinline__ void mma_chunk(uint32_t dtmem, uint32_t fslot, uint32
 // the block's NCH slices from the ring; frees each slot when consumed.
 template <typename E, class C>
 __device__ __forceinline__ bool mma_block(uint8_t* sA, const Bars& b, uint32_t& ai, uint32_t dtmem, uint32_t btile,
-                                          bool& first, const Share& sh) {
+                                          bool& first) {
   for (int c = 0; c < C::NCH; ++c) {
     const uint32_t slot = ai % C::NA, use = ai / C::NA;
     if (!mbar_wait(&b.fullA[slot], use & 1)) return false;
     tc_fence_after();
     mma_chunk<E, C>(dtmem, smem_u32(sA + slot * C::SLOT), btile, c, first);
-    if (sh.csize == 1)
-      mma_commit(&b.emptyA[slot]);
-    else
-      mma_commit_mc(&b.emptyA[slot], sh.mask);
+    mma_commit(&b.emptyA[slot]);
     ++ai;
   }
   return true;
@@ -445,7 +424,7 @@ enum { FT_DINV = 0, FT_E = 1, FT_G = 2, FT_U = 3, FT_V = 4 };
 template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_sweep(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_r,
-               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, int csize, int shareD,
+               const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, int shareD,
                const int* done, int* status) {
   if (flag_set(done)) return;
   extern __shared__ uint8_t smraw[];
@@ -466,20 +445,13 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   const int fplane = 5 * N * C::M;  // tensor-map rows per factor plane
   const int pplane = N * Kp;        // tensor-map rows per panel plane
 
-  Share sh;
-  sh.csize = csize;
-  sh.crank = csize > 1 ? (int)cluster_rank() : 0;
-  sh.mask = (uint16_t)((1u << csize) - 1u);
-  if (threadIdx.x == 0) init_bars<C>(b, csize);
+  if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
     tmem_alloc(tslot, C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  if (csize > 1)
-    cluster_sync();  // every CTA's barriers exist before any multicast reaches them
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -498,10 +470,10 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         if (ok) ok = load_tile<C>(sP, b, pi, fwd ? &tm_r : &tm_w, i * Kp + n0, pplane);
         const int first_type = fwd ? FT_DINV : FT_G;
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane, sh);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (first_type * N + i) * C::M, fplane);
         if (fwd && t > 0 && !shareD)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane, sh);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_E * N + i) * C::M, fplane);
       }
       if (!ok) atomicExch(status, 1);
       // no copy may still be landing when the CTA exits
@@ -552,16 +524,16 @@ __global__ void __launch_bounds__(C::THREADS, 1)
           pslot = pi % C::NP;
           ok = mbar_wait(&b.fullP[pslot], (pi / C::NP) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::PT), first, sh);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sP + pslot * C::PT), first);
           if (ok && t > 0) {
             ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
             tc_fence_after();
-            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first, sh);
+            if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first);
           }
         } else if (ok) {
           ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
           tc_fence_after();
-          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first, sh);
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, yop, first);
         }
         if (ok) {
           mma_commit(&b.mdone[bsel]);
@@ -704,10 +676,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     if (!ok && leader) atomicExch(status, 3);
   }
   tc_fence_before();
-  if (csize > 1)
-    cluster_sync();  // no CTA leaves while another may still signal it
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -724,7 +693,7 @@ template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_correct(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
                  const __grid_constant__ CUtensorMap tm_d, const E* __restrict__ wp, float* __restrict__ dp, int N,
-                 int L, int S, int Kp, int rows_per_cta, int csize, const int* done, int* status) {
+                 int L, int S, int Kp, int rows_per_cta, const int* done, int* status) {
   if (flag_set(done)) return;
   using CF = Cfg<float, C::M, C::NT, 1, 1>;      // layout of one FP32 d tile
   constexpr int DT = CF::TILE;                    // bytes of one d tile
@@ -753,20 +722,13 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   const int fplane = 5 * N * C::M;
   const int pplane = N * Kp;
 
-  Share sh;
-  sh.csize = csize;
-  sh.crank = csize > 1 ? (int)cluster_rank() : 0;
-  sh.mask = (uint16_t)((1u << csize) - 1u);
-  if (threadIdx.x == 0) init_bars<C>(b, csize);
+  if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
     tmem_alloc(tslot, C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  if (csize > 1)
-    cluster_sync();  // every CTA's barriers exist before any multicast reaches them
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
@@ -788,10 +750,10 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         const int i = r0 + t;
         if constexpr (!C::SW) ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane);
         if (has_next)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane, sh);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane);
       }
       if (!ok) atomicExch(status, 4);
       mbar_wait(&b.extra[0], 0);
@@ -815,8 +777,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
         tc_fence_after();
         bool first = true;
-        if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first, sh);
-        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::PT), first, sh);
+        if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB), first);
+        if (ok && has_next) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sB + C::PT), first);
         if (ok) mma_commit(&b.mdone[bsel]);
       }
       if (!ok) atomicExch(status, 5);
@@ -946,10 +908,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     if (!ok && leader) atomicExch(status, 6);
   }
   tc_fence_before();
-  if (csize > 1)
-    cluster_sync();  // no CTA leaves while another may still signal it
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -999,8 +958,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   const IfJob jb = jobs[job0 + blockIdx.y];
   const int np = (jb.a[0] >= 0 ? 1 : 0) + (jb.a[1] >= 0 ? 1 : 0);
   const int pplane = N * Kp;
-  const Share sh{1, 0, 1};
-  if (threadIdx.x == 0) init_bars<C>(b, 1);
+  if (threadIdx.x == 0) init_bars<C>(b);
   if (warp == 1) {
     tmem_alloc(tslot, C::TMEM_COLS);
     tmem_relinquish();
@@ -1029,7 +987,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       for (int p = 0; p < 2 && ok; ++p) {
         if (jb.a[p] < 0) continue;
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_if, c * C::CE, jb.b[p] * C::M, nblk * C::M, sh);
+          ok = load_slice<C>(sA, b, ai, &tm_if, c * C::CE, jb.b[p] * C::M, nblk * C::M);
       }
       if (!ok) atomicExch(status, 7);
       mbar_wait(&b.extra[0], 0);
@@ -1044,7 +1002,7 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       tc_fence_after();
       uint32_t ai = 0;
       bool first = true;
-      for (int k = 0; k < np && ok; ++k) ok = mma_block<E, C>(sA, b, ai, tmem, smem_u32(sT + k * C::PT), first, sh);
+      for (int k = 0; k < np && ok; ++k) ok = mma_block<E, C>(sA, b, ai, tmem, smem_u32(sT + k * C::PT), first);
       if (ok) mma_commit(&b.mdone[0]);
       if (!ok) atomicExch(status, 8);
       mma_commit(&b.extra[1]);
@@ -1150,10 +1108,9 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   const int T = max(0, r1 - r0);
   const bool do_iface = blockIdx.z == 0;
   const int fplane = 5 * N * C::M;
-  const Share sh{1, 0, 1};
   auto acol = [](int q, int pl) { return (uint32_t)(2 * C::M + (2 * q + pl) * (C::M / 2)); };
   if (threadIdx.x == 0) {
-    init_bars<C>(b, 1);
+    init_bars<C>(b);
     mbar_init(&b.yrdy[0], 4 * C::EG);  // A operands stored by every epilogue warp
     fence_mbar_init();
   }
@@ -1177,10 +1134,10 @@ __global__ void __launch_bounds__(C::THREADS, 1)
         const int i = r0 + t;
         if (WR) ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
         for (int c = 0; c < C::NCH && ok; ++c)
-          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane, sh);
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_U * N + i) * C::M, fplane);
         if (has_next)
           for (int c = 0; c < C::NCH && ok; ++c)
-            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane, sh);
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FT_V * N + i) * C::M, fplane);
       }
       if (!ok) atomicExch(status, 4);
       for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
@@ -1774,23 +1731,9 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   static_assert(CS::SP == CC::SP, "one plane count per precision");
   const int M = CS::M, N = (int)h->N, L = (int)h->L, S = (int)h->S, Kp = (int)tb.Kp;
   CUtensorMap tm_fac_s, tm_fac_c, tm_r, tm_w, tm_wc, tm_d;
-  // cluster size along the column tiles: every A slice is loaded once per cluster
-  // (measured on the acoustic workload: sharing through clusters of 2-4 made the
-  // sweep slower -- the kernels are latency-bound, not L2-bound -- so every
-  // CTA loads its own slices; the multicast path stays for other shapes)
-  // BT_TC_CLUSTER (1, 2 or 4; default 1) overrides the cluster size when it
-  // divides the number of column tiles.
-  auto pick_cluster = [](int ntiles) {
-    static const int want = [] {
-      const char* e = std::getenv("BT_TC_CLUSTER");
-      const int v = e ? std::atoi(e) : 1;
-      return (v == 2 || v == 4) ? v : 1;
-    }();
-    return (ntiles % want == 0) ? want : 1;
-  };
-  const int cs_sweep = pick_cluster(Kp / CS::NT), cs_corr = pick_cluster(Kp / CC::NT);
-  BT_TRY(make_map(&tm_fac_s, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M / cs_sweep));
-  BT_TRY(make_map(&tm_fac_c, tb.fac, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CC::CE, M / cs_corr));
+  // every CTA loads its own factor slices
+  BT_TRY(make_map(&tm_fac_s, tb.fac, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CS::CE, M));
+  BT_TRY(make_map(&tm_fac_c, tb.fac, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * 5 * N * M, CC::CE, M));
   BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CS::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CS::CE, CS::NT));
   BT_TRY(make_map(&tm_wc, tb.w, ET<E>::dt, CC::eb, (uint64_t)M, (uint64_t)SP * N * Kp, CC::CE, CC::NT));
@@ -1803,23 +1746,11 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
     const size_t smem = sweep_smem<CS>();
     BT_CUDA(cudaFuncSetAttribute(k_tc_sweep<E, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(h, st, "tc_sweep");
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs_sweep;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(Kp / CS::NT, S);
-    cfg.blockDim = dim3(CS::THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
     // A_i = I lets the forward sweep reuse Dinv_i for the recurrence term (needs a
-    // ring that holds all of a block's slices plus one; no multicast sharing)
-    const int shareD = (h->stencil && cs_sweep == 1 && CS::NA > CS::NCH) ? 1 : 0;
-    BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_sweep<E, CS>, tm_fac_s, tm_r, tm_w, N, L, Kp, cs_sweep, shareD, done,
-                               status));
+    // ring that holds all of a block's slices plus one)
+    const int shareD = (h->stencil && CS::NA > CS::NCH) ? 1 : 0;
+    k_tc_sweep<E, CS><<<dim3(Kp / CS::NT, S), CS::THREADS, smem, st>>>(tm_fac_s, tm_r, tm_w, N, L, Kp, shareD, done,
+                                                                       status);
   }
   BT_CUDA(cudaGetLastError());
   // step 2.2: tensor cores for the split-BF16 precision, FP32 CUDA cores otherwise
@@ -1869,20 +1800,8 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       const size_t smem = correct_smem<CC>();
       BT_CUDA(cudaFuncSetAttribute(k_tc_correct<E, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       ProfScope ps(h, st, "tc_correct");
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = cs_corr;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(ntiles, S, chunks);
-      cfg.blockDim = dim3(CC::THREADS);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = st;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      BT_CUDA(cudaLaunchKernelEx(&cfg, k_tc_correct<E, CC>, tm_fac_c, tm_wc, tm_d, (const E*)w, tb.d, N, L, S, Kp,
-                                 L > 1 ? rpc : 0, cs_corr, done, status));
+      k_tc_correct<E, CC><<<dim3(ntiles, S, chunks), CC::THREADS, smem, st>>>(
+          tm_fac_c, tm_wc, tm_d, (const E*)w, tb.d, N, L, S, Kp, L > 1 ? rpc : 0, done, status);
     }
     BT_CUDA(cudaGetLastError());
     const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && !accumulate;

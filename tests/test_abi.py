@@ -85,3 +85,12 @@ def test_schur_argument_errors_without_gpu(lib):
         assert not h.value
     assert L.bt_schur_solve(None, ctypes.c_void_p(8), 1, ctypes.c_void_p(16), 1e-8, 10, None, None) == 1
     assert L.bt_schur_apply(None, ctypes.c_void_p(8), 1, ctypes.c_void_p(16), None) == 1
+
+
+def test_noalloc_scratch_size_matches_the_header():
+    from paper_1108_4181_gb300 import _lib
+
+    src = open(os.path.join(ROOT, "include", "bt.h")).read()
+    m = re.search(r"#define\s+BT_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*\*\s*(\d+)u\s*\*\s*(\d+)u\)", src)
+    assert m, "BT_NOALLOC_SCRATCH_BYTES not found in bt.h"
+    assert _lib.NOALLOC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))
