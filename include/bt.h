@@ -63,10 +63,12 @@ typedef struct {
   double tol;         /* target ||F - P X||_F / ||F||_F (0 = default 1e-10) */
   void* stream;       /* cudaStream_t */
   int32_t k_tile;     /* right-hand-side columns per CTA (0 = automatic) */
-  int32_t residual;   /* how F - P X is formed: 0 automatic (2 where it applies,
-                         else 1), 1 FP64 on the CUDA cores, 2 exactly on the
-                         tensor cores from BF16 digit slices (dense blocks,
-                         M = 64 or 128; BT_ERR_UNSUPPORTED otherwise) */
+  int32_t residual;   /* how F - P X is formed: 0 automatic (2 or 3 where they
+                         apply, else 1), 1 FP64 on the CUDA cores, 2 exactly on
+                         the tensor cores from BF16 digit slices (dense blocks,
+                         M = 64 or 128), 3 in FP32 double-word arithmetic (unit
+                         stencils: see bt_residual); BT_ERR_UNSUPPORTED where
+                         2 or 3 does not apply */
 } bt_opts;
 
 /* Result report of bt_solve_ex (filled only when a non-NULL pointer is given;
@@ -207,6 +209,17 @@ bt_status bt_solve_host(bt_handle h, const double* F, int64_t K, double* X, cons
  *      e_X the scales (2^e_A > the row's largest |A|, |B|, |C| entry, 2^e_X >
  *      the column's largest |X| entry).  Dense blocks with M = 64 or 128 only
  *      (BT_ERR_UNSUPPORTED otherwise).
+ *   3  in FP32 arithmetic on the CUDA cores, for unit stencils: A_j = B_j = I
+ *      and C_j = tridiag(-1, c, -1) with 2^-30 <= |c| <= 2^30, M a multiple
+ *      of 8 (BT_ERR_UNSUPPORTED otherwise).  Every FP64 value is split into
+ *      two FP32 terms (24 + 23 bits), the unit-coefficient terms are summed
+ *      exactly (TwoSum), c x enters through one FMA and the low-order terms
+ *      are summed in FP32; the result is an FP32 value per entry (stored in
+ *      R as FP64).  Error per entry at most 2^-23 |r| + 2^-42 S with
+ *      S = |f| + |x_{j-1}| + |x_{j+1}| + |x_{m-1}| + |x_{m+1}| + |c x|;
+ *      values below 2^-100 in magnitude count as zero.  If any value of F or
+ *      X is 2^77 or larger in magnitude (or not finite) the residual is
+ *      recomputed by method 1.
  * norm2 (host, may be NULL) receives ||r||_F^2.  Synchronises `stream`.
  */
 bt_status bt_residual(bt_handle h, const double* F, const double* X, int64_t K, double* R, int32_t method,

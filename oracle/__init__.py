@@ -38,6 +38,7 @@ from .blocktri import (  # noqa: F401
     dense_P,
     solve_dense,
     solve_block_thomas,
+    col_err,
     residual,
     rel_err,
     rel_res,

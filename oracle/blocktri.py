@@ -92,6 +92,15 @@ def rel_err(X, X_ref):
     return float(np.linalg.norm((X - X_ref).ravel()) / np.linalg.norm(X_ref.ravel()))
 
 
+def col_err(X, X_ref):
+    """max over right-hand-side columns n of max_i |X - X_ref|[i, n] / max_i |X_ref|[i, n],
+    i running over the N*M rows of the panel (each column measured on its own)."""
+    K = X.shape[-1]
+    D = np.abs(X - X_ref).reshape(-1, K).max(axis=0)
+    R = np.abs(X_ref).reshape(-1, K).max(axis=0)
+    return float(np.max(D / R))
+
+
 def rel_res(A, B, C, X, F):
     """||F - P X||_F / ||F||_F over the whole panel."""
     return float(np.linalg.norm(residual(A, B, C, X, F).ravel()) / np.linalg.norm(F.ravel()))

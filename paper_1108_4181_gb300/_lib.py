@@ -21,7 +21,7 @@ STATUS_NAMES = {
 # bytes of the fixed scratch array of bt_solve_noalloc (BT_NOALLOC_SCRATCH_BYTES in bt.h)
 NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 PREC = {"f64": 0, "tf32": 1, "bf16": 2, "f32": 3, "bf16x3": 4}
-RESIDUAL = {"auto": 0, "fp64": 1, "digits": 2}
+RESIDUAL = {"auto": 0, "fp64": 1, "digits": 2, "dw": 3}
 
 # Every symbol declared in include/bt.h, with (restype, argtypes).
 _vp = ctypes.c_void_p

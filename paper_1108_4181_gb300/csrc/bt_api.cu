@@ -391,7 +391,7 @@ bt_status bt_solve_ex(bt_handle h, const double* F, int64_t K, double* X, const 
     set_error("bt_solve_ex: unknown precision");
     return BT_ERR_ARG;
   }
-  if (o.residual < 0 || o.residual > 2) {
+  if (o.residual < 0 || o.residual > 3) {
     set_error("bt_solve_ex: unknown residual method");
     return BT_ERR_ARG;
   }
@@ -411,7 +411,7 @@ bt_status bt_residual(bt_handle h, const double* F, const double* X, int64_t K, 
     set_error("bt_residual: need a handle, device F, X and R, K >= 1");
     return BT_ERR_ARG;
   }
-  if (method < 0 || method > 2) {
+  if (method < 0 || method > 3) {
     set_error("bt_residual: unknown method");
     return BT_ERR_ARG;
   }

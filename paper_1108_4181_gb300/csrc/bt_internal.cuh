@@ -88,6 +88,10 @@ struct bt_handle_s {
   int64_t N = 0, M = 0, S = 0, L = 0;
   int depth = 0;
   int stencil = 0;  // A_j = B_j = I, C_j tridiagonal
+  // a stencil whose off-diagonals inside every C_j are exactly -1 and whose
+  // diagonal entries lie in [2^-30, 2^30] in magnitude: the refinement forms
+  // its residual in FP32 double-word arithmetic (refine.cu, k_resid_dw)
+  int stencil_unit = 0;
   int band[4] = {0, 0, 0, 0};  // nonzero diagonals c - r of A_j: [lo, hi]; of B_j: [lo, hi]
   int64_t band_n = 0;          // handles of bt_factor_band: rows n of the band matrix
   double* band_buf = nullptr;  // padded F and X panels of bt_solve_band
@@ -115,6 +119,9 @@ struct bt_handle_s {
   double* BK = nullptr;
   // Diagonals of C_j ([N][M][3]: sub, main, super) when the operator is a stencil.
   double* Cdiag = nullptr;
+  // The main diagonal of C_j as FP32 pairs [N][M][2]: the rounded value and the
+  // rounded remainder (|c - hi - lo| <= 2^-48 |c|).
+  float* Cdw = nullptr;
 
   // Reduced system of eq. red1, [S][M][M].
   double* At = nullptr;
@@ -309,6 +316,9 @@ int resident_grid(const void* fn, int threads, size_t smem);
 bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const double* const* F, const int64_t* K,
                       double* const* X, const bt_opts& o);
 bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
+
+// The FP32 double-word residual (refine.cu) applies: a unit stencil with M % 8 == 0.
+bool resid_dw_supported(const bt_handle_s* h);
 
 // Exact residual on the tensor cores (resid_digits.cu): whether it applies to
 // the handle for K columns; the digit slices of the operator (once) and the

@@ -234,17 +234,29 @@ __global__ void k_gather_blocks(const double* __restrict__ src, double* __restri
   }
 }
 
-// Cdiag[j][m] = (C_j[m][m-1], C_j[m][m], C_j[m][m+1]), zero outside the block.
-__global__ void k_tridiag(const double* __restrict__ C, double* __restrict__ Cd, int64_t N, int M) {
+// Cdiag[j][m] = (C_j[m][m-1], C_j[m][m], C_j[m][m+1]), zero outside the block;
+// Cdw[j][m] = C_j[m][m] as two FP32 terms (the rounded value, then the rounded
+// remainder).  *not_unit is set when an off-diagonal inside a block is not
+// exactly -1 or a diagonal entry lies outside [2^-30, 2^30] in magnitude.
+__global__ void k_tridiag(const double* __restrict__ C, double* __restrict__ Cd, float* __restrict__ Cdw,
+                          int64_t N, int M, int* not_unit) {
   const size_t n = (size_t)N * M;
+  bool bad = false;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const size_t j = e / M;
     const int m = (int)(e % M);
     const double* Cj = C + j * (size_t)M * M + (size_t)m * M;
-    Cd[3 * e + 0] = m > 0 ? Cj[m - 1] : 0.0;
-    Cd[3 * e + 1] = Cj[m];
-    Cd[3 * e + 2] = m + 1 < M ? Cj[m + 1] : 0.0;
+    const double lo = m > 0 ? Cj[m - 1] : 0.0, d = Cj[m], up = m + 1 < M ? Cj[m + 1] : 0.0;
+    Cd[3 * e + 0] = lo;
+    Cd[3 * e + 1] = d;
+    Cd[3 * e + 2] = up;
+    const float dh = __double2float_rn(d);
+    Cdw[2 * e] = dh;
+    Cdw[2 * e + 1] = __double2float_rn(d - (double)dh);
+    const double ad = fabs(d);
+    bad = bad || (m > 0 && lo != -1.0) || (m + 1 < M && up != -1.0) || !(ad >= 0x1p-30 && ad <= 0x1p30);
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(not_unit, 1);
 }
 
 __global__ void k_set_identity(double* I, int M) {
@@ -592,8 +604,8 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   const double** dtab = nullptr;
   int* dstatus = nullptr;
   BT_CUDA(cudaMallocAsync((void**)&dtab, std::max<size_t>(1, sc.tab.size()) * sizeof(double*), st));
-  BT_CUDA(cudaMallocAsync((void**)&dstatus, 2 * sizeof(int), st));
-  BT_CUDA(cudaMemsetAsync(dstatus, 0, 2 * sizeof(int), st));
+  BT_CUDA(cudaMallocAsync((void**)&dstatus, 3 * sizeof(int), st));
+  BT_CUDA(cudaMemsetAsync(dstatus, 0, 3 * sizeof(int), st));
   BT_CUDA(cudaMemcpyAsync(dtab, sc.tab.data(), sc.tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
 
   const int use_smem = M <= INV_SMEM_MAX ? 1 : 0;
@@ -629,9 +641,10 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_TRY(ar.alloc((void**)&h->AK, S * MM * sizeof(double)));
   BT_TRY(ar.alloc((void**)&h->BK, S * MM * sizeof(double)));
   BT_TRY(ar.alloc((void**)&h->Cdiag, (size_t)N * M * 3 * sizeof(double)));
+  BT_TRY(ar.alloc((void**)&h->Cdw, (size_t)N * M * 2 * sizeof(float)));
   k_gather_blocks<<<256, 256, 0, st>>>(h->A, h->AK, S, L, MM);
   k_gather_blocks<<<256, 256, 0, st>>>(h->B, h->BK, S, L, MM);
-  k_tridiag<<<256, 256, 0, st>>>(h->C, h->Cdiag, N, M);
+  k_tridiag<<<256, 256, 0, st>>>(h->C, h->Cdiag, h->Cdw, N, M, dstatus + 2);
   BT_CUDA(cudaGetLastError());
 
   // tree tables for the solve kernels
@@ -647,12 +660,13 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_CUDA(cudaMemcpyAsync(h->d_nodes, hn.data(), hn.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   BT_CUDA(cudaMemcpyAsync(h->d_mid_level, hml.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
 
-  int hstatus[2] = {0, 0};
-  BT_CUDA(cudaMemcpyAsync(hstatus, dstatus, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hstatus[3] = {0, 0, 0};
+  BT_CUDA(cudaMemcpyAsync(hstatus, dstatus, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
   BT_CUDA(cudaStreamSynchronize(st));
   BT_CUDA(cudaFreeAsync(dtab, st));
   BT_CUDA(cudaFreeAsync(dstatus, st));
   h->stencil = hstatus[1] ? 0 : 1;
+  h->stencil_unit = (h->stencil && !hstatus[2]) ? 1 : 0;
   if (hstatus[0]) {
     set_error("bt_factor: a pivot block of the block sweep or of the reduced system is singular or non-finite");
     return BT_ERR_SINGULAR;

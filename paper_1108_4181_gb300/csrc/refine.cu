@@ -32,6 +32,8 @@ struct IrState {
   int solves;               // refinement solves performed after the first
   int kstatus;              // non-zero: a tensor-core kernel gave up a bounded wait
   int cur;                  // slot of the next residual (advanced by every check)
+  int range;                // the FP32 double-word residual met a value it cannot represent
+  double rn2_fb;            // ||r||_F^2 of the FP64 residual that then replaced it
 };
 
 template <typename T>
@@ -56,6 +58,36 @@ __device__ __forceinline__ void block_add(double v, double* target) {
     if (l == 0 && v != 0.0) atomicAdd(target, v);
   }
 }
+
+// Sum of squares of FP32 values with a per-thread power-of-two scale: a value
+// v enters as (v 2^-e)^2; when one of magnitude 2^(e+32) or more arrives, e
+// is raised to its exponent and the sum rescaled, so the squares neither
+// overflow (|v| up to FP32's largest) nor lose the values near the largest
+// one; values below 2^(e-74) vanish, at most 2^-148 of the largest square
+// each.  total() is the sum in FP64.
+struct Ssq {
+  float acc = 0.f;
+  float f = 0x1p100f;   // 2^-e
+  float thr = 0x1p-68f; // 2^(e+32); +inf once e + 32 > 127
+  int e = -100;
+  __device__ __forceinline__ void add(float v) {
+    if (fabsf(v) >= thr) rescale(v);
+    const float w = v * f;
+    acc = fmaf(w, w, acc);
+  }
+  __device__ __forceinline__ void rescale(float v) {
+    const int ev = (int)((__float_as_uint(v) >> 23) & 0xffu) - 127;
+    const int en = min(ev, 126);
+    const int d = 2 * (e - en);  // <= -64
+    acc *= d >= -126 ? __int_as_float((127 + d) << 23) : 0.f;
+    e = en;
+    f = __int_as_float((127 - en) << 23);
+    thr = en + 32 <= 127 ? __int_as_float((127 + en + 32) << 23) : __int_as_float(0x7f800000);
+  }
+  __device__ __forceinline__ double total() const {
+    return (double)acc * __hiloint2double((1023 + 2 * e) << 20, 0);
+  }
+};
 
 // One residual entry of the stencil operator (A_j = B_j = I, tridiagonal C_j):
 // r = F_j + X_{j-1} + X_{j+1} - C_j X_j at (j, m, n), FP64.
@@ -104,12 +136,14 @@ __device__ __forceinline__ void put_planes(float* r, size_t idx, size_t plane, i
 }
 
 // Row-major residual panel (leading dimension K): grid-stride over entries.
+// With `gate` non-NULL the kernel runs only when *gate is set (the fallback of
+// the double-word residual) and adds its squared norm to st->rn2_fb.
 template <typename TR>
 __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict__ F, const double* __restrict__ X,
                                                       const double* __restrict__ Cd, TR* __restrict__ r,
                                                       int64_t N, int M, int64_t K, int first, int pass,
-                                                      IrState* st) {
-  if (st->done) return;
+                                                      IrState* st, const int* gate) {
+  if (st->done || (gate != nullptr && *(volatile const int*)gate == 0)) return;
   const size_t MK = (size_t)M * K, n = (size_t)N * MK;
   double acc = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -120,7 +154,7 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
     acc += v * v;
   }
   (void)pass;
-  block_add(acc, first ? &st->fn2 : &st->rn2[st->cur]);
+  block_add(acc, first ? &st->fn2 : gate ? &st->rn2_fb : &st->rn2[st->cur]);
   if (first) block_add(acc, &st->rn2[0]);
 }
 
@@ -135,16 +169,16 @@ template <typename TR>
 __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict__ F, const double* __restrict__ X,
                                                       const double* __restrict__ Cd, TR* __restrict__ r, int64_t N,
                                                       int M, int64_t K, int64_t Kp, int pass, int sp,
-                                                      IrState* st) {
+                                                      IrState* st, const int* gate) {
   constexpr int first = 0;
-  if (st->done) return;
+  if (st->done || (gate != nullptr && *(volatile const int*)gate == 0)) return;
   const size_t plane = (size_t)N * Kp * M;
   const size_t MK = (size_t)M * K;
   const int lane = threadIdx.x % 32;
   const int tn = (int)((Kp + 31) / 32), tm = M / 8;
   const int64_t nitem = N * tm * tn;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  float acc = 0.f;
+  Ssq acc;
   for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
     const int n = (int)(it % tn) * 32 + lane;
     const int m0 = (int)((it / tn) % tm) * 8;
@@ -180,7 +214,7 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
         if (m + 1 < M) w = fma(-cd[2], xs[q + 2], w);
       }
       v[q] = ncol ? f64_to_f32_rz(w) : 0.f;
-      acc = fmaf(v[q], v[q], acc);
+      acc.add(v[q]);
     }
     if (n < Kp) {
       TR* o = r + ((size_t)j * Kp + n) * M + m0;
@@ -213,8 +247,249 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
     }
   }
   (void)pass;
-  block_add((double)acc, first ? &st->fn2 : &st->rn2[st->cur]);
-  if (first) block_add((double)acc, &st->rn2[0]);
+  block_add(acc.total(), first ? &st->fn2 : gate ? &st->rn2_fb : &st->rn2[st->cur]);
+  if (first) block_add(acc.total(), &st->rn2[0]);
+}
+
+// ----------------------------------------------------------------------------
+// The stencil residual in FP32 double-word arithmetic (not in the paper).
+//
+// For A_j = B_j = I and C_j = tridiag(-1, c, -1) (the unit-stencil operators)
+//   r = f + x_{j-1} + x_{j+1} + x_{m-1} + x_{m+1} - c x
+// per entry, where the FP64 pipe of this GPU (1/64 of the FP32 rate) would
+// bound five FP64 operations per entry well below the HBM rate.  Every FP64
+// value v is split on the integer pipe into two FP32 terms (dw_split): h = v
+// truncated to 24 significant bits and l = the next 23 bits, so that
+// |v - h - l| < 2^-46 |v|; c comes split from the factorisation (Cdw).  The
+// five unit terms are summed exactly by Knuth's TwoSum on the h parts
+// (errors e_1..e_4 kept), the product c x enters through one FMA whose exact
+// intermediate absorbs the cancellation, r_hi = fma(-c_h, x_h, s), and every
+// low-order term -- l parts, TwoSum errors, c_h x_l, c_l x_h -- is summed in
+// FP32 into r = r_hi + lo.  Error per entry, against the exact residual:
+//   |r - r_exact| <= 2^-23 |r_exact| + 2^-42 S,   S = |f| + |P||x| summed
+// over the six terms (split truncation 2^-46 per term, dropped c_l x_l
+// 2^-47, the rounding of r_hi and of the low-order sum at most 66 2^-48 S in
+// all, the FP32 result 2^-23 |r|).  Values below 2^-100 in magnitude count as
+// zero (an absolute error below 2^-100 each).  A value of 2^77 or more (or
+// non-finite) in a warp's item sets *range; the FP64 kernel then recomputes
+// the whole residual (it runs gated on that flag) and k_ir_check takes its
+// norm.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// v = h + l + d with |d| < 2^-46 |v|; h, l carry v's sign.  amax collects the
+// largest |v| bit pattern (high word shifted left once, sign dropped) for the
+// caller's range check.
+__device__ __forceinline__ void dw_split(double v, float& h, float& l, uint32_t& amax) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t mag2 = hi << 1;
+  amax = max(amax, mag2);
+  // the FP64 exponent re-biased to FP32 (hi - 896 << 20 keeps the sign bit
+  // for biased exponents 897..1151), shifted into place with the top 23
+  // fraction bits; the shift drops the sign, which is put back
+  const uint32_t hs = __funnelshift_l(lo, hi - (896u << 20), 3) | (hi & 0x80000000u);
+  // eb = +-2^(E-23), one unit in the last place of h; the next 23 fraction
+  // bits of v below that unit are read off as (eb with those bits) - eb, exactly
+  const uint32_t eb = (hs & 0xff800000u) - (23u << 23);
+  const uint32_t tb = ((lo >> 6) & 0x007fffffu) | eb;
+  const bool tiny = mag2 < (923u << 21);  // |v| < 2^-100
+  h = tiny ? 0.f : __uint_as_float(hs);
+  l = tiny ? 0.f : __uint_as_float(tb) - __uint_as_float(eb);
+}
+
+// One entry: f + u + d + l + r - c x from double-word terms.
+__device__ __forceinline__ float dw_entry(float fh, float fl, float uh, float ul, float dh, float dl, float lh,
+                                          float ll, float rh, float rl, float xh, float xl, float ch, float cl) {
+  float s1, e1, s2, e2, s3, e3, s4, e4;
+  two_sum(uh, dh, s1, e1);
+  two_sum(lh, rh, s2, e2);
+  two_sum(s1, s2, s3, e3);
+  two_sum(s3, fh, s4, e4);
+  const float rhi = fmaf(-ch, xh, s4);  // exact intermediate, one rounding
+  float lo = ((e1 + e2) + (e3 + e4)) + ((ul + dl) + (ll + rl)) + fl;
+  lo = fmaf(-ch, xl, lo);
+  lo = fmaf(-cl, xh, lo);
+  return rhi + lo;
+}
+
+__device__ __forceinline__ uint32_t bf2_u32(__nv_bfloat162 b) { return *reinterpret_cast<const uint32_t*>(&b); }
+
+// Rows m0 - 1 .. m0 + MC of one column of one block row of X (the item's rows
+// and their halo in the block's row direction), split into double words.
+template <int MC>
+struct Slot {
+  float h[MC + 2], l[MC + 2];
+};
+
+// One warp per item (JC block rows j, MC rows m, 32 columns n): lane n marches
+// down the item's block rows keeping X_{j-1}, X_j and X_{j+1} (rows m0 - 1 ..
+// m0 + MC each) split into double-word registers, so every X value is loaded
+// and split once per item and its halo; the march is unrolled by three so the
+// window rotates by renaming.  The next block row's X_{j+2} and F_{j+1} are
+// loaded at the start of a step and split at its end.  Measured on the
+// acoustic workload (N = 4096, M = 128, K = 512): 1.32 ms per residual, 0.60
+// of the HBM copy rate, bound by load latency at 16 warps per SM (128
+// registers; 80 registers spill and run 2.5x slower, rows fed through a TMA
+// ring of small boxes or an L2 bulk prefetch ran slower).  Output: TRANS -- the
+// block-transposed panel of the tensor-core solve (element (m, n) of block
+// row j at (j ldr + n) M + m, ldr = Kp, columns K..Kp-1 written as zero; with
+// sp = 2 the rounding remainder in plane 1); otherwise the row-major panel
+// (ld = K) in FP32 or FP64.
+template <typename TR, bool TRANS>
+struct DwResid {
+  static constexpr int MC = 4, JC = 48;
+  const double* __restrict__ F;
+  const double* __restrict__ X;
+  const float2* __restrict__ Cdw;
+  TR* __restrict__ r;
+  int N, K, ldr, M, sp;
+  size_t plane;
+  // per item
+  int n, j1, m0;
+  bool colok, okl, okr;
+  uint32_t amax = 0;
+  Ssq acc;
+
+  __device__ __forceinline__ void load_x(int j, double (&t)[MC + 2]) const {
+    const bool jok = j >= 0 && j < N;
+    const double* p = X + ((size_t)j * M + m0 - 1) * K + n;
+    t[0] = (jok && okl) ? __ldg(p) : 0.0;
+#pragma unroll
+    for (int q = 1; q <= MC; ++q) t[q] = (jok && colok) ? __ldg(p + (size_t)q * K) : 0.0;
+    t[MC + 1] = (jok && okr) ? __ldg(p + (size_t)(MC + 1) * K) : 0.0;
+  }
+  __device__ __forceinline__ void load_f(int j, double (&t)[MC]) const {
+    const bool jok = j >= 0 && j < N && colok;
+    const double* p = F + ((size_t)j * M + m0) * K + n;
+#pragma unroll
+    for (int q = 0; q < MC; ++q) t[q] = jok ? __ldg(p + (size_t)q * K) : 0.0;
+  }
+  __device__ __forceinline__ void split_x(const double (&t)[MC + 2], Slot<MC>& o) {
+#pragma unroll
+    for (int q = 0; q < MC + 2; ++q) dw_split(t[q], o.h[q], o.l[q], amax);
+  }
+  __device__ __forceinline__ void split_f(const double (&t)[MC], float (&fh)[MC], float (&fl)[MC]) {
+#pragma unroll
+    for (int q = 0; q < MC; ++q) dw_split(t[q], fh[q], fl[q], amax);
+  }
+
+  // Row j from U = X_{j-1}, C = X_j, D = X_{j+1}; then U <- X_{j+2}, f <- F_{j+1}.
+  __device__ __forceinline__ void step(Slot<MC>& U, const Slot<MC>& C, const Slot<MC>& D, float (&fh)[MC],
+                                       float (&fl)[MC], int j) {
+    const bool more = j + 1 < j1;
+    double px[MC + 2], pf[MC];
+    load_x(more ? j + 2 : -1, px);
+    load_f(more ? j + 1 : -1, pf);
+    const float4* cp = reinterpret_cast<const float4*>(Cdw + (size_t)j * M + m0);
+    const float4 c01 = __ldg(cp), c23 = __ldg(cp + 1);
+    const float ch[MC] = {c01.x, c01.z, c23.x, c23.z}, cl[MC] = {c01.y, c01.w, c23.y, c23.w};
+    float v[MC];
+#pragma unroll
+    for (int q = 0; q < MC; ++q) {
+      v[q] = dw_entry(fh[q], fl[q], U.h[q + 1], U.l[q + 1], D.h[q + 1], D.l[q + 1], C.h[q], C.l[q], C.h[q + 2],
+                      C.l[q + 2], C.h[q + 1], C.l[q + 1], ch[q], cl[q]);
+      acc.add(v[q]);
+    }
+    store(v, j);
+    split_x(px, U);
+    split_f(pf, fh, fl);
+  }
+
+  __device__ __forceinline__ void store(const float (&v)[MC], int j) const {
+    if constexpr (TRANS) {
+      if (n < ldr) {
+        TR* o = r + ((size_t)j * ldr + n) * M + m0;
+        if constexpr (sizeof(TR) == 2) {
+          const __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]), b1 = __floats2bfloat162_rn(v[2], v[3]);
+          *reinterpret_cast<uint2*>(o) = make_uint2(bf2_u32(b0), bf2_u32(b1));
+          if (sp == 2) {
+            const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+            const __nv_bfloat162 c0 = __floats2bfloat162_rn(v[0] - f0.x, v[1] - f0.y);
+            const __nv_bfloat162 c1 = __floats2bfloat162_rn(v[2] - f1.x, v[3] - f1.y);
+            *reinterpret_cast<uint2*>(o + plane) = make_uint2(bf2_u32(c0), bf2_u32(c1));
+          }
+        } else {
+          float hi[MC], lo[MC];
+#pragma unroll
+          for (int q = 0; q < MC; ++q) {
+            hi[q] = sp == 2 ? __uint_as_float(__float_as_uint(v[q]) & 0xFFFFE000u) : v[q];
+            lo[q] = v[q] - hi[q];
+          }
+          *reinterpret_cast<float4*>(o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          if (sp == 2) *reinterpret_cast<float4*>(o + plane) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
+    } else if (colok) {
+      TR* o = r + ((size_t)j * M + m0) * K + n;
+#pragma unroll
+      for (int q = 0; q < MC; ++q) {
+        if constexpr (sizeof(TR) == 8)
+          o[(size_t)q * K] = f32_to_f64(v[q]);
+        else
+          o[(size_t)q * K] = v[q];
+      }
+    }
+  }
+};
+
+template <typename TR, bool TRANS>
+__global__ void __launch_bounds__(256, 2) k_resid_dw(const double* __restrict__ F, const double* __restrict__ X,
+                                                    const float2* __restrict__ Cdw, TR* __restrict__ r, int64_t N,
+                                                    int M, int64_t K, int64_t ldr, int sp, IrState* st) {
+  using W = DwResid<TR, TRANS>;
+  constexpr int MC = W::MC, JC = W::JC;
+  if (st->done) return;
+  W w;
+  w.F = F;
+  w.X = X;
+  w.Cdw = Cdw;
+  w.r = r;
+  w.N = (int)N;
+  w.K = (int)K;
+  w.ldr = (int)ldr;
+  w.M = M;
+  w.sp = sp;
+  w.plane = (size_t)N * ldr * M;
+  const int lane = threadIdx.x % 32;
+  const int tn = (int)(((TRANS ? ldr : K) + 31) / 32), tm = M / MC;
+  const int64_t tj = (N + JC - 1) / JC;
+  const int64_t nitem = tj * tm * tn;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
+    w.n = (int)(it % tn) * 32 + lane;
+    w.m0 = (int)((it / tn) % tm) * MC;
+    const int j0 = (int)(it / ((int64_t)tn * tm)) * JC;
+    w.j1 = (int)min((int64_t)j0 + JC, N);
+    w.colok = w.n < K;
+    w.okl = w.colok && w.m0 > 0;
+    w.okr = w.colok && w.m0 + MC < M;
+    Slot<MC> A, B, C;
+    float fh[MC], fl[MC];
+    {
+      double t[MC + 2], tf[MC];
+      w.load_x(j0 - 1, t);
+      w.split_x(t, A);
+      w.load_x(j0, t);
+      w.split_x(t, B);
+      w.load_x(j0 + 1, t);
+      w.split_x(t, C);
+      w.load_f(j0, tf);
+      w.split_f(tf, fh, fl);
+    }
+    // rows (j-1, j, j+1) in (A, B, C), (B, C, A), (C, A, B) in turn
+    for (int j = j0; j < w.j1; j += 3) {
+      w.step(A, B, C, fh, fl, j);
+      if (j + 1 < w.j1) w.step(B, C, A, fh, fl, j + 1);
+      if (j + 2 < w.j1) w.step(C, A, B, fh, fl, j + 2);
+    }
+  }
+  // |v| >= 2^77 (or non-finite) anywhere: the FP64 kernel recomputes
+  if (__any_sync(0xffffffffu, w.amax >= (1100u << 21)) && lane == 0) atomicExch(&st->range, 1);
+  block_add(w.acc.total(), &st->rn2[st->cur]);
 }
 
 // The first residual (X = 0): F rounded into the block-transposed panel, one
@@ -230,7 +505,7 @@ __global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F,
   const int tn = (int)((Kp + 31) / 32), tm = M / 16;
   const int64_t nitem = N * tm * tn;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  float acc = 0.f;
+  Ssq acc;
   for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
     const int n = (int)(it % tn) * 32 + lane;
     const int m0 = (int)((it / tn) % tm) * 16;
@@ -241,7 +516,7 @@ __global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F,
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       v[q] = n < K ? f64_to_f32_rz(fj[(size_t)q * K]) : 0.f;
-      acc = fmaf(v[q], v[q], acc);
+      acc.add(v[q]);
     }
     TR* o = r + ((size_t)j * Kp + n) * M + m0;
     if constexpr (sizeof(TR) == 2) {
@@ -274,8 +549,8 @@ __global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F,
       }
     }
   }
-  block_add((double)acc, &st->fn2);
-  block_add((double)acc, &st->rn2[0]);
+  block_add(acc.total(), &st->fn2);
+  block_add(acc.total(), &st->rn2[0]);
 }
 
 // r_j = F_j + A_j X_{j-1} + B_j X_{j+1} - C_j X_j with dense blocks, FP64.
@@ -345,6 +620,11 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
 // done and fewer than max_it refinement solves have run.
 __global__ void k_ir_check(IrState* st, double tol2, int max_it, cudaGraphConditionalHandle loop) {
   const int pass = st->cur;
+  if (st->range) {  // the FP64 residual replaced the double-word one
+    st->rn2[pass] = st->rn2_fb;
+    st->rn2_fb = 0.0;
+    st->range = 0;
+  }
   if (!st->done) {
     st->last = pass;
     if (pass > 0) {
@@ -392,14 +672,51 @@ bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
 
 // Residual into the solve's panel: row-major (ld = K) for the SIMT solve,
 // block-transposed (ld = Kp) for the tensor-core solve.
+// rmode: 1 FP64 on the CUDA cores, 2 the tensor-core digit residual (dense
+// blocks), 3 FP32 double-word arithmetic (unit stencils).
 template <typename TR>
 bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
-                          int sp, int first, int pass, IrState* st, bool digits, cudaStream_t s) {
+                          int sp, int first, int pass, IrState* st, int rmode, cudaStream_t s) {
   const int M = (int)h->M;
+  const bool digits = rmode == 2;
   if (digits && !first)  // dense blocks: the exact residual on the tensor cores
     return launch_resid_digits(h, F, X, K, trans ? 0 : 1, sizeof(TR) == 4, r, sp, &st->done, st->rn2, &st->cur,
                                &st->kstatus, s);
   // the first pass (X = 0) only rounds F into the panel: timed under its own name
+  if (!first && rmode == 3) {
+    // FP32 double-word residual; the FP64 kernel behind it runs only when a
+    // value was out of its range (gated on st->range)
+    const float2* cdw = reinterpret_cast<const float2*>(h->Cdw);
+    {
+      ProfScope ps(h, s, "resid_dw");
+      const int64_t rows = (h->N + DwResid<TR, true>::JC - 1) / DwResid<TR, true>::JC;
+      if (trans) {
+        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<TR, true>), 256, 0);
+        const int64_t items = rows * (M / 4) * ((Kp + 31) / 32);
+        const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
+        k_resid_dw<TR, true><<<blocks, 256, 0, s>>>(F, X, cdw, r, h->N, M, K, Kp, sp, st);
+      } else {
+        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<TR, false>), 256, 0);
+        const int64_t items = rows * (M / 4) * ((K + 31) / 32);
+        const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
+        k_resid_dw<TR, false><<<blocks, 256, 0, s>>>(F, X, cdw, r, h->N, M, K, K, sp, st);
+      }
+    }
+    ProfScope ps(h, s, "resid_fb");
+    if (trans) {
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
+      const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
+      const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
+      k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, &st->range);
+    } else {
+      const size_t n = (size_t)h->N * M * K;
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
+      const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)grid);
+      k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st, &st->range);
+    }
+    BT_CUDA(cudaGetLastError());
+    return BT_OK;
+  }
   ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
     if (trans) {  // the tensor-core panels: M is 64 or 128
@@ -412,13 +729,13 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
         static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
         const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
         const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
-        k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st);
+        k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, nullptr);
       }
     } else {
       const size_t n = (size_t)h->N * M * K;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
       const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)grid);
-      k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st);
+      k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st, nullptr);
     }
   } else {
     constexpr int CW = 4;
@@ -444,6 +761,8 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
 }
 
 }  // namespace
+
+bool resid_dw_supported(const bt_handle_s* h) { return h->stencil && h->stencil_unit && h->M % 8 == 0; }
 
 bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st) {
   LowFactors& f = h->f32;
@@ -487,14 +806,22 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     Kp = (K + nt - 1) / nt * nt;
     eb = prec == BT_PREC_TF32 ? 4 : 2;
   }
-  // residual: 0 automatic (the tensor-core digit residual where it applies),
-  // 1 FP64 on the CUDA cores, 2 the tensor-core digit residual
+  // residual: 0 automatic (the tensor-core digit residual for dense blocks,
+  // the FP32 double-word residual for unit stencils, where they apply), 1 FP64
+  // on the CUDA cores, 2 the tensor-core digit residual, 3 double-word
   const bool dig_ok = resid_digits_supported(h, K);
+  const bool dw_ok = resid_dw_supported(h);
   if (o.residual == 2 && !dig_ok) {
     set_error("bt_solve_ex: the tensor-core residual needs dense blocks with M = 64 or M = 128");
     return BT_ERR_UNSUPPORTED;
   }
+  if (o.residual == 3 && !dw_ok) {
+    set_error("bt_solve_ex: the double-word residual needs A_j = B_j = I, C_j = tridiag(-1, c, -1) with "
+              "2^-30 <= |c| <= 2^30, and M a multiple of 8");
+    return BT_ERR_UNSUPPORTED;
+  }
   const bool digits = o.residual == 2 || (o.residual == 0 && dig_ok);
+  const int rmode = digits ? 2 : (o.residual == 3 || (o.residual == 0 && dw_ok)) ? 3 : 1;
     const void* before[4] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x};
   const size_t panel = (size_t)sp * h->N * M * Kp * eb;
   // series terms [depth][S] and, for the tensor-core step 2.2, one node sum per tree node
@@ -520,8 +847,8 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   auto residual = [&](cudaStream_t q, int first) -> bt_status {
     if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
       return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
-                                            first, 0, st, digits, q);
-    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, 0, st, digits,
+                                            first, 0, st, rmode, q);
+    return launch_residual<float>(h, F, X, reinterpret_cast<float*>(h->lp_r), K, Kp, tcore, sp, first, 0, st, rmode,
                                   q);
   };
   auto inner = [&](cudaStream_t q, int accumulate) -> bt_status {
@@ -628,7 +955,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       ++i;
     }
   }
-  const int rkey = digits ? 1 : 0;
+  const int rkey = rmode;
   bt_handle_s::RefineGraph* e = nullptr;
   for (auto& g : cache)
     if (g.F == F && g.X == X && g.K == K && g.precision == prec && g.tol == tol && g.max_it == max_it &&
@@ -708,18 +1035,33 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
     set_error("bt_residual: the tensor-core residual needs dense blocks with M = 64 or M = 128");
     return BT_ERR_UNSUPPORTED;
   }
+  const int M = (int)h->M;
+  if (method == 3 && !resid_dw_supported(h)) {
+    set_error("bt_residual: the double-word residual needs A_j = B_j = I, C_j = tridiag(-1, c, -1) with "
+              "2^-30 <= |c| <= 2^30, and M a multiple of 8");
+    return BT_ERR_UNSUPPORTED;
+  }
   if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
   IrState* st = reinterpret_cast<IrState*>(h->ir_state);
   BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), s));
   if (method == 2) {
     BT_TRY(resid_digits_prepare(h, K, s));
     BT_TRY(launch_resid_digits(h, F, X, K, 2, false, R, 1, &st->done, st->rn2, nullptr, &st->kstatus, s));
+  } else if (method == 3) {
+    const int64_t items = ((h->N + DwResid<double, false>::JC - 1) / DwResid<double, false>::JC) * (M / 4) *
+                          ((K + 31) / 32);
+    static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<double, false>), 256, 0);
+    k_resid_dw<double, false><<<(int)std::min<int64_t>((items + 7) / 8, grid), 256, 0, s>>>(
+        F, X, reinterpret_cast<const float2*>(h->Cdw), R, h->N, M, K, K, 1, st);
+    const size_t n = (size_t)h->N * M * K;
+    k_resid_stencil<double><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+        F, X, h->Cdiag, R, h->N, M, K, 0, 0, st, &st->range);
+    BT_CUDA(cudaGetLastError());
   } else {
-    const int M = (int)h->M;
     if (h->stencil) {
       const size_t n = (size_t)h->N * M * K;
       k_resid_stencil<double><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(
-          F, X, h->Cdiag, R, h->N, M, K, 0, 0, st);
+          F, X, h->Cdiag, R, h->N, M, K, 0, 0, st, nullptr);
     } else {
       constexpr int CW = 4;
       const int CG = std::max(1, std::min(1024 / M, std::max(1, 128 / M)));
@@ -740,7 +1082,7 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
     set_error("bt_residual: a tensor-core kernel gave up a bounded wait (code " + std::to_string(hs.kstatus) + ")");
     return BT_ERR_TIMEOUT;
   }
-  if (norm2) *norm2 = hs.rn2[0];
+  if (norm2) *norm2 = hs.range ? hs.rn2_fb : hs.rn2[0];
   return BT_OK;
 }
 

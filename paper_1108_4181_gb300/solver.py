@@ -126,7 +126,9 @@ class Factorization:
         """(R, ||R||_F^2) with R = F - P X ([N, M, K] float64, on the device).
 
         method: "fp64" (CUDA cores), "digits" (exact digit products on the
-        tensor cores; dense blocks, M = 64 or 128), "auto"."""
+        tensor cores; dense blocks, M = 64 or 128), "dw" (FP32 double-word
+        arithmetic; A_j = B_j = I, C_j = tridiag(-1, c, -1), M % 8 == 0),
+        "auto"."""
         F = _as_device_f64(self._panel(F, "F"), self.device, "F")
         X = _as_device_f64(self._panel(X, "X"), self.device, "X")
         if F.shape != X.shape:

@@ -133,6 +133,16 @@ def test_residual_and_error_norms():
     assert np.abs(r).max() < 1e-13
     assert oracle.rel_err(2 * X, X) == pytest.approx(1.0)
     assert oracle.rel_res(A, B, C, np.zeros_like(F), F) == pytest.approx(1.0)
+    # per-column error: each column measured against its own largest entry
+    Xr = np.zeros((2, 2, 3))
+    Xr[:, :, 0] = [[1.0, -4.0], [2.0, 0.5]]   # max |.| 4
+    Xr[:, :, 1] = [[1e-6, 0.0], [0.0, 0.0]]   # max |.| 1e-6
+    Xr[:, :, 2] = [[3.0, 3.0], [3.0, 3.0]]
+    Xe = Xr.copy()
+    Xe[0, 1, 0] += 0.4      # 0.4 / 4 = 0.1 in column 0
+    Xe[1, 1, 1] += 2e-7     # 2e-7 / 1e-6 = 0.2 in column 1 (tiny against the panel's norm)
+    assert oracle.col_err(Xe, Xr) == pytest.approx(0.2)
+    assert oracle.rel_err(Xe, Xr) < 0.1
 
 
 # --------------------------------------------------------------------------
