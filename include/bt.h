@@ -248,7 +248,15 @@ bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_
  *   the handles must outlive it.  Synchronous; BT_ERR_ARG on invalid input.
  * bt_batch_run -- enqueues one batched solve on `stream` (one graph launch).
  * bt_batch_status -- waits for the plan's work and returns BT_OK, or
- *   BT_ERR_TIMEOUT if a grid-barrier wait of the last run gave up (20 s).
+ *   BT_ERR_TIMEOUT if a grid-barrier wait of the last run gave up (20 s by
+ *   default; see bt_batch_debug).  The device stays usable: the plan can be
+ *   run again.
+ * bt_batch_debug -- diagnostics for testing the failure path: limit_s sets
+ *   the grid-barrier wait limit of later runs (0 = the 20 s default, at most
+ *   60 s); skip_stage >= 0 plants a failure -- CTA 0 of the persistent launch
+ *   leaves the kernel instead of arriving at the barrier after that stage, so
+ *   the other CTAs' waits run out and the run reports BT_ERR_TIMEOUT; -1
+ *   removes it.  Takes effect in graph replays too.  Synchronises the device.
  * bt_batch_query -- out[0] work items, out[1] stages, out[2] CTAs of the
  *   persistent launch, out[3] threads per CTA, out[4] columns per item,
  *   out[5] 1 when runs replay a CUDA graph.
@@ -260,6 +268,7 @@ bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F,
 bt_status bt_batch_run(bt_batch b, void* stream);
 bt_status bt_batch_status(bt_batch b);
 bt_status bt_batch_query(bt_batch b, int64_t out[6]);
+bt_status bt_batch_debug(bt_batch b, double limit_s, int32_t skip_stage);
 void bt_batch_destroy(bt_batch b);
 bt_status bt_solve_batched(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,
                            double* const* X, const bt_opts* opts);

@@ -94,8 +94,9 @@ def rel_err(X, X_ref):
 
 def col_err(X, X_ref):
     """max over right-hand-side columns n of max_i |X - X_ref|[i, n] / max_i |X_ref|[i, n],
-    i running over the N*M rows of the panel (each column measured on its own)."""
-    K = X.shape[-1]
+    i running over the N*M rows of the panel (each column measured on its own); a
+    1-D vector is one column."""
+    K = X.shape[-1] if X.ndim > 1 else 1
     D = np.abs(X - X_ref).reshape(-1, K).max(axis=0)
     R = np.abs(X_ref).reshape(-1, K).max(axis=0)
     return float(np.max(D / R))

@@ -583,6 +583,14 @@ bt_status bt_batch_status(bt_batch b) {
   return BT_OK;
 }
 
+bt_status bt_batch_debug(bt_batch b, double limit_s, int32_t skip_stage) {
+  if (!b || !(limit_s >= 0.0) || limit_s > 60.0 || skip_stage < -1) {
+    set_error("bt_batch_debug: need a plan, 0 <= limit_s <= 60 and skip_stage >= -1");
+    return BT_ERR_ARG;
+  }
+  return batch_set_debug(b, (unsigned long long)(limit_s * 1e9), skip_stage);
+}
+
 bt_status bt_batch_query(bt_batch b, int64_t out[6]) {
   if (!b || !out) {
     set_error("bt_batch_query: NULL argument");

@@ -316,6 +316,9 @@ int resident_grid(const void* fn, int threads, size_t smem);
 bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const double* const* F, const int64_t* K,
                       double* const* X, const bt_opts& o);
 bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
+// Sets the plan's grid-barrier wait limit (0: the default) and its planted
+// failure (a stage index, or -1); synchronous.
+bt_status batch_set_debug(bt_batch_s* b, unsigned long long limit_ns, int skip_stage);
 
 // The FP32 double-word residual (refine.cu) applies: a unit stencil with M % 8 == 0.
 bool resid_dw_supported(const bt_handle_s* h);

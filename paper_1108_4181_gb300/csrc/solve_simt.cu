@@ -26,6 +26,7 @@
 // Every kernel returns at once when the refinement flag `done` is set.
 
 #include <algorithm>
+#include <cstddef>
 #include <mutex>
 #include <string>
 
@@ -548,6 +549,18 @@ enum : int32_t { kStSweep = 0, kStIface = 1, kStDich = 2, kStCorrect = 3 };
 
 constexpr unsigned long long kBarrierLimitNs = 20ull * 1000000000ull;
 
+// Control words of a plan (d_ctl, 64 bytes): [0] arrivals, [1] generation,
+// [2] status -- cleared before every launch -- then, kept across launches,
+// the barrier wait limit in ns at byte 16 (0: kBarrierLimitNs) and at byte 24
+// a planted failure for tests: CTA 0 leaves the kernel instead of arriving at
+// the barrier after that stage (-1: none).
+struct BatchCtl {
+  unsigned bar[2];
+  int status;
+  int pad;
+  unsigned long long limit_ns;
+  int skip_stage;
+};
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -557,7 +570,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // Sense-free grid barrier on two counters: bar[0] counts arrivals, bar[1] is
 // the generation.  Returns false (after recording the failure) when the wait
 // passes its time limit or another CTA has already failed.
-__device__ bool grid_barrier(unsigned* bar, int* status) {
+__device__ bool grid_barrier(unsigned* bar, int* status, unsigned long long limit_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -572,7 +585,7 @@ __device__ bool grid_barrier(unsigned* bar, int* status) {
     } else {
       const unsigned long long t0 = gtimer();
       while (*gen == g) {
-        if (*(volatile int*)status != 0 || gtimer() - t0 > kBarrierLimitNs) {
+        if (*(volatile int*)status != 0 || gtimer() - t0 > limit_ns) {
           atomicCAS(status, 0, (int)BT_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -592,6 +605,9 @@ __global__ void k_batched_f64(const BatchSet* __restrict__ sets, const BatchItem
                               unsigned* bar, int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sm = reinterpret_cast<double*>(smraw);
+  const BatchCtl* ctl = reinterpret_cast<const BatchCtl*>(bar);
+  const unsigned long long lim = ctl->limit_ns ? ctl->limit_ns : kBarrierLimitNs;
+  const int skip = ctl->skip_stage;
   for (int st = 0; st < n_stages; ++st) {
     const int kind = stage_kind[st];
     for (int i = stage_off[st] + (int)blockIdx.x; i < stage_off[st + 1]; i += (int)gridDim.x) {
@@ -607,7 +623,10 @@ __global__ void k_batched_f64(const BatchSet* __restrict__ sets, const BatchItem
           break;
       }
     }
-    if (st + 1 < n_stages && !grid_barrier(bar, status)) return;
+    if (st + 1 < n_stages) {
+      if (st == skip && blockIdx.x == 0) return;  // planted failure: this CTA never arrives
+      if (!grid_barrier(bar, status, lim)) return;
+    }
   }
 }
 
@@ -721,6 +740,9 @@ bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const doubl
   if (!kind.empty())
     BT_CUDA(cudaMemcpy(b->d_stage_kind, kind.data(), kind.size() * sizeof(int), cudaMemcpyHostToDevice));
   BT_CUDA(cudaMemset(b->d_ctl, 0, 64));
+  const int no_skip = -1;
+  BT_CUDA(cudaMemcpy(reinterpret_cast<char*>(b->d_ctl) + offsetof(BatchCtl, skip_stage), &no_skip, sizeof(int),
+                     cudaMemcpyHostToDevice));
 
   const void* fn = b->CW == 4 ? batched_kernel<4>() : b->CW == 2 ? batched_kernel<2>() : batched_kernel<1>();
   b->kernel = fn;
@@ -737,6 +759,16 @@ bt_status batch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const doubl
 }
 
 // Enqueues one batched solve on `st` (also used while capturing the graph).
+bt_status batch_set_debug(bt_batch_s* b, unsigned long long limit_ns, int skip_stage) {
+  BatchCtl c;
+  BT_CUDA(cudaDeviceSynchronize());
+  BT_CUDA(cudaMemcpy(&c, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
+  c.limit_ns = limit_ns;
+  c.skip_stage = skip_stage;
+  BT_CUDA(cudaMemcpy(b->d_ctl, &c, sizeof(BatchCtl), cudaMemcpyHostToDevice));
+  return BT_OK;
+}
+
 bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st) {
   unsigned* bar = reinterpret_cast<unsigned*>(b->d_ctl);
   int* status = reinterpret_cast<int*>(b->d_ctl) + 2;

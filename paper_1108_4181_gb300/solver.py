@@ -311,6 +311,12 @@ class BatchPlan:
         """Waits for the plan's work; raises if a bounded grid-barrier wait gave up."""
         _lib.check(_lib.load().bt_batch_status(self._b), "bt_batch_status")
 
+    def debug(self, limit_s: float = 0.0, skip_stage: int = -1):
+        """Diagnostics (bt_batch_debug): the grid-barrier wait limit of later
+        runs (0 = default) and a planted failure (CTA 0 leaves instead of
+        arriving at the barrier after stage `skip_stage`; -1 = none)."""
+        _lib.check(_lib.load().bt_batch_debug(self._b, float(limit_s), int(skip_stage)), "bt_batch_debug")
+
     def close(self):
         if self._b is not None and self._b.value:
             _lib.load().bt_batch_destroy(self._b)

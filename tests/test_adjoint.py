@@ -111,3 +111,40 @@ def test_autograd_fp32_forward(bt):
     Xr = oracle.solve_block_thomas(Av.detach().double().cpu().numpy(), Bv.detach().double().cpu().numpy(),
                                    Cv.detach().double().cpu().numpy(), Fv.detach().double().cpu().numpy())
     assert _rel(X.detach().double().cpu().numpy(), Xr) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3"])
+def test_autograd_fp32_forward_full_size(bt, precision):
+    # The differentiation workload as specified: N = 2048, M = 64, K = 128,
+    # L = 0.5 ||X - X_target||^2, the forward solve in FP32 arithmetic (FP32 CUDA
+    # cores, or split-BF16 tensor cores) on FP64 factors with refinement, the
+    # adjoint in FP64.  Against the FP64 oracle gradient at the oracle's own
+    # solution: the forward's residual tolerance (1e-12) bounds the difference.
+    A, B, C, F, Xt = gen.config4()
+    Av, Bv, Cv, Fv = (_t(x).requires_grad_(True) for x in (A, B, C, F))
+    X = bt.bt_solve(Av, Bv, Cv, Fv, 64, precision=precision, tol=1e-12)
+    loss = 0.5 * torch.sum((X - _t(Xt)) ** 2)
+    loss.backward()
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    assert oracle.rel_err(X.detach().cpu().numpy(), Xr) <= 1e-10
+    rF, rA, rB, rC = oracle.adjoint_grads(A, B, C, Xr, Xr - Xt)
+    for got, ref, name in ((Fv.grad, rF, "F"), (Av.grad, rA, "A"), (Bv.grad, rB, "B"), (Cv.grad, rC, "C")):
+        assert _rel(got.cpu().numpy(), ref) <= 1e-8, name
+    assert float(Av.grad[0].abs().max()) == 0.0 and float(Bv.grad[-1].abs().max()) == 0.0
+
+
+def test_autograd_fp32_dtype_full_size(bt):
+    # FP32 tensors in and out at full size: the gradients (FP32) against the
+    # FP64 oracle gradient of the FP32-rounded inputs, to FP32 accuracy
+    A, B, C, F, Xt = gen.config4()
+    Av, Bv, Cv, Fv = (_t(x).float().requires_grad_(True) for x in (A, B, C, F))
+    X = bt.bt_solve(Av, Bv, Cv, Fv, 64)
+    assert X.dtype == torch.float32
+    loss = 0.5 * torch.sum((X.double() - _t(Xt)) ** 2)
+    loss.backward()
+    A64, B64, C64, F64 = (v.detach().double().cpu().numpy() for v in (Av, Bv, Cv, Fv))
+    Xr = oracle.solve_block_thomas(A64, B64, C64, F64)
+    rF, rA, rB, rC = oracle.adjoint_grads(A64, B64, C64, Xr, Xr - Xt)
+    for got, ref, name in ((Fv.grad, rF, "F"), (Av.grad, rA, "A"), (Bv.grad, rB, "B"), (Cv.grad, rC, "C")):
+        assert got.dtype == torch.float32
+        assert _rel(got.double().cpu().numpy(), ref) <= 1e-6, name

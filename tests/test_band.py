@@ -71,7 +71,9 @@ def test_band_parity(bt, n, kl, ku, M, S, K):
     assert info["A"][0] >= M - kl or kl == 0  # upper triangular A_j
     assert info["B"][1] <= ku - M or ku == 0  # lower triangular B_j
     assert oracle.rel_err(X, Xr) <= 1e-12
+    assert oracle.col_err(X, Xr) <= 1e-12
     assert oracle.rel_err(X, Xl) <= 1e-12
+    assert oracle.col_err(X, Xl) <= 1e-12
 
 
 @pytest.mark.parametrize("n", [2560, 2500])
@@ -87,6 +89,7 @@ def test_band_refined(bt, n):
         X, info = fac.solve(_t(F), precision="bf16x3", tol=1e-11, return_info=True)
     assert info["converged"]
     assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10
+    assert oracle.col_err(X.cpu().numpy(), Xr) <= 1e-10
 
 
 def test_band_vector_rhs_and_out(bt):
@@ -100,6 +103,7 @@ def test_band_vector_rhs_and_out(bt):
     assert x.shape == (n,) and x2.data_ptr() == out.data_ptr()
     xl = scipy.linalg.solve_banded((kl, ku), ab, f)
     assert oracle.rel_err(x.cpu().numpy(), xl) <= 1e-12
+    assert oracle.col_err(x.cpu().numpy(), xl) <= 1e-12
     assert torch.equal(x, out)
 
 
@@ -124,6 +128,7 @@ def test_band_detection_general_blocks(bt, M):
         X = fac.solve(_t(F)).cpu().numpy()
     assert info["A"] == (5, 20) and info["B"] == (-30, -3) and info["n"] == 0
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-12
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-12
 
 
 def test_band_detection_dense_and_stencil(bt):

@@ -44,6 +44,7 @@ def _check(mats, sets, Xs):
         Xr = oracle.solve_block_thomas(A, B, C, st.F)
         err = oracle.rel_err(X.cpu().numpy(), Xr)
         assert err <= TOL, (st.K, err)
+        assert oracle.col_err(X.cpu().numpy(), Xr) <= TOL, st.K
 
 
 @pytest.mark.parametrize("S_list", [(8, 16, 4), (1, 64, 2)])
@@ -108,11 +109,13 @@ def test_batched_config3_shape_sampled(bt):
     torch.cuda.synchronize()
     rng = np.random.default_rng(0)
     for st, X in zip(sets, Xs):
-        cols = sorted(set(rng.integers(0, st.K, size=min(3, st.K)).tolist()))
+        # one column from every 128-column tile, and the last column
+        cols = sorted({int(t + rng.integers(0, min(128, st.K - t))) for t in range(0, st.K, 128)} | {st.K - 1})
         A, B, C = mats[st.matrix]
         Xr = oracle.solve_block_thomas(A, B, C, st.F[:, :, cols])
         err = oracle.rel_err(X[:, :, cols].cpu().numpy(), Xr)
         assert err <= TOL, (st.K, err)
+        assert oracle.col_err(X[:, :, cols].cpu().numpy(), Xr) <= TOL, st.K
 
 
 def test_batched_rejects_bad_input(bt):
@@ -144,3 +147,50 @@ def test_batched_matrices_of_different_sizes(bt):
     Xs = bt.solve_batched([facs[s.matrix] for s in sets], [_t(s.F) for s in sets])
     torch.cuda.synchronize()
     _check(mats, sets, Xs)
+
+
+def test_grid_barrier_timeout_is_reported_and_the_plan_recovers(bt):
+    # Failure detection without a GPU fault: CTA 0 of the persistent launch
+    # leaves instead of arriving at the barrier after the first stage, so the
+    # other CTAs' bounded waits (limited to 5 ms here) run out; the run reports
+    # BT_ERR_TIMEOUT promptly, and the same plan then solves correctly.
+    import time
+
+    mats = [gen.dominant_blocks(64, 16, seed=s) for s in (1, 2)]
+    sets = [gen.uniform_rhs(64, 16, k, seed=10 + k) for k in (5, 40)]
+    facs = _factors(bt, mats, (8, 16))
+    Fs = [_t(F) for F in sets]
+    Xs = [torch.zeros_like(F) for F in Fs]
+    plan = bt.BatchPlan(facs, Fs, Xs)
+    assert plan.stages >= 2 and plan.ctas >= 2
+    plan.debug(limit_s=0.005, skip_stage=0)
+    t0 = time.perf_counter()
+    plan.run()
+    with pytest.raises(bt.BtError) as ei:
+        plan.status()
+    assert ei.value.name == "BT_ERR_TIMEOUT"
+    assert time.perf_counter() - t0 < 2.0  # the limit, not the 20 s default
+    # the failure was contained: the device and the plan still work
+    plan.debug(limit_s=0.0, skip_stage=-1)
+    plan.run()
+    plan.status()
+    for (A, B, C), F, X in zip(mats, sets, Xs):
+        Xr = oracle.solve_block_thomas(A, B, C, F)
+        assert oracle.rel_err(X.cpu().numpy(), Xr) <= TOL
+        assert oracle.col_err(X.cpu().numpy(), Xr) <= TOL
+    plan.close()
+    for f in facs:
+        f.close()
+
+
+def test_batch_debug_rejects_bad_arguments(bt):
+    mats = [gen.dominant_blocks(16, 4, seed=1)]
+    facs = _factors(bt, mats, (4,))
+    F = _t(gen.uniform_rhs(16, 4, 3, seed=2))
+    plan = bt.BatchPlan(facs, [F], [torch.zeros_like(F)])
+    for lim, skip in ((-1.0, -1), (61.0, -1), (0.0, -2)):
+        with pytest.raises(bt.BtError) as ei:
+            plan.debug(limit_s=lim, skip_stage=skip)
+        assert ei.value.name == "BT_ERR_ARG"
+    plan.close()
+    facs[0].close()

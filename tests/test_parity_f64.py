@@ -47,7 +47,9 @@ def test_config0_tiny_random(bt):
     X = _solve(bt, w.A, w.B, w.C, w.F, w.S)
     Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F)
     assert oracle.rel_err(X, Xr) <= TOL
+    assert oracle.col_err(X, Xr) <= TOL
     assert oracle.rel_err(X, oracle.solve_dense(w.A, w.B, w.C, w.F)) <= TOL
+    assert oracle.col_err(X, oracle.solve_dense(w.A, w.B, w.C, w.F)) <= TOL
     assert oracle.rel_res(w.A, w.B, w.C, X, w.F) <= TOL
 
 
@@ -67,6 +69,7 @@ def test_random_shapes(bt, N, M, K, S):
     F = gen.uniform_rhs(N, M, K, seed=K + 3)
     X = _solve(bt, A, B, C, F, S)
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
 
 
 @pytest.mark.parametrize("N,M,S", [(256, 60, 64), (128, 150, 32), (2048, 60, 256)])
@@ -83,6 +86,7 @@ def test_paper_block_sizes(bt, N, M, S):
         F = gen.uniform_rhs(N, M, K, seed=K)
         X = _solve(bt, A, B, C, F, S)
         assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
+        assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= TOL
         assert oracle.rel_res(A, B, C, X, F) <= TOL
 
 
@@ -161,6 +165,7 @@ def test_host_buffers_end_to_end(bt):
         Xh = fac.solve(torch.from_numpy(w.F).pin_memory())
         assert Xh.device.type == "cpu"
         assert oracle.rel_err(Xh.numpy(), oracle.solve_block_thomas(w.A, w.B, w.C, w.F)) <= TOL
+        assert oracle.col_err(Xh.numpy(), oracle.solve_block_thomas(w.A, w.B, w.C, w.F)) <= TOL
 
 
 # ---------------------------------------------------------------------------
@@ -177,16 +182,18 @@ def test_config1_poisson_full_size(bt):
     Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
     err_oracle = oracle.rel_err(X[:, :, cols], Xr)
     assert err_oracle <= TOL, err_oracle
+    assert oracle.col_err(X[:, :, cols], Xr) <= TOL
     assert err_exact <= 1e-11, err_exact  # kappa ~ 5e4 times FP64 rounding
 
 
 def test_config2_acoustic_fp64_sampled_columns(bt):
-    cols = [0, 255, 511]
+    cols = [0, 130, 300, 511]  # one column in each 128-column tile
     w = gen.config2()
     with bt.factor(_t(w.A), _t(w.B), _t(w.C), w.S) as fac:
         X = fac.solve(_t(w.F)).cpu().numpy()
     Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
     assert oracle.rel_err(X[:, :, cols], Xr) <= TOL
+    assert oracle.col_err(X[:, :, cols], Xr) <= TOL
 
 
 def test_config4_matrix_fp64(bt):
@@ -196,3 +203,4 @@ def test_config4_matrix_fp64(bt):
         X = fac.solve(_t(F)).cpu().numpy()
     Xr = oracle.solve_block_thomas(A, B, C, F[:, :, cols])
     assert oracle.rel_err(X[:, :, cols], Xr) <= TOL
+    assert oracle.col_err(X[:, :, cols], Xr) <= TOL

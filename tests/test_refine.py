@@ -43,6 +43,7 @@ def test_refined_dense_random(bt, prec, N, M, K, S):
     assert info["converged"] and info["rel_res"] <= 1e-12
     assert oracle.rel_res(A, B, C, X, F) <= 2e-12
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -57,18 +58,20 @@ def test_refined_poisson_stencil(bt, prec):
     assert info["converged"]
     assert oracle.rel_res(A, B, C, X, F) <= 2e-12
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
 def test_refined_acoustic_full_size(bt, prec):
     w = gen.config2()
-    cols = [0, 100, 511]
+    cols = [0, 130, 300, 511]  # one column in each 128-column tile
     with bt.factor(_t(w.A), _t(w.B), _t(w.C), w.S) as fac:
         X, info = fac.solve(_t(w.F), precision=prec, tol=1e-12, return_info=True)
         X = X.cpu().numpy()
     assert info["converged"] and info["rel_res"] <= 1e-12
     Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
     assert oracle.rel_err(X[:, :, cols], Xr) <= 1e-10
+    assert oracle.col_err(X[:, :, cols], Xr) <= 1e-10
     assert oracle.rel_res(w.A, w.B, w.C, X[:, :, cols], w.F[:, :, cols]) <= 1e-11
 
 
@@ -112,6 +115,7 @@ def test_tc_refined_dense(bt, prec, N, M, K, S):
     assert info["converged"] and info["rel_res"] <= 1e-12
     assert oracle.rel_res(A, B, C, X, F) <= 2e-12
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
 
 
 @pytest.mark.parametrize("prec", TC)
@@ -126,18 +130,20 @@ def test_tc_refined_stencil(bt, prec):
     assert info["converged"]
     assert oracle.rel_res(A, B, C, X, F) <= 2e-12
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
 
 
 @pytest.mark.parametrize("prec", TC)
 def test_tc_refined_acoustic_full_size(bt, prec):
     w = gen.config2()
-    cols = [0, 257, 511]
+    cols = [0, 130, 300, 511]  # one column in each 128-column tile
     with bt.factor(_t(w.A), _t(w.B), _t(w.C), w.S) as fac:
         X, info = fac.solve(_t(w.F), precision=prec, tol=1e-12, return_info=True)
         X = X.cpu().numpy()
     assert info["converged"] and info["rel_res"] <= 1e-12, info
     Xr = oracle.solve_block_thomas(w.A, w.B, w.C, w.F[:, :, cols])
     assert oracle.rel_err(X[:, :, cols], Xr) <= 1e-10
+    assert oracle.col_err(X[:, :, cols], Xr) <= 1e-10
 
 
 def test_tc_unsupported_block_size(bt):
@@ -161,6 +167,7 @@ def test_split_precision_needs_fewer_passes(bt):
     assert i3["rel_res0"] < 1e-2 * i1["rel_res0"], (i1, i3)
     assert i3["iters"] < i1["iters"], (i1, i3)
     assert oracle.rel_err(X3.cpu().numpy(), oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X3.cpu().numpy(), oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
 
 
 def test_repeated_solves_replay_a_graph(bt):
@@ -224,6 +231,7 @@ def test_refined_sets_on_concurrent_streams(bt):
                 A, B, C = mats[i % 2]
                 Xr = oracle.solve_block_thomas(A, B, C, Fs_np[i])
                 assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10, (rnd, i)
+                assert oracle.col_err(X.cpu().numpy(), Xr) <= 1e-10, (rnd, i)
 
 
 @pytest.mark.parametrize("pinned", [True, False])
@@ -244,6 +252,7 @@ def test_host_buffers_in_overlapped_chunks(bt, pinned):
                 X = fac.solve(Fh, precision=prec, tol=1e-11)
                 assert X.device.type == "cpu" and X.shape == F.shape
                 assert oracle.rel_err(X.numpy(), Xr) <= bar, prec
+                assert oracle.col_err(X.numpy(), Xr) <= bar, prec
 
 
 def test_graph_cache_evicts_beyond_its_capacity(bt):
@@ -265,3 +274,4 @@ def test_graph_cache_evicts_beyond_its_capacity(bt):
         torch.cuda.synchronize()
         for X in outs:
             assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10
+            assert oracle.col_err(X.cpu().numpy(), Xr) <= 1e-10

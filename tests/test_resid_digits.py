@@ -196,7 +196,9 @@ def test_refined_solve_with_digit_residual(bt, prec):
     assert abs(info["rel_res"] - rr) <= 1e-3 * rr + 1e-13
     Xr = oracle.solve_block_thomas(A, B, C, F)
     assert oracle.rel_err(X, Xr) <= 1e-10
+    assert oracle.col_err(X, Xr) <= 1e-10
     assert oracle.rel_err(X2.cpu().numpy(), Xr) <= 1e-10
+    assert oracle.col_err(X2.cpu().numpy(), Xr) <= 1e-10
 
 
 def test_residual_rejects_bad_arguments(bt):

@@ -182,3 +182,4 @@ def test_refinement_with_out_of_range_values(bt):
     assert info["converged"]
     assert oracle.rel_res(A, B, C, X, F) <= 2e-12
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-10

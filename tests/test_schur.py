@@ -75,6 +75,7 @@ def test_schur_solve(bt, d, K):
     A, B, C = schur.grid_blocks(nr, nz, shift)
     assert info["converged"] and info["rel_res"] <= 1e-11
     assert oracle.rel_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-9
+    assert oracle.col_err(X, oracle.solve_block_thomas(A, B, C, F)) <= 1e-9
     # iteration count of the oracle's PCG with the oracle's S and B
     n = (p - 1) * nr
     g = schur.schur_rhs(F, nr, h, p, shift).reshape(n, K)
