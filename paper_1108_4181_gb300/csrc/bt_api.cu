@@ -98,7 +98,7 @@ static void destroy_handle(bt_handle_s* h) {
   h->prof.destroy();
   h->arena.release();
   if (h->scratch) cudaFree(h->scratch);
-  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->ir_state, h->adj_lam, h->dg_fac,
+  for (void* q : {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->lp_x1, h->ir_state, h->adj_lam, h->dg_fac,
                   static_cast<void*>(h->dg_ea), h->dg_x, h->dg_col})
     if (q) cudaFree(q);
   for (auto& g : h->rgraphs) {

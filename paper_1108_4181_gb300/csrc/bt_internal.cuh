@@ -167,8 +167,9 @@ struct bt_handle_s {
   void* lp_r = nullptr;
   void* lp_d = nullptr;
   void* lp_c = nullptr;
-  void* lp_x = nullptr;  // FP32 correction panel of the tensor-core solve
-  size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0, lp_x_bytes = 0;
+  void* lp_x = nullptr;   // FP32 correction panel of the tensor-core solve
+  void* lp_x1 = nullptr;  // the first solve's result as an FP32 panel (unit-stencil refinement)
+  size_t lp_panel_bytes = 0, lp_d_bytes = 0, lp_c_bytes = 0, lp_x_bytes = 0, lp_x1_bytes = 0;
   void* ir_state = nullptr;
   int lp_gen = 0;  // bumped whenever a refinement buffer is reallocated
 
@@ -287,6 +288,9 @@ struct TcBuffers {
   float* c;
   float* d;  // FP32 correction panel, block-transposed like w
   int64_t Kp;
+  // with accumulate 2 and the split-BF16 M = 128 correction: the result as a
+  // row-major [N][M][K] FP32 panel here instead of d
+  float* drow = nullptr;
 };
 
 // Column tile of the tensor-core kernels for a precision and block size (0: unsupported).
@@ -296,6 +300,8 @@ int tc_planes(int precision);
 // Builds the tensor-core factor copies for `precision` (once per handle).
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st);
 // One tensor-core stage-2 solve: r -> w (y, W, X~), then X (+)= solution.
+// accumulate: 0 X = d (the first solve), 1 X += d, 2 only the FP32 correction
+// panel is written (tb.drow when set, else tb.d; X is not touched).
 bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,
                    const int* done, int* status, cudaStream_t st);
 

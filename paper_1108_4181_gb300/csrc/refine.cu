@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "bt_internal.cuh"
@@ -339,11 +340,24 @@ struct Slot {
 // row j at (j ldr + n) M + m, ldr = Kp, columns K..Kp-1 written as zero; with
 // sp = 2 the rounding remainder in plane 1); otherwise the row-major panel
 // (ld = K) in FP32 or FP64.
-template <typename TR, bool TRANS>
+//
+// Where X comes from (SRC):
+//   0  the row-major FP64 solution X, split on the integer pipe;
+//   1  X = d1, a row-major [N][M][K] FP32 panel (the first solve's result,
+//      exact in FP32: no split);
+//   2  X = d1 + d, two such panels (the first refinement pass: the two
+//      solves' results), summed exactly by TwoSum; the kernel also writes
+//      X = d1 + d (FP64, exact) into the row-major solution for its own rows,
+//      so the update and the residual are one pass over the panels.
+// SRC 1 and 2 are used with TRANS (the tensor-core solve's residual panel).
+template <typename TR, bool TRANS, int SRC>
 struct DwResid {
   static constexpr int MC = 4, JC = 48;
   const double* __restrict__ F;
   const double* __restrict__ X;
+  const float* __restrict__ D1;
+  const float* __restrict__ D2;
+  double* __restrict__ Xout;
   const float2* __restrict__ Cdw;
   TR* __restrict__ r;
   int N, K, ldr, M, sp;
@@ -352,15 +366,35 @@ struct DwResid {
   int n, j1, m0;
   bool colok, okl, okr;
   uint32_t amax = 0;
+  bool fbig = false;  // an FP32 input of magnitude 2^77 or more
   Ssq acc;
 
-  __device__ __forceinline__ void load_x(int j, double (&t)[MC + 2]) const {
-    const bool jok = j >= 0 && j < N;
-    const double* p = X + ((size_t)j * M + m0 - 1) * K + n;
-    t[0] = (jok && okl) ? __ldg(p) : 0.0;
+  // raw X values of one row window (FP64 for SRC 0, FP32 panel values otherwise)
+  struct Raw {
+    double x[SRC == 0 ? MC + 2 : 1];
+    float a[SRC == 0 ? 1 : MC + 2];
+    float b[SRC == 2 ? MC + 2 : 1];
+  };
+
+  __device__ __forceinline__ void load_panel(const float* __restrict__ P, bool jok, int j, float (&t)[MC + 2]) const {
+    const float* p = P + ((size_t)j * M + m0 - 1) * K + n;
+    t[0] = (jok && okl) ? __ldg(p) : 0.f;
 #pragma unroll
-    for (int q = 1; q <= MC; ++q) t[q] = (jok && colok) ? __ldg(p + (size_t)q * K) : 0.0;
-    t[MC + 1] = (jok && okr) ? __ldg(p + (size_t)(MC + 1) * K) : 0.0;
+    for (int q = 1; q <= MC; ++q) t[q] = (jok && colok) ? __ldg(p + (size_t)q * K) : 0.f;
+    t[MC + 1] = (jok && okr) ? __ldg(p + (size_t)(MC + 1) * K) : 0.f;
+  }
+  __device__ __forceinline__ void load_x(int j, Raw& t) const {
+    const bool jok = j >= 0 && j < N;
+    if constexpr (SRC == 0) {
+      const double* p = X + ((size_t)j * M + m0 - 1) * K + n;
+      t.x[0] = (jok && okl) ? __ldg(p) : 0.0;
+#pragma unroll
+      for (int q = 1; q <= MC; ++q) t.x[q] = (jok && colok) ? __ldg(p + (size_t)q * K) : 0.0;
+      t.x[MC + 1] = (jok && okr) ? __ldg(p + (size_t)(MC + 1) * K) : 0.0;
+    } else {
+      load_panel(D1, jok, j, t.a);
+      if constexpr (SRC == 2) load_panel(D2, jok, j, t.b);
+    }
   }
   __device__ __forceinline__ void load_f(int j, double (&t)[MC]) const {
     const bool jok = j >= 0 && j < N && colok;
@@ -368,9 +402,20 @@ struct DwResid {
 #pragma unroll
     for (int q = 0; q < MC; ++q) t[q] = jok ? __ldg(p + (size_t)q * K) : 0.0;
   }
-  __device__ __forceinline__ void split_x(const double (&t)[MC + 2], Slot<MC>& o) {
+  __device__ __forceinline__ void split_x(const Raw& t, Slot<MC>& o) {
 #pragma unroll
-    for (int q = 0; q < MC + 2; ++q) dw_split(t[q], o.h[q], o.l[q], amax);
+    for (int q = 0; q < MC + 2; ++q) {
+      if constexpr (SRC == 0) {
+        dw_split(t.x[q], o.h[q], o.l[q], amax);
+      } else if constexpr (SRC == 1) {
+        o.h[q] = t.a[q];
+        o.l[q] = 0.f;
+        fbig = fbig || !(fabsf(t.a[q]) < 0x1p77f);
+      } else {
+        two_sum(t.a[q], t.b[q], o.h[q], o.l[q]);
+        fbig = fbig || !(fabsf(t.a[q]) < 0x1p77f) || !(fabsf(t.b[q]) < 0x1p77f);
+      }
+    }
   }
   __device__ __forceinline__ void split_f(const double (&t)[MC], float (&fh)[MC], float (&fl)[MC]) {
 #pragma unroll
@@ -381,7 +426,8 @@ struct DwResid {
   __device__ __forceinline__ void step(Slot<MC>& U, const Slot<MC>& C, const Slot<MC>& D, float (&fh)[MC],
                                        float (&fl)[MC], int j) {
     const bool more = j + 1 < j1;
-    double px[MC + 2], pf[MC];
+    Raw px;
+    double pf[MC];
     load_x(more ? j + 2 : -1, px);
     load_f(more ? j + 1 : -1, pf);
     const float4* cp = reinterpret_cast<const float4*>(Cdw + (size_t)j * M + m0);
@@ -395,6 +441,13 @@ struct DwResid {
       acc.add(v[q]);
     }
     store(v, j);
+    if constexpr (SRC == 2) {
+      if (colok) {  // X = d1 + d for the item's rows of block row j (exact in FP64)
+        double* o = Xout + ((size_t)j * M + m0) * K + n;
+#pragma unroll
+        for (int q = 0; q < MC; ++q) o[(size_t)q * K] = f32_to_f64(C.h[q + 1]) + f32_to_f64(C.l[q + 1]);
+      }
+    }
     split_x(px, U);
     split_f(pf, fh, fl);
   }
@@ -436,16 +489,23 @@ struct DwResid {
   }
 };
 
-template <typename TR, bool TRANS>
+// Runs when pass_lo <= st->solves <= pass_hi (the refinement's pass count).
+template <typename TR, bool TRANS, int SRC>
 __global__ void __launch_bounds__(256, 2) k_resid_dw(const double* __restrict__ F, const double* __restrict__ X,
-                                                    const float2* __restrict__ Cdw, TR* __restrict__ r, int64_t N,
-                                                    int M, int64_t K, int64_t ldr, int sp, IrState* st) {
-  using W = DwResid<TR, TRANS>;
+                                                    const float* __restrict__ D1, const float* __restrict__ D2,
+                                                    double* __restrict__ Xout, const float2* __restrict__ Cdw,
+                                                    TR* __restrict__ r, int64_t N, int M, int64_t K, int64_t ldr,
+                                                    int sp, int pass_lo, int pass_hi, IrState* st) {
+  using W = DwResid<TR, TRANS, SRC>;
   constexpr int MC = W::MC, JC = W::JC;
-  if (st->done) return;
+  static_assert(SRC == 0 || TRANS, "the FP32 panels are block-transposed");
+  if (st->done || st->solves < pass_lo || st->solves > pass_hi) return;
   W w;
   w.F = F;
   w.X = X;
+  w.D1 = D1;
+  w.D2 = D2;
+  w.Xout = Xout;
   w.Cdw = Cdw;
   w.r = r;
   w.N = (int)N;
@@ -470,7 +530,8 @@ __global__ void __launch_bounds__(256, 2) k_resid_dw(const double* __restrict__ 
     Slot<MC> A, B, C;
     float fh[MC], fl[MC];
     {
-      double t[MC + 2], tf[MC];
+      typename W::Raw t;
+      double tf[MC];
       w.load_x(j0 - 1, t);
       w.split_x(t, A);
       w.load_x(j0, t);
@@ -488,8 +549,32 @@ __global__ void __launch_bounds__(256, 2) k_resid_dw(const double* __restrict__ 
     }
   }
   // |v| >= 2^77 (or non-finite) anywhere: the FP64 kernel recomputes
-  if (__any_sync(0xffffffffu, w.amax >= (1100u << 21)) && lane == 0) atomicExch(&st->range, 1);
+  if (__any_sync(0xffffffffu, w.amax >= (1100u << 21) || w.fbig) && lane == 0) atomicExch(&st->range, 1);
   block_add(w.acc.total(), &st->rn2[st->cur]);
+}
+
+// X from the row-major FP32 panels of the unit-stencil refinement: X = d1
+// (+ d when D2 != NULL), exact in FP64.  Runs when pass_lo <= st->solves <=
+// pass_hi and, with need_range, only if st->range is set (the double-word
+// residual then hands over to the FP64 one, which reads X); ignores the stop
+// flag (it also writes the final iterate once the refinement has stopped).
+// Grid-stride over the N M K entries; consecutive threads, consecutive n.
+__global__ void __launch_bounds__(256) k_x_from_panels(const float* __restrict__ D1, const float* __restrict__ D2,
+                                                       double* __restrict__ X, size_t n, int pass_lo, int pass_hi,
+                                                       int need_range, const IrState* st) {
+  if (st->solves < pass_lo || st->solves > pass_hi || (need_range && !st->range)) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    X[e] = D2 != nullptr ? f32_to_f64(__ldg(D1 + e)) + f32_to_f64(__ldg(D2 + e)) : f32_to_f64(__ldg(D1 + e));
+}
+
+// X += d (row-major FP32 panel) for the later refinement passes of the
+// unit-stencil flow (runs when st->solves >= pass_lo and the refinement has
+// not stopped).
+__global__ void __launch_bounds__(256) k_x_add_panel(const float* __restrict__ D, double* __restrict__ X, size_t n,
+                                                     int pass_lo, const IrState* st) {
+  if (st->done || st->solves < pass_lo) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    X[e] += f32_to_f64(__ldg(D + e));
 }
 
 // The first residual (X = 0): F rounded into the block-transposed panel, one
@@ -670,6 +755,88 @@ bt_status grow(void** p, size_t* have, size_t need, cudaStream_t st) {
   return BT_OK;
 }
 
+template <typename TR, bool TRANS, int SRC>
+bt_status launch_dw(bt_handle_s* h, const double* F, const double* X, const float* d1, const float* d2, double* xout,
+                    TR* r, int64_t K, int64_t ldr, int sp, int pass_lo, int pass_hi, IrState* st, cudaStream_t s) {
+  using W = DwResid<TR, TRANS, SRC>;
+  const int M = (int)h->M;
+  static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<TR, TRANS, SRC>), 256, 0);
+  const int64_t items = ((h->N + W::JC - 1) / W::JC) * (M / W::MC) * (((TRANS ? ldr : K) + 31) / 32);
+  const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
+  k_resid_dw<TR, TRANS, SRC><<<blocks, 256, 0, s>>>(F, X, d1, d2, xout, reinterpret_cast<const float2*>(h->Cdw), r,
+                                                     h->N, M, K, ldr, sp, pass_lo, pass_hi, st);
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+// The FP64 residual from X, run only if the double-word residual met an
+// out-of-range value (gated on st->range; its norm goes to st->rn2_fb).
+template <typename TR>
+bt_status launch_fallback(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
+                          int sp, int pass, IrState* st, cudaStream_t s) {
+  const int M = (int)h->M;
+  ProfScope ps(h, s, "resid_fb");
+  if (trans) {
+    static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
+    const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
+    const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
+    k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, &st->range);
+  } else {
+    const size_t n = (size_t)h->N * M * K;
+    static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)grid);
+    k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, 0, pass, st, &st->range);
+  }
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+// X from the FP32 panels (k_x_from_panels), gated as that kernel describes.
+bt_status launch_x_from_panels(bt_handle_s* h, const float* d1, const float* d2, double* X, int64_t K, int pass_lo,
+                               int pass_hi, int need_range, const IrState* st, cudaStream_t s) {
+  static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_from_panels), 256, 0);
+  const size_t n = (size_t)h->N * h->M * K;
+  k_x_from_panels<<<(int)std::min<size_t>((n + 255) / 256, (size_t)grid), 256, 0, s>>>(d1, d2, X, n, pass_lo,
+                                                                                      pass_hi, need_range, st);
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
+// The residuals of the unit-stencil refinement on the tensor-core panels,
+// where the iterate lives in FP32 panels until the first refinement pass:
+//   stage 1 (after the first solve): r = F - P d1 (X not written);
+//   stage 2 (after a refinement solve d): on the first pass one kernel forms
+//     X = d1 + d and r = F - P X from the panels; on later passes X += d,
+//     then r from X.
+// Either stage ends with the gated FP64 fallback.
+template <typename TR>
+bt_status launch_residual_panels(bt_handle_s* h, const double* F, double* X, const float* d1, const float* d,
+                                 TR* r, int64_t K, int64_t Kp, int sp, IrState* st, int stage, cudaStream_t s) {
+  const int M = (int)h->M;
+  if (stage == 1) {
+    {
+      ProfScope ps(h, s, "resid_dw");
+      BT_TRY((launch_dw<TR, true, 1>(h, F, nullptr, d1, nullptr, nullptr, r, K, Kp, sp, 0, 0, st, s)));
+    }
+    {
+      ProfScope ps(h, s, "resid_fb");
+      BT_TRY(launch_x_from_panels(h, d1, nullptr, X, K, 0, 0, 1, st, s));
+    }
+  } else {
+    {
+      ProfScope ps(h, s, "x_update");
+      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_add_panel), 256, 0);
+      const size_t n = (size_t)h->N * M * K;
+      k_x_add_panel<<<(int)std::min<size_t>((n + 255) / 256, (size_t)grid), 256, 0, s>>>(d, X, n, 2, st);
+      BT_CUDA(cudaGetLastError());
+    }
+    ProfScope ps(h, s, "resid_dw");
+    BT_TRY((launch_dw<TR, true, 0>(h, F, X, nullptr, nullptr, nullptr, r, K, Kp, sp, 2, INT32_MAX, st, s)));
+    BT_TRY((launch_dw<TR, true, 2>(h, F, nullptr, d1, d, X, r, K, Kp, sp, 1, 1, st, s)));
+  }
+  return launch_fallback<TR>(h, F, X, r, K, Kp, true, sp, 0, st, s);
+}
+
 // Residual into the solve's panel: row-major (ld = K) for the SIMT solve,
 // block-transposed (ld = Kp) for the tensor-core solve.
 // rmode: 1 FP64 on the CUDA cores, 2 the tensor-core digit residual (dense
@@ -686,36 +853,14 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   if (!first && rmode == 3) {
     // FP32 double-word residual; the FP64 kernel behind it runs only when a
     // value was out of its range (gated on st->range)
-    const float2* cdw = reinterpret_cast<const float2*>(h->Cdw);
     {
       ProfScope ps(h, s, "resid_dw");
-      const int64_t rows = (h->N + DwResid<TR, true>::JC - 1) / DwResid<TR, true>::JC;
-      if (trans) {
-        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<TR, true>), 256, 0);
-        const int64_t items = rows * (M / 4) * ((Kp + 31) / 32);
-        const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
-        k_resid_dw<TR, true><<<blocks, 256, 0, s>>>(F, X, cdw, r, h->N, M, K, Kp, sp, st);
-      } else {
-        static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<TR, false>), 256, 0);
-        const int64_t items = rows * (M / 4) * ((K + 31) / 32);
-        const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
-        k_resid_dw<TR, false><<<blocks, 256, 0, s>>>(F, X, cdw, r, h->N, M, K, K, sp, st);
-      }
+      if (trans)
+        BT_TRY((launch_dw<TR, true, 0>(h, F, X, nullptr, nullptr, nullptr, r, K, Kp, sp, 0, INT32_MAX, st, s)));
+      else
+        BT_TRY((launch_dw<TR, false, 0>(h, F, X, nullptr, nullptr, nullptr, r, K, K, sp, 0, INT32_MAX, st, s)));
     }
-    ProfScope ps(h, s, "resid_fb");
-    if (trans) {
-      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
-      const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
-      const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
-      k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, &st->range);
-    } else {
-      const size_t n = (size_t)h->N * M * K;
-      static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
-      const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)grid);
-      k_resid_stencil<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, first, pass, st, &st->range);
-    }
-    BT_CUDA(cudaGetLastError());
-    return BT_OK;
+    return launch_fallback<TR>(h, F, X, r, K, Kp, trans, sp, pass, st, s);
   }
   ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
@@ -822,7 +967,11 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   }
   const bool digits = o.residual == 2 || (o.residual == 0 && dig_ok);
   const int rmode = digits ? 2 : (o.residual == 3 || (o.residual == 0 && dw_ok)) ? 3 : 1;
-    const void* before[4] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x};
+  // unit stencils on the tensor-core panels: the first solve's result stays an
+  // FP32 panel (d1) and the first refinement pass forms X = d1 + d together
+  // with its residual (launch_residual_panels)
+  const bool pairflow = tcore && rmode == 3 && prec == BT_PREC_BF16X3 && M == 128;
+  const void* before[5] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->lp_x1};
   const size_t panel = (size_t)sp * h->N * M * Kp * eb;
   // series terms [depth][S] and, for the tensor-core step 2.2, one node sum per tree node
   const size_t cbytes = ((size_t)h->depth * h->S + h->nodes.size()) * M * Kp * sizeof(float);
@@ -830,7 +979,10 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
   BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));
   if (tcore) BT_TRY(grow(&h->lp_x, &h->lp_x_bytes, (size_t)h->N * M * Kp * sizeof(float), s));
-  if (before[0] != h->lp_r || before[1] != h->lp_d || before[2] != h->lp_c || before[3] != h->lp_x) ++h->lp_gen;
+  if (pairflow) BT_TRY(grow(&h->lp_x1, &h->lp_x1_bytes, (size_t)h->N * M * K * sizeof(float), s));
+  if (before[0] != h->lp_r || before[1] != h->lp_d || before[2] != h->lp_c || before[3] != h->lp_x ||
+      before[4] != h->lp_x1)
+    ++h->lp_gen;
   if (!h->ir_state) BT_CUDA(cudaMalloc(&h->ir_state, sizeof(IrState)));
   if (digits) BT_TRY(resid_digits_prepare(h, K, s));
   BT_TRY(make_f32_factors(h, s));
@@ -844,7 +996,18 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   // Launched directly, the body is unrolled max_it times and passes after
   // convergence return at once; in the CUDA graph it is the body of a
   // device-side WHILE node whose condition the check kernel sets.
-  auto residual = [&](cudaStream_t q, int first) -> bt_status {
+  float* d1 = reinterpret_cast<float*>(h->lp_x1);
+  float* dk = reinterpret_cast<float*>(h->lp_x);
+  // first: 1 the first residual (X = 0: F rounded), else 0; stage: 1 after the
+  // first solve, 2 after a refinement solve
+  auto residual = [&](cudaStream_t q, int first, int stage) -> bt_status {
+    if (pairflow && !first) {
+      if (prec == BT_PREC_TF32)
+        return launch_residual_panels<float>(h, F, X, d1, dk, reinterpret_cast<float*>(h->lp_r), K, Kp, sp, st,
+                                             stage, q);
+      return launch_residual_panels<__nv_bfloat16>(h, F, X, d1, dk, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K,
+                                                   Kp, sp, st, stage, q);
+    }
     if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
       return launch_residual<__nv_bfloat16>(h, F, X, reinterpret_cast<__nv_bfloat16*>(h->lp_r), K, Kp, true, sp,
                                             first, 0, st, rmode, q);
@@ -854,9 +1017,10 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   auto inner = [&](cudaStream_t q, int accumulate) -> bt_status {
     if (tcore) {
       TcBuffers tb{prec == BT_PREC_BF16 ? h->tc_fac_bf16 : prec == BT_PREC_TF32 ? h->tc_fac_tf32 : h->tc_fac_bf16x3,
-                   h->lp_r, h->lp_d, reinterpret_cast<float*>(h->lp_c),
-                   reinterpret_cast<float*>(h->lp_x), Kp};
-      return solve_tc(h, prec, tb, K, X, accumulate, done, &st->kstatus, q);
+                   h->lp_r, h->lp_d, reinterpret_cast<float*>(h->lp_c), dk, Kp,
+                   pairflow ? (accumulate == 0 ? d1 : dk) : nullptr};
+      // the panel flow keeps the solves' results in the FP32 panels (mode 2)
+      return solve_tc(h, prec, tb, K, X, pairflow ? 2 : accumulate, done, &st->kstatus, q);
     }
     return solve_simt_f32(h, reinterpret_cast<float*>(h->lp_r), K, reinterpret_cast<float*>(h->lp_d),
                           reinterpret_cast<float*>(h->lp_c), X, accumulate, done, q);
@@ -867,12 +1031,19 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   };
   auto prologue = [&](cudaStream_t q, cudaGraphConditionalHandle loop) -> bt_status {
     BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), q));
-    BT_TRY(residual(q, 1));
+    BT_TRY(residual(q, 1, 0));
     check(q, 0);
     BT_TRY(inner(q, 0));
-    BT_TRY(residual(q, 0));
+    BT_TRY(residual(q, 0, 1));
     check(q, loop);
     return BT_OK;
+  };
+  // after the refinement: with no refinement pass taken, the panel flow's
+  // solution is still the FP32 panel d1
+  auto epilogue = [&](cudaStream_t q) -> bt_status {
+    if (!pairflow) return BT_OK;
+    ProfScope ps(h, q, "x_update");
+    return launch_x_from_panels(h, d1, nullptr, X, K, 0, 0, 0, st, q);
   };
   auto body = [&](cudaStream_t q, cudaGraphConditionalHandle loop) -> bt_status {
     {
@@ -880,13 +1051,14 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       k_count_solve<<<1, 1, 0, q>>>(st);
     }
     BT_TRY(inner(q, 1));
-    BT_TRY(residual(q, 0));
+    BT_TRY(residual(q, 0, 2));
     check(q, loop);
     return BT_OK;
   };
   auto enqueue = [&](cudaStream_t q) -> bt_status {
     BT_TRY(prologue(q, 0));
     for (int it = 0; it < max_it; ++it) BT_TRY(body(q, 0));
+    BT_TRY(epilogue(q));
     BT_CUDA(cudaGetLastError());
     return BT_OK;
   };
@@ -926,6 +1098,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
         ok = cudaStreamEndCapture(cap2, &bg_out) == cudaSuccess && bs == BT_OK;
       }
     }
+    ok = ok && epilogue(cap) == BT_OK;  // after the WHILE node
     cudaGraph_t graph = nullptr;
     const bool ended = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
     if (!(ok && ended && graph)) {
@@ -1048,11 +1221,7 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
     BT_TRY(resid_digits_prepare(h, K, s));
     BT_TRY(launch_resid_digits(h, F, X, K, 2, false, R, 1, &st->done, st->rn2, nullptr, &st->kstatus, s));
   } else if (method == 3) {
-    const int64_t items = ((h->N + DwResid<double, false>::JC - 1) / DwResid<double, false>::JC) * (M / 4) *
-                          ((K + 31) / 32);
-    static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_dw<double, false>), 256, 0);
-    k_resid_dw<double, false><<<(int)std::min<int64_t>((items + 7) / 8, grid), 256, 0, s>>>(
-        F, X, reinterpret_cast<const float2*>(h->Cdw), R, h->N, M, K, K, 1, st);
+    BT_TRY((launch_dw<double, false, 0>(h, F, X, nullptr, nullptr, nullptr, R, K, K, 1, 0, INT32_MAX, st, s)));
     const size_t n = (size_t)h->N * M * K;
     k_resid_stencil<double><<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(
         F, X, h->Cdiag, R, h->N, M, K, 0, 0, st, &st->range);

@@ -1085,8 +1085,9 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 template <class C, bool WR>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_correct_ta(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
-                    const __nv_bfloat16* __restrict__ wp, float* __restrict__ dp, double* __restrict__ Xo, int K,
-                    int N, int L, int S, int Kp, int rows_per_cta, const int* done, int* status) {
+                    const __nv_bfloat16* __restrict__ wp, float* __restrict__ dp, double* __restrict__ Xo,
+                    float* __restrict__ Drow, int K, int N, int L, int S, int Kp, int rows_per_cta, const int* done,
+                    int* status) {
   using E = __nv_bfloat16;
   static_assert(C::SW && C::SP == 2 && C::M == 128 && C::MH == 64, "split BF16, M = 128, swapped roles");
   constexpr int TCOLS = 4 * C::M;
@@ -1199,9 +1200,21 @@ __global__ void __launch_bounds__(C::THREADS, 1)
     // Xo != nullptr (the first solve): the result is the solution itself,
     // written as FP64 rows of the row-major X (exact widening; for each block
     // row m the warp's 32 columns are 256 contiguous bytes) instead of the
-    // FP32 correction panel
+    // FP32 correction panel; Drow != nullptr: FP32 rows of a row-major
+    // [N][M][K] panel (128 contiguous bytes per warp and row m)
     auto store_row = [&](const float (&v)[C::MH], int irow) {
-      if (Xo != nullptr) {
+      if (Drow != nullptr) {
+        const int n = n0 + nl;
+        if (n < K) {
+          float* x = Drow + ((size_t)irow * C::M + m0) * K + n;
+#pragma unroll
+          for (int q0 = 0; q0 < C::MH; q0 += 16) {
+#pragma unroll
+            for (int q = q0; q < q0 + 16; ++q) x[(size_t)q * K] = v[q];
+            asm volatile("" ::: "memory");  // one batch of stores at a time
+          }
+        }
+      } else if (Xo != nullptr) {
         const int n = n0 + nl;
         if (n < K) {
           double* x = Xo + ((size_t)irow * C::M + m0) * K + n;
@@ -1794,7 +1807,8 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       ProfScope ps(h, st, "tc_correct");
       // first solve: X = d written by the correction itself (no FP32 round trip)
       k_tc_correct_ta<CT, true><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(
-          tm_fac_c, tm_wc, (const E*)w, tb.d, accumulate ? nullptr : X, (int)K, N, L, S, Kp, L > 1 ? rpc : 0, done,
+          tm_fac_c, tm_wc, (const E*)w, tb.d, accumulate == 0 ? X : nullptr, accumulate == 2 ? tb.drow : nullptr,
+          (int)K, N, L, S, Kp, L > 1 ? rpc : 0, done,
           status);
     } else {
       const size_t smem = correct_smem<CC>();
@@ -1804,8 +1818,8 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
           tm_fac_c, tm_wc, tm_d, (const E*)w, tb.d, N, L, S, Kp, L > 1 ? rpc : 0, done, status);
     }
     BT_CUDA(cudaGetLastError());
-    const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && !accumulate;
-    if (!direct_x) {  // M is 64 or 128
+    const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && accumulate == 0;
+    if (!direct_x && accumulate != 2) {  // M is 64 or 128
       const int64_t nitem = (int64_t)((K + 31) / 32) * (M / 8) * N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update_warp), 256, 0);
       const int blocks = (int)std::min<int64_t>((nitem + 7) / 8, grid);
