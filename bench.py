@@ -200,9 +200,8 @@ FP64_OPS_PEAK = 152 * 2 * 2.070e9  # FP64 pipe operations per second (nominal un
 # the kernel and is reported as null.
 TRAFFIC = {
     # k_resid_warp, one full residual pass of N=1024 (M=128, K=512, S=16):
-    # 1.078 GB read + 0.253 GB written for 6.7e7 unknowns (profiles/
-    # mixed_solve_acoustic_N4096_M128_K512_S64.md); the kernel streams F and X
-    # once per pass, so traffic scales with the unknowns
+    # 1.078 GB read + 0.253 GB written for 6.7e7 unknowns; the kernel streams
+    # F and X once per pass, so traffic scales with the unknowns
     "residual": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
                  "sha256": "48b564ed045e2d9a0ef25b010efcf23d2d97023418e10e02598f551cb7941cef",
                  "bytes_per_unknown": 19.8262},
