@@ -399,7 +399,11 @@ bt_status bt_handle_band(bt_handle h, int64_t out[5]);
  *   what = 2: At [S][M][M]   reduced system of eq. red1, sub-diagonal blocks
  *   what = 3: Ct [S][M][M]   reduced system, diagonal blocks
  *   what = 4: Bt [S][M][M]   reduced system, super-diagonal blocks
- * Rows that are interfaces hold zeros in U and V.  Synchronous.
+ *   what = 5: Y  [N][M][M]   forward responses of the left coupling on
+ *                            interior rows, Y_a = E_a, Y_i = E_i Y_{i-1} with
+ *                            E_i = D_i^{-1} A_i (the first half of eq. sub1;
+ *                            built on first use)
+ * Rows that are interfaces hold zeros in U, V and Y.  Synchronous.
  */
 bt_status bt_factor_export(bt_handle h, int32_t what, double* dst);
 

@@ -647,9 +647,13 @@ bt_status bt_handle_band(bt_handle h, int64_t out[5]) {
 }
 
 bt_status bt_factor_export(bt_handle h, int32_t what, double* dst) {
-  if (!h || !dst || what < 0 || what > 4) {
-    set_error("bt_factor_export: need a handle, a device buffer and what in 0..4");
+  if (!h || !dst || what < 0 || what > 5) {
+    set_error("bt_factor_export: need a handle, a device buffer and what in 0..5");
     return BT_ERR_ARG;
+  }
+  if (what == 5) {
+    cudaSetDevice(h->device);
+    BT_TRY(factor_left_responses(h, nullptr));
   }
   const size_t MM = (size_t)h->M * h->M;
   const double* src = nullptr;
@@ -660,6 +664,7 @@ bt_status bt_factor_export(bt_handle h, int32_t what, double* dst) {
     case 2: src = h->At; n = h->S * MM; break;
     case 3: src = h->Ct; n = h->S * MM; break;
     case 4: src = h->Bt; n = h->S * MM; break;
+    case 5: src = h->Y; n = h->N * MM; break;
   }
   BT_CUDA(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice));
   return BT_OK;

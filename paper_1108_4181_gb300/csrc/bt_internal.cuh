@@ -113,6 +113,9 @@ struct bt_handle_s {
   double* G = nullptr;
   double* U = nullptr;
   double* V = nullptr;
+  // Forward responses of the left coupling (Y_a = E_a, Y_i = E_i Y_{i-1}),
+  // built on first use (factor_left_responses).
+  double* Y = nullptr;
 
   // Coupling blocks of the interface rows, A_{k_s} and B_{k_s}, [S][M][M].
   double* AK = nullptr;
@@ -155,6 +158,9 @@ struct bt_handle_s {
   void* tc_fac_bf16 = nullptr;
   void* tc_fac_tf32 = nullptr;
   void* tc_fac_bf16x3 = nullptr;  // [2][5][N][M][M]: rounded values and their remainders
+  // split-BF16 copies [2][4][N][M][M] of Dinv, G, Z = U^T and Y for the
+  // forward / backward stage 2 of unit stencils (solve_tc.cu)
+  void* tc_fac_fb = nullptr;
   // Split-BF16 copies of the interface blocks for the tensor-core step 2.2,
   // [2][AK (S), BK (S), R (depth*S), HL (S), HR (S)][M][M], and the job table of
   // that step (device; host offsets: F~ jobs, series-term jobs, one group per level).
@@ -300,6 +306,9 @@ int tc_planes(int precision);
 // Builds the tensor-core factor copies for `precision` (once per handle).
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st);
 // One tensor-core stage-2 solve: r -> w (y, W, X~), then X (+)= solution.
+// Y of the handle (see bt_handle_s::Y), built once.
+bt_status factor_left_responses(bt_handle_s* h, cudaStream_t st);
+
 // accumulate: 0 X = d (the first solve), 1 X += d, 2 only the FP32 correction
 // panel is written (tb.drow when set, else tb.d; X is not touched).
 bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,

@@ -382,6 +382,38 @@ struct InvBatch {
   }
 };
 
+// Runs an uploaded schedule (pointer table dtab) of batched GEMMs and
+// inverses on `st`; singular pivots set dstatus[0].
+bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dstatus, cudaStream_t st) {
+  const size_t MM = (size_t)M * M;
+  const int use_smem = M <= INV_SMEM_MAX ? 1 : 0;
+  const size_t inv_smem = use_smem ? (MM + M) * sizeof(double) + M * sizeof(int)
+                                   : M * sizeof(double) + M * sizeof(int);
+  BT_CUDA(cudaFuncSetAttribute(k_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
+  const int inv_threads = (int)std::min<size_t>(1024, std::max<size_t>(32, ((MM + 31) / 32) * 32));
+  // GEMM tile: 32 when 64-tiles would pad the block by more than about 15 % in area
+  const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
+  const int GT = (double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64;
+  const int tiles = (M + GT - 1) / GT;
+  for (const Op& o : sc.ops) {
+    // grid.z / grid.x limits: split very large batches
+    for (int b0 = 0; b0 < o.batch; b0 += 65535) {
+      int nb = std::min(65535, o.batch - b0);
+      if (o.kind == 0) {
+        dim3 grid(tiles, tiles, nb);
+        if (GT == 32)
+          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
+        else
+          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
+      } else {
+        k_inverse_batched<<<nb, inv_threads, inv_smem, st>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
+      }
+    }
+  }
+  BT_CUDA(cudaGetLastError());
+  return BT_OK;
+}
+
 }  // namespace
 
 std::vector<TreeNode> build_tree(int S, int* depth_out) {
@@ -608,31 +640,7 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_CUDA(cudaMemsetAsync(dstatus, 0, 3 * sizeof(int), st));
   BT_CUDA(cudaMemcpyAsync(dtab, sc.tab.data(), sc.tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
 
-  const int use_smem = M <= INV_SMEM_MAX ? 1 : 0;
-  const size_t inv_smem = use_smem ? (MM + M) * sizeof(double) + M * sizeof(int)
-                                   : M * sizeof(double) + M * sizeof(int);
-  BT_CUDA(cudaFuncSetAttribute(k_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
-  const int inv_threads = (int)std::min<size_t>(1024, std::max<size_t>(32, ((MM + 31) / 32) * 32));
-  // GEMM tile: 32 when 64-tiles would pad the block by more than about 15 % in area
-  const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
-  const int GT = (double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64;
-  const int tiles = (M + GT - 1) / GT;
-  for (const Op& o : sc.ops) {
-    // grid.z / grid.x limits: split very large batches
-    for (int b0 = 0; b0 < o.batch; b0 += 65535) {
-      int nb = std::min(65535, o.batch - b0);
-      if (o.kind == 0) {
-        dim3 grid(tiles, tiles, nb);
-        if (GT == 32)
-          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
-        else
-          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
-      } else {
-        k_inverse_batched<<<nb, inv_threads, inv_smem, st>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
-      }
-    }
-  }
-  BT_CUDA(cudaGetLastError());
+  BT_TRY(run_schedule(sc, dtab, M, dstatus, st));
 
   // stencil detection (A_j = B_j = I, tridiagonal C_j) for the residual
   k_detect_stencil<<<1024, 256, 0, st>>>(h->A, h->B, h->C, N, M, dstatus + 1);
@@ -671,6 +679,48 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
     set_error("bt_factor: a pivot block of the block sweep or of the reduced system is singular or non-finite");
     return BT_ERR_SINGULAR;
   }
+  return BT_OK;
+}
+
+// The forward responses of the left interface coupling, Y_a = E_a and
+// Y_i = E_i Y_{i-1} on the interior rows a..b of every segment (the part of
+// eq. sub1 before the backward products), into h->Y ([N][M][M] FP64,
+// interface rows zero); built on first use by the tensor-core stage 2 of
+// unit stencils, whose backward pass applies Y_i X~_s row by row.
+bt_status factor_left_responses(bt_handle_s* h, cudaStream_t st) {
+  if (h->Y) return BT_OK;
+  const int64_t N = h->N, S = h->S, L = h->L;
+  const int M = (int)h->M;
+  const size_t MM = (size_t)M * M;
+  double* Y = nullptr;
+  BT_TRY(h->arena.alloc((void**)&Y, N * MM * sizeof(double)));
+  BT_CUDA(cudaMemsetAsync(Y, 0, N * MM * sizeof(double), st));
+  double* Iw = nullptr;
+  BT_CUDA(cudaMallocAsync((void**)&Iw, MM * sizeof(double), st));
+  k_set_identity<<<(int)((MM + 255) / 256), 256, 0, st>>>(Iw, M);
+  BT_CUDA(cudaGetLastError());
+  Schedule sc;
+  GemmBatch g;
+  auto blk = [&](double* base, int64_t j) { return base + (size_t)j * MM; };
+  for (int64_t t = 1; t < L; ++t) {
+    for (int64_t s = 0; s < S; ++s) {
+      const int64_t i = s * L + t;
+      g.add(blk(h->E, i), t == 1 ? Iw : blk(Y, i - 1), nullptr, blk(Y, i));
+    }
+    g.flush(sc, 1.0, 0.0);
+  }
+  const double** dtab = nullptr;
+  int* dstatus = nullptr;
+  BT_CUDA(cudaMallocAsync((void**)&dtab, std::max<size_t>(1, sc.tab.size()) * sizeof(double*), st));
+  BT_CUDA(cudaMallocAsync((void**)&dstatus, sizeof(int), st));
+  BT_CUDA(cudaMemsetAsync(dstatus, 0, sizeof(int), st));
+  BT_CUDA(cudaMemcpyAsync(dtab, sc.tab.data(), sc.tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  BT_TRY(run_schedule(sc, dtab, M, dstatus, st));
+  BT_CUDA(cudaStreamSynchronize(st));  // the host table goes out of scope
+  BT_CUDA(cudaFreeAsync(dtab, st));
+  BT_CUDA(cudaFreeAsync(dstatus, st));
+  BT_CUDA(cudaFreeAsync(Iw, st));
+  h->Y = Y;
   return BT_OK;
 }
 

@@ -48,6 +48,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <cstring>
 
@@ -928,7 +929,8 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 // [depth * S][Kp][M] so one thread reads and writes a contiguous row share.
 // ======================================================================
 struct IfJob {
-  int32_t a[2];      // work-panel block rows of the A operands (-1: absent)
+  int32_t a[2];      // block rows of the A operands (-1: absent)
+  int32_t a_src[2];  // 0: a[p] is a work-panel row, 1: a residual-panel row
   int32_t b[2];      // interface block index paired with a[p]
   int32_t add_r;     // r-panel block row added to the result (-1: none)
   int32_t sum_lev;   // series terms c[sum_lev][sum_lo..sum_hi] added (sum_lo > sum_hi: none)
@@ -940,7 +942,7 @@ struct IfJob {
 template <typename E, class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
     k_tc_ifgemm(const __grid_constant__ CUtensorMap tm_if, const __grid_constant__ CUtensorMap tm_w,
-                const IfJob* __restrict__ jobs, int job0, const E* __restrict__ rp, E* __restrict__ wp,
+                const __grid_constant__ CUtensorMap tm_r, const IfJob* __restrict__ jobs, int job0, const E* __restrict__ rp, E* __restrict__ wp,
                 float* __restrict__ cp, const float* __restrict__ sumbase, int N, int S, int nblk, int Kp,
                 const int* done, int* status) {
   static_assert(C::SW, "swapped roles only");
@@ -976,9 +978,10 @@ __global__ void __launch_bounds__(C::THREADS, 1)
       int k = 0;
       for (int p = 0; p < 2; ++p) {
         if (jb.a[p] < 0) continue;
+        const CUtensorMap* tm = jb.a_src[p] ? &tm_r : &tm_w;
         for (int pl = 0; pl < C::SP; ++pl)
           for (int c = 0; c < C::NCH; ++c)
-            tma_load_2d(sT + k * C::PT + pl * C::TILE + c * C::TCH, &tm_w, c * C::CE,
+            tma_load_2d(sT + k * C::PT + pl * C::TILE + c * C::TCH, tm, c * C::CE,
                         pl * pplane + jb.a[p] * Kp + n0, &b.extra[0]);
         ++k;
       }
@@ -1308,6 +1311,438 @@ __global__ void __launch_bounds__(C::THREADS, 1)
   if (warp == 1) tmem_dealloc(tmem, TCOLS);
 }
 
+// ======================================================================
+// Forward / backward stage 2 for unit stencils (A_i = B_i = I, symmetric P),
+// split BF16, swapped roles, M = 128.  The correction of step 2.3 folds into
+// a backward pass that forms X directly once the interface values are known:
+//   forward  (k_tc_fwd):  y_i = Dinv_i (r_i + y_{i-1})            -> work panel row i
+//                         W_a = sum_i Z_i r_i, Z_i = U_i^T        -> residual panel row a
+//   step 2.2 (unchanged but F~ reads W_a from the residual panel; W_b = y_b)
+//   backward (k_tc_bwd):  X_i = y_i + Y_i X~_s + G_i X_{i+1},  X_{b+1} = X~_{s+1}
+// (a..b: a segment's interior rows).  Z_i is block row a of the interior's
+// inverse: U_i = [P_II^-1]_{i,a} (A_a = I) and P_II is symmetric.  Y_i =
+// E_i Y_{i-1}, Y_a = E_a, is the forward response to the left interface
+// value.  In exact arithmetic X equals eq. superposition's W + U X~_s + V
+// X~_{s+1}; the panel traffic per solve drops from 24 to 16 bytes per
+// unknown (no W panel written and read back, no separate correction pass).
+// Factor set [2 planes][4][N][M][M]: Dinv, G, Z, Y (FB_*).
+// ======================================================================
+enum { FB_DINV = 0, FB_G = 1, FB_Z = 2, FB_Y = 3 };
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+    k_tc_fwd(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_r,
+             const __grid_constant__ CUtensorMap tm_w, int N, int L, int Kp, const int* done, int* status) {
+  using E = __nv_bfloat16;
+  static_assert(C::SW && C::SP == 2 && C::M == 128 && C::YB == 1, "split BF16, M = 128, swapped roles");
+  constexpr int TCOLS = 4 * C::M;  // two row accumulators, the W_a accumulator (and a spare region)
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;
+  uint8_t* sP = sA + C::NA * C::SLOT;
+  uint8_t* sY = sP + C::NP * C::PT;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + C::PT);
+  const Bars b = carve<C>(barmem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP));
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const int s = blockIdx.y;
+  const int a = s * L + 1;   // first interior row
+  const int nrow = L - 1;    // interior rows (>= 1)
+  const int fplane = 4 * N * C::M;
+  const int pplane = N * Kp;
+  const uint32_t zacc = 2 * C::ACC;  // TMEM columns of the W_a accumulator
+  if (threadIdx.x == 0) init_bars<C>(b);
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tm_fac);
+      prefetch_tmap(&tm_r);
+      prefetch_tmap(&tm_w);
+      uint32_t ai = 0, pi = 0;
+      bool ok = true;
+      for (int t = 0; t < nrow && ok; ++t) {
+        const int i = a + t;
+        ok = load_tile<C>(sP, b, pi, &tm_r, i * Kp + n0, pplane);
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FB_DINV * N + i) * C::M, fplane);
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FB_Z * N + i) * C::M, fplane);
+      }
+      if (!ok) atomicExch(status, 11);
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = ai - 1 - q;
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+      for (uint32_t q = 0; q < C::NP && q < pi; ++q) {
+        const uint32_t last = pi - 1 - q;
+        mbar_wait(&b.fullP[last % C::NP], (last / C::NP) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t ai = 0, pi = 0;
+      bool ok = true, zfirst = true;
+      for (int t = 0; t < nrow && ok; ++t) {
+        const int bsel = t & 1;
+        const uint32_t dt = tmem + bsel * C::ACC;
+        if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
+        tc_fence_after();
+        const uint32_t pslot = pi % C::NP;
+        if (ok) ok = mbar_wait(&b.fullP[pslot], (pi / C::NP) & 1);
+        tc_fence_after();
+        const uint32_t ptile = smem_u32(sP + pslot * C::PT);
+        bool first = true;
+        // Dinv_i r_i (+ Dinv_i y_{i-1}): each Dinv slice serves both products
+        const uint32_t ai0 = ai;
+        for (int c = 0; c < C::NCH && ok; ++c) {
+          const uint32_t q = ai0 + c, slot = q % C::NA;
+          ok = mbar_wait(&b.fullA[slot], (q / C::NA) & 1);
+          tc_fence_after();
+          if (ok) mma_chunk<E, C>(dt, smem_u32(sA + slot * C::SLOT), ptile, c, first);
+        }
+        if (ok && t > 0) {
+          ok = mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
+          tc_fence_after();
+          for (int c = 0; c < C::NCH && ok; ++c)
+            mma_chunk<E, C>(dt, smem_u32(sA + ((ai0 + c) % C::NA) * C::SLOT), smem_u32(sY), c, first);
+        }
+        if (!ok) break;
+        for (int c = 0; c < C::NCH; ++c) mma_commit(&b.emptyA[(ai0 + c) % C::NA]);
+        mma_commit(&b.mdone[bsel]);
+        ai = ai0 + C::NCH;
+        // Z_i r_i into the W_a accumulator (off the recurrence's critical path)
+        for (int c = 0; c < C::NCH && ok; ++c) {
+          const uint32_t slot = ai % C::NA;
+          ok = mbar_wait(&b.fullA[slot], (ai / C::NA) & 1);
+          tc_fence_after();
+          if (ok) {
+            mma_chunk<E, C>(tmem + zacc, smem_u32(sA + slot * C::SLOT), ptile, c, zfirst);
+            mma_commit(&b.emptyA[slot]);
+          }
+          ++ai;
+        }
+        if (ok) {
+          mma_commit(&b.emptyP[pslot]);
+          ++pi;
+        }
+      }
+      if (ok) mma_commit(&b.extra[0]);  // the W_a accumulator is complete
+      if (!ok) atomicExch(status, 12);
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    constexpr int ET_THREADS = 128 * C::EG;
+    const int n = 32 * (warp & 3) + lane;
+    const int m0 = ((warp - 2) / 4) * C::MH;
+    const bool leader = (warp == 2 && lane == 0);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    bool ok = true;
+    for (int t = 0; t < nrow; ++t) {
+      const int i = a + t;
+      const int bsel = t & 1;
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      float v[C::MH];
+      if (ok) {
+        tmem_cols<C::MH>(tmem + lane_base + bsel * C::ACC + m0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      // one y buffer: the previous row's store must have read it
+      if (leader) tma_store_wait_read<0>();
+      named_bar_sync(1, ET_THREADS);
+      if (ok) row_put<E, C>(sY, n, m0, v);
+      fence_proxy_async_smem();
+      named_bar_sync(1, ET_THREADS);
+      if (leader && ok) {
+        mbar_arrive(&b.yrdy[bsel]);
+        for (int p = 0; p < C::SP; ++p)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_store_2d(&tm_w, c * C::CE, p * pplane + i * Kp + n0, sY + p * C::TILE + c * C::TCH);
+        tma_store_commit();
+      }
+    }
+    // W_a = sum_i Z_i r_i -> residual panel row a
+    if (ok) ok = mbar_wait(&b.extra[0], 0);
+    ok = __all_sync(0xffffffffu, ok);
+    tc_fence_after();
+    float v[C::MH];
+    if (ok) {
+      tmem_cols<C::MH>(tmem + lane_base + zacc + m0, v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+    }
+    tc_fence_before();
+    if (leader) tma_store_wait_read<0>();
+    named_bar_sync(1, ET_THREADS);
+    if (ok) row_put<E, C>(sY, n, m0, v);
+    fence_proxy_async_smem();
+    named_bar_sync(1, ET_THREADS);
+    if (leader && ok) {
+      for (int p = 0; p < C::SP; ++p)
+        for (int c = 0; c < C::NCH; ++c)
+          tma_store_2d(&tm_r, c * C::CE, p * pplane + a * Kp + n0, sY + p * C::TILE + c * C::TCH);
+      tma_store_commit();
+    }
+    if (leader) tma_store_wait<0>();
+    if (!ok && leader) atomicExch(status, 13);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
+// Backward pass: X_i = y_i + Y_i X~_s + G_i X_{i+1} for i = b..a with
+// X_{b+1} = X~_{s+1} (zero for the last segment).  X~_s lives in TMEM as the A
+// operand of every Y product; the recurrence operand X_{i+1} is a shared-
+// memory tile (X~_{s+1} by TMA for the first row, then each row written by
+// the epilogue); y_i comes through the panel ring and is added in the
+// epilogue.  Each X_i goes to the row-major FP32 panel Drow ([N][M][K]), the
+// interface row k_s takes X~_s.
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+    k_tc_bwd(const __grid_constant__ CUtensorMap tm_fac, const __grid_constant__ CUtensorMap tm_w,
+             const __nv_bfloat16* __restrict__ wp, float* __restrict__ Drow, int K, int N, int L, int S, int Kp,
+             const int* done, int* status) {
+  using E = __nv_bfloat16;
+  static_assert(C::SW && C::SP == 2 && C::M == 128 && C::MH == 64, "split BF16, M = 128, swapped roles");
+  constexpr int TCOLS = 4 * C::M;
+  if (flag_set(done)) return;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = sm;
+  uint8_t* sP = sA + C::NA * C::SLOT;
+  uint8_t* sY = sP + C::NP * C::PT;
+  uint64_t* barmem = reinterpret_cast<uint64_t*>(sY + C::PT);
+  const Bars b = carve<C>(barmem);
+  // beyond the common set: X~_s stored into TMEM by every epilogue warp
+  uint64_t* a_rdy = barmem + kBars(C::NA, C::NP);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(barmem + kBars(C::NA, C::NP) + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * C::NT;
+  const int s = blockIdx.y;
+  const bool has_next = s + 1 < S;
+  const int a = s * L + 1, nrow = L - 1;
+  const int bl = a + nrow - 1;  // last interior row
+  const int fplane = 4 * N * C::M;
+  const int pplane = N * Kp;
+  auto acol = [](int pl) { return (uint32_t)(2 * C::M + pl * (C::M / 2)); };
+  if (threadIdx.x == 0) {
+    init_bars<C>(b);
+    mbar_init(a_rdy, 4 * C::EG);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tslot, TCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tmap(&tm_fac);
+      prefetch_tmap(&tm_w);
+      bool ok = true;
+      if (has_next) {  // X~_{s+1}: the first recurrence operand
+        mbar_arrive_expect_tx(&b.extra[0], C::PT);
+        for (int p = 0; p < C::SP; ++p)
+          for (int c = 0; c < C::NCH; ++c)
+            tma_load_2d(sY + p * C::TILE + c * C::TCH, &tm_w, c * C::CE, p * pplane + (s + 1) * L * Kp + n0,
+                        &b.extra[0]);
+      }
+      uint32_t ai = 0, pi = 0;
+      for (int t = 0; t < nrow && ok; ++t) {
+        const int i = bl - t;
+        ok = load_tile<C>(sP, b, pi, &tm_w, i * Kp + n0, pplane);
+        for (int c = 0; c < C::NCH && ok; ++c)
+          ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FB_Y * N + i) * C::M, fplane);
+        if (t > 0 || has_next)
+          for (int c = 0; c < C::NCH && ok; ++c)
+            ok = load_slice<C>(sA, b, ai, &tm_fac, c * C::CE, (FB_G * N + i) * C::M, fplane);
+      }
+      if (!ok) atomicExch(status, 14);
+      if (has_next) mbar_wait(&b.extra[0], 0);
+      for (uint32_t q = 0; q < C::NA && q < ai; ++q) {
+        const uint32_t last = ai - 1 - q;
+        mbar_wait(&b.fullA[last % C::NA], (last / C::NA) & 1);
+      }
+      for (uint32_t q = 0; q < C::NP && q < pi; ++q) {
+        const uint32_t last = pi - 1 - q;
+        mbar_wait(&b.fullP[last % C::NP], (last / C::NP) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(a_rdy, 0);
+      tc_fence_after();
+      uint32_t ai = 0;
+      for (int t = 0; t < nrow && ok; ++t) {
+        const int bsel = t & 1;
+        const uint32_t dt = tmem + bsel * C::ACC;
+        if (t >= 2) ok = mbar_wait(&b.afree[bsel], ((t >> 1) - 1) & 1);
+        tc_fence_after();
+        bool first = true;
+        // Y_i X~_s: X~_s from TMEM (two BF16 values per 32-bit column)
+        for (int c = 0; c < C::NCH && ok; ++c) {
+          const uint32_t slot = ai % C::NA;
+          ok = mbar_wait(&b.fullA[slot], (ai / C::NA) & 1);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t fb = smem_u32(sA + slot * C::SLOT);
+#pragma unroll
+          for (int kq = 0; kq < C::CE / C::KS; ++kq) {
+            const uint32_t kc = (uint32_t)(c * (C::CE / C::KS) + kq) * (C::KS / 2);
+            const uint32_t ahi = tmem + acol(0) + kc, alo = tmem + acol(1) + kc;
+            const uint64_t bhi = smem_desc(fb + kq * 32, 16, 1024);
+            const uint64_t blo = smem_desc(fb + C::SLICE + kq * 32, 16, 1024);
+            mma_f16_ta(dt, ahi, bhi, C::IDESC, first ? 0u : 1u);
+            first = false;
+            mma_f16_ta(dt, alo, bhi, C::IDESC, 1u);
+            mma_f16_ta(dt, ahi, blo, C::IDESC, 1u);
+          }
+          mma_commit(&b.emptyA[slot]);
+          ++ai;
+        }
+        // G_i X_{i+1}: the recurrence operand in shared memory
+        if (ok && (t > 0 || has_next)) {
+          ok = t == 0 ? mbar_wait(&b.extra[0], 0) : mbar_wait(&b.yrdy[(t - 1) & 1], ((t - 1) >> 1) & 1);
+          tc_fence_after();
+          if (ok) ok = mma_block<E, C>(sA, b, ai, dt, smem_u32(sY), first);
+        }
+        if (ok) mma_commit(&b.mdone[bsel]);
+      }
+      if (!ok) atomicExch(status, 15);
+      mma_commit(&b.extra[1]);
+      mbar_wait(&b.extra[1], 0);
+    }
+  } else {
+    constexpr int ET_THREADS = 128 * C::EG;
+    constexpr int per16 = 8;           // bf16 per 16 bytes
+    constexpr int NU = C::MH / per16;  // 16-byte units of one plane of a row share
+    const int nl = 32 * (warp & 3) + lane;
+    const int g = (warp - 2) / 4;
+    const int m0 = g * C::MH;
+    const bool leader = (warp == 2 && lane == 0);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const size_t wplane = (size_t)N * Kp * C::M;
+    const int n = n0 + nl;
+    auto store_row = [&](const float (&v)[C::MH], int irow) {
+      if (n < K) {
+        float* x = Drow + ((size_t)irow * C::M + m0) * K + n;
+#pragma unroll
+        for (int q0 = 0; q0 < C::MH; q0 += 16) {
+#pragma unroll
+          for (int q = q0; q < q0 + 16; ++q) x[(size_t)q * K] = v[q];
+          asm volatile("" ::: "memory");  // one batch of stores at a time
+        }
+      }
+    };
+    {  // X~_s into TMEM (the A operand of the Y products); d_{k_s} = X~_s
+      const uint4* src = reinterpret_cast<const uint4*>(wp + ((size_t)s * L * Kp + n0 + nl) * C::M + m0);
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const uint4 h4 = __ldg(src + u);
+        const uint4 l4 = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const E*>(src) + wplane) + u);
+        hi[4 * u] = h4.x; hi[4 * u + 1] = h4.y; hi[4 * u + 2] = h4.z; hi[4 * u + 3] = h4.w;
+        lo[4 * u] = l4.x; lo[4 * u + 1] = l4.y; lo[4 * u + 2] = l4.z; lo[4 * u + 3] = l4.w;
+      }
+      tmem_st32(tmem + lane_base + acol(0) + g * (C::MH / 2), hi);
+      tmem_st32(tmem + lane_base + acol(1) + g * (C::MH / 2), lo);
+      float v[C::MH];
+#pragma unroll
+      for (int e = 0; e < C::MH; ++e) v[e] = 0.f;
+#pragma unroll
+      for (int u = 0; u < NU; ++u)
+        unpack16_add<E, 2>(make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]),
+                           make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]), &v[u * per16]);
+      store_row(v, s * L);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(a_rdy);
+    bool ok = true;
+    uint32_t pe = 0;
+    for (int t = 0; t < nrow; ++t) {
+      const int i = bl - t;
+      const int bsel = t & 1;
+      if (ok) ok = mbar_wait(&b.mdone[bsel], (t >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      float v[C::MH];
+      if (ok) {
+        tmem_cols<C::MH>(tmem + lane_base + bsel * C::ACC + m0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < C::MH; ++q) v[q] = 0.f;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&b.afree[bsel]);
+      const uint32_t ps = pe % C::NP;
+      if (ok) ok = mbar_wait(&b.fullP[ps], (pe / C::NP) & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok) row_add<E, C>(sP + ps * C::PT, nl, m0, v);  // + y_i
+      // the MMAs of this row (the last readers of sY) have completed: mdone
+      named_bar_sync(1, ET_THREADS);
+      if (ok && leader) mbar_arrive(&b.emptyP[ps]);
+      ++pe;
+      if (ok) row_put<E, C>(sY, nl, m0, v);  // X_i: the next row's recurrence operand
+      fence_proxy_async_smem();
+      named_bar_sync(1, ET_THREADS);
+      if (ok && leader) mbar_arrive(&b.yrdy[bsel]);
+      if (ok) store_row(v, i);
+    }
+    if (!ok && leader) atomicExch(status, 16);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
+// Split-BF16 copies of Dinv, G, Z = U^T and Y, [2][4][N][M][M].
+__global__ void k_cast_fb(const double* __restrict__ D, const double* __restrict__ G, const double* __restrict__ U,
+                          const double* __restrict__ Y, __nv_bfloat16* __restrict__ out, size_t nb, int M) {
+  const size_t n = 4 * nb, MM = (size_t)M * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t w = e / nb, o = e % nb;
+    double x;
+    if (w == FB_Z) {  // element (m, k) of Z_i is element (k, m) of U_i
+      const size_t blk = o / MM, r = o % MM;
+      x = U[blk * MM + (r % M) * M + r / M];
+    } else {
+      x = (w == FB_DINV ? D : w == FB_G ? G : Y)[o];
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    out[e] = hi;
+    out[e + n] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+  }
+}
+
 // X (+)= d: the block-transposed FP32 correction panel into the caller's
 // row-major FP64 solution, one warp per (block row j, 8 rows m, 32 columns n): lane n
 // reads its 8 FP32 corrections (32 contiguous bytes of the block-transposed
@@ -1620,6 +2055,7 @@ bt_status make_tc_interface(bt_handle_s* h, cudaStream_t st) {
   auto blank = [] {
     IfJob j;
     j.a[0] = j.a[1] = -1;
+    j.a_src[0] = j.a_src[1] = 0;
     j.b[0] = j.b[1] = 0;
     j.add_r = -1;
     j.sum_lev = 0;
@@ -1674,6 +2110,14 @@ bt_status make_tc_interface(bt_handle_s* h, cudaStream_t st) {
     }
     h->if_off.push_back((int)jobs.size());
   }
+  // F~ of the forward / backward stage 2: W_{k_s + 1} is the residual panel's
+  // row k_s + 1 (k_tc_fwd leaves it there), W_{k_s - 1} = y of the last row
+  for (int s = 0; s < S; ++s) {
+    IfJob j = jobs[h->if_off[0] + s];
+    if (j.a[1] >= 0) j.a_src[1] = 1;
+    jobs.push_back(j);
+  }
+  h->if_off.push_back((int)jobs.size());
   BT_TRY(h->arena.alloc(&h->if_jobs, jobs.size() * sizeof(IfJob)));
   BT_CUDA(cudaMemcpyAsync(h->if_jobs, jobs.data(), jobs.size() * sizeof(IfJob), cudaMemcpyHostToDevice, st));
   BT_CUDA(cudaStreamSynchronize(st));  // the host vector goes out of scope
@@ -1687,15 +2131,18 @@ size_t ifgemm_smem() {
 }
 
 // Step 2.2 on the tensor cores (split BF16): F~, series terms, then one launch per level.
+// fb: the forward / backward stage 2 (F~ reads W_{k_s+1} from the residual panel).
 template <class CI>
-bt_status run_interface_tc(bt_handle_s* h, const TcBuffers& tb, const int* done, int* status, cudaStream_t st) {
+bt_status run_interface_tc(bt_handle_s* h, const TcBuffers& tb, const int* done, int* status, cudaStream_t st,
+                           bool fb = false) {
   using E = __nv_bfloat16;
   const int M = CI::M, N = (int)h->N, S = (int)h->S, Kp = (int)tb.Kp;
   BT_TRY(make_tc_interface(h, st));
   const int nblk = (4 + h->depth) * S;
-  CUtensorMap tm_if, tm_w;
+  CUtensorMap tm_if, tm_w, tm_r;
   BT_TRY(make_map(&tm_if, h->tc_if_bf16x3, ET<E>::dt, CI::eb, (uint64_t)M, (uint64_t)CI::SP * nblk * M, CI::CE, M));
   BT_TRY(make_map(&tm_w, tb.w, ET<E>::dt, CI::eb, (uint64_t)M, (uint64_t)CI::SP * N * Kp, CI::CE, CI::NT));
+  BT_TRY(make_map(&tm_r, tb.r, ET<E>::dt, CI::eb, (uint64_t)M, (uint64_t)CI::SP * N * Kp, CI::CE, CI::NT));
   const size_t smem = ifgemm_smem<CI>();
   BT_CUDA(cudaFuncSetAttribute(k_tc_ifgemm<E, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const IfJob* jobs = reinterpret_cast<const IfJob*>(h->if_jobs);
@@ -1709,12 +2156,12 @@ bt_status run_interface_tc(bt_handle_s* h, const TcBuffers& tb, const int* done,
     const int j0 = h->if_off[g], nj = h->if_off[g + 1] - j0;
     if (nj <= 0) return BT_OK;
     ProfScope ps(h, st, name);
-    k_tc_ifgemm<E, CI><<<dim3(Kp / CI::NT, nj), CI::THREADS, smem, st>>>(tm_if, tm_w, jobs, j0, r, w, tb.c, sums,
-                                                                        N, S, nblk, Kp, done, status);
+    k_tc_ifgemm<E, CI><<<dim3(Kp / CI::NT, nj), CI::THREADS, smem, st>>>(tm_if, tm_w, tm_r, jobs, j0, r, w, tb.c,
+                                                                        sums, N, S, nblk, Kp, done, status);
     BT_CUDA(cudaGetLastError());
     return BT_OK;
   };
-  BT_TRY(launch(0, "tc_iface", tb.c));
+  BT_TRY(launch(fb ? 2 + h->depth : 0, "tc_iface", tb.c));
   BT_TRY(launch(1, "tc_iface", tb.c));
   {
     ProfScope ps(h, st, "tc_dichotomy");
@@ -1754,6 +2201,32 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
   BT_TRY(make_map(&tm_d, tb.d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (uint64_t)M, (uint64_t)N * Kp, 32, CC::NT));
   const E* r = reinterpret_cast<const E*>(tb.r);
   E* w = reinterpret_cast<E*>(tb.w);
+  // unit stencils, split BF16, M = 128, results into a row-major FP32 panel:
+  // forward pass, step 2.2, backward pass (no correction kernel)
+  if constexpr (CS::SW && SP == 2 && M == 128 && std::is_same<E, __nv_bfloat16>::value) {
+    if (accumulate == 2 && tb.drow != nullptr && h->stencil_unit && L > 1 && h->tc_fac_fb != nullptr) {
+      using CF = CS;
+      CUtensorMap tm_fb;
+      BT_TRY(make_map(&tm_fb, h->tc_fac_fb, ET<E>::dt, CF::eb, (uint64_t)M, (uint64_t)SP * 4 * N * M, CF::CE, M));
+      const size_t smem = 1024 + CF::NA * CF::SLOT + (CF::NP + 1) * CF::PT + (kBars(CF::NA, CF::NP) + 1) * 8 + 16;
+      {
+        BT_CUDA(cudaFuncSetAttribute(k_tc_fwd<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope ps(h, st, "tc_sweep");
+        k_tc_fwd<CF><<<dim3(Kp / CF::NT, S), CF::THREADS, smem, st>>>(tm_fb, tm_r, tm_w, N, L, Kp, done, status);
+        BT_CUDA(cudaGetLastError());
+      }
+      using CI = Cfg<E, CS::M, 128, 3, 2, 1, true>;
+      BT_TRY(run_interface_tc<CI>(h, tb, done, status, st, true));
+      {
+        BT_CUDA(cudaFuncSetAttribute(k_tc_bwd<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope ps(h, st, "tc_correct");
+        k_tc_bwd<CF><<<dim3(Kp / CF::NT, S), CF::THREADS, smem, st>>>(tm_fb, tm_w, (const E*)w, tb.drow, (int)K, N,
+                                                                      L, S, Kp, done, status);
+        BT_CUDA(cudaGetLastError());
+      }
+      return BT_OK;
+    }
+  }
   // step 2.1
   if (L > 1) {
     const size_t smem = sweep_smem<CS>();
@@ -1879,6 +2352,16 @@ bt_status make_f32t_factors(bt_handle_s* h, cudaStream_t st) {
 
 bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
   BT_TRY(make_f32t_factors(h, st));
+  if (precision == BT_PREC_BF16X3 && h->M == 128 && h->stencil_unit && h->L > 1 && !h->tc_fac_fb) {
+    // Dinv, G, Z = U^T, Y for the forward / backward stage 2 of unit stencils
+    BT_TRY(factor_left_responses(h, st));
+    const size_t nb = (size_t)h->N * h->M * h->M;
+    void* buf = nullptr;
+    BT_TRY(h->arena.alloc(&buf, (size_t)2 * 4 * nb * sizeof(__nv_bfloat16)));
+    k_cast_fb<<<1024, 256, 0, st>>>(h->Dinv, h->G, h->U, h->Y, reinterpret_cast<__nv_bfloat16*>(buf), nb, (int)h->M);
+    BT_CUDA(cudaGetLastError());
+    h->tc_fac_fb = buf;
+  }
   void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : precision == BT_PREC_TF32 ? &h->tc_fac_tf32 : &h->tc_fac_bf16x3;
   if (*slot) return BT_OK;
   const size_t nb = (size_t)h->N * h->M * h->M;

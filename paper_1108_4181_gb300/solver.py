@@ -160,9 +160,9 @@ class Factorization:
         return dict(A=(int(q[0]), int(q[1])), B=(int(q[2]), int(q[3])), n=int(q[4]))
 
     def export(self, what: str) -> torch.Tensor:
-        """FP64 factor arrays: 'U', 'V' ([N, M, M]) or 'At', 'Ct', 'Bt' ([S, M, M])."""
-        code = {"U": 0, "V": 1, "At": 2, "Ct": 3, "Bt": 4}[what]
-        n = self.N if code < 2 else self.S
+        """FP64 factor arrays: 'U', 'V', 'Y' ([N, M, M]) or 'At', 'Ct', 'Bt' ([S, M, M])."""
+        code = {"U": 0, "V": 1, "At": 2, "Ct": 3, "Bt": 4, "Y": 5}[what]
+        n = self.N if code in (0, 1, 5) else self.S
         dst = torch.empty((n, self.M, self.M), dtype=torch.float64, device=self.device)
         torch.cuda.synchronize(self.device)
         _lib.check(_lib.load().bt_factor_export(self._h, code, _ptr(dst)), "bt_factor_export")

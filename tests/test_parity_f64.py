@@ -204,3 +204,31 @@ def test_config4_matrix_fp64(bt):
     Xr = oracle.solve_block_thomas(A, B, C, F[:, :, cols])
     assert oracle.rel_err(X[:, :, cols], Xr) <= TOL
     assert oracle.col_err(X[:, :, cols], Xr) <= TOL
+
+
+def test_left_responses_export_matches_definition(bt):
+    # Y_i, the forward response of a segment interior to its left interface
+    # value (Y_a = E_a, Y_i = E_i Y_{i-1}), is the last block of the solution
+    # of the interior's leading principal subsystem (rows a..i) whose right-hand
+    # side is A_a in its first block: forward elimination of rows a..i alone.
+    N, M, S = 24, 5, 3
+    L = N // S
+    A, B, C = gen.dominant_blocks(N, M, seed=31)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        Y = fac.export("Y").cpu().numpy()
+    for s in range(S):
+        a = s * L + 1
+        assert np.all(Y[s * L] == 0.0)
+        for i in range(a, s * L + L):
+            n = i - a + 1
+            P = np.zeros((n * M, n * M))
+            for r in range(n):
+                P[r * M:(r + 1) * M, r * M:(r + 1) * M] = C[a + r]
+                if r > 0:
+                    P[r * M:(r + 1) * M, (r - 1) * M:r * M] = -A[a + r]
+                if r + 1 < n:
+                    P[r * M:(r + 1) * M, (r + 1) * M:(r + 2) * M] = -B[a + r]
+            rhs = np.zeros((n * M, M))
+            rhs[:M] = A[a]
+            ref = np.linalg.solve(P, rhs)[(n - 1) * M:]
+            np.testing.assert_allclose(Y[i], ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))

@@ -275,3 +275,31 @@ def test_graph_cache_evicts_beyond_its_capacity(bt):
         for X in outs:
             assert oracle.rel_err(X.cpu().numpy(), Xr) <= 1e-10
             assert oracle.col_err(X.cpu().numpy(), Xr) <= 1e-10
+
+
+@pytest.mark.parametrize("N,K,S", [
+    (64, 40, 8),     # several segments, one ragged column tile
+    (32, 130, 16),   # L = 2: one interior row per segment; two column tiles, the last ragged
+    (48, 5, 1),      # one segment: no right interface
+    (96, 300, 4),    # three column tiles
+])
+def test_tc_refined_unit_stencil_forward_backward(bt, N, K, S):
+    # unit stencil with split BF16 and M = 128: the forward pass accumulating
+    # W at each segment's first interior row, step 2.2, and the backward pass
+    # forming X from the interface values (no correction kernel)
+    M = 128
+    A, B, C = gen.acoustic_system(N, M)
+    F = gen.acoustic_rhs(N, M, K, seed=N + K)
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        assert fac.stencil == 1
+        X, info = fac.solve(_t(F), precision="bf16x3", tol=1e-12, return_info=True)
+        assert info["converged"], info
+        # the first solve alone (no refinement) carries the split-BF16 solve's accuracy
+        X0, info0 = fac.solve(_t(F), precision="bf16x3", tol=1.0, return_info=True)
+    X = X.cpu().numpy()
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, Xr) <= 1e-10
+    assert oracle.col_err(X, Xr) <= 1e-10
+    assert info0["iters"] == 0 and info0["rel_res0"] <= 1e-4
+    assert oracle.rel_err(X0.cpu().numpy(), Xr) <= 1e-3
