@@ -230,10 +230,24 @@ bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_
 
 /*
  * Batched solves (not in the paper): many right-hand-side sets, each against
- * its own factored matrix, solved in FP64 by ONE persistent cooperative
- * launch that runs stage 2 of Algorithm 2 for all of them -- sweeps,
- * interface terms, one stage per dichotomy level, corrections, separated by
- * grid-wide barriers -- and that is replayed from a CUDA graph.
+ * one of a few factored matrices, planned once and run as ONE CUDA graph
+ * launch.
+ *   - FP64 plans (opts->precision BT_PREC_F64): one persistent cooperative
+ *     launch runs stage 2 of Algorithm 2 for all sets -- sweeps, interface
+ *     terms, one stage per dichotomy level, corrections, separated by
+ *     grid-wide barriers.
+ *   - Refined plans (any other precision): stage 2 is linear in F and its
+ *     factors do not depend on F, so the sets of each matrix are packed side
+ *     by side into one panel and solved by ONE refined solve (bt_solve_ex) per
+ *     matrix; the matrices run on concurrent branches of the graph and every
+ *     refinement loop is a device-side WHILE node.  Set s is scaled by the
+ *     power of two 2^-e_s with 2^(e_s-1) <= ||F_s||_F < 2^e_s before packing
+ *     (exact), and the packed refinement runs until EVERY set meets
+ *     ||F_s - P X_s||_F <= tol ||F_s||_F on its own, as if solved alone
+ *     (each set's sum of squares is taken from the residual panel after
+ *     every pass, with a margin for the panel's rounding).  The packed panels
+ *     (2 N M sum(K) doubles per matrix) are
+ *     owned by the plan.
  *
  * bt_batch_create -- plans a batch of n >= 1 sets; set i solves
  *   P_{h[i]} X_i = F_i, F[i] and X[i] being device [N_i][M][K[i]] FP64 panels
@@ -241,25 +255,40 @@ bt_status bt_solve_adjoint(bt_handle h, const double* X, const double* G, int64_
  *   device memory owned by the caller that must keep their addresses while
  *   the plan is used (the plan records the pointers).  All handles live on the
  *   current device and share one block size M (N and S may differ).  No X[i]
- *   may overlap an F[j] or another X[j].  opts (may be NULL): precision must
- *   be BT_PREC_F64 (otherwise BT_ERR_UNSUPPORTED); k_tile = right-hand-side
- *   columns per work item (0 = automatic); stream is not used.  The plan owns
- *   its scratch (the sum over sets of depth*S*M*K[i] doubles) and its graph;
- *   the handles must outlive it.  Synchronous; BT_ERR_ARG on invalid input.
+ *   may overlap an F[j] or another X[j].  opts (may be NULL): precision,
+ *   tol, max_it and residual as for bt_solve_ex (refined plans; at most 1024
+ *   sets per matrix); k_tile = right-hand-side columns per work item of the
+ *   FP64 launch (0 = automatic); stream is not used.  The plan owns its
+ *   scratch and its graph; the handles must outlive it, and no other call may
+ *   use a handle of a refined plan while the plan runs (they share the
+ *   handle's refinement scratch).  Synchronous; BT_ERR_ARG on invalid input,
+ *   BT_ERR_UNSUPPORTED where bt_solve_ex would refuse the precision or
+ *   residual for a handle.
  * bt_batch_run -- enqueues one batched solve on `stream` (one graph launch).
+ *   A refined plan whose handles' refinement scratch was reallocated by a
+ *   later call with more columns is prepared and captured again first
+ *   (synchronous, allocating).
  * bt_batch_status -- waits for the plan's work and returns BT_OK, or
- *   BT_ERR_TIMEOUT if a grid-barrier wait of the last run gave up (20 s by
- *   default; see bt_batch_debug).  The device stays usable: the plan can be
- *   run again.
- * bt_batch_debug -- diagnostics for testing the failure path: limit_s sets
- *   the grid-barrier wait limit of later runs (0 = the 20 s default, at most
- *   60 s); skip_stage >= 0 plants a failure -- CTA 0 of the persistent launch
- *   leaves the kernel instead of arriving at the barrier after that stage, so
- *   the other CTAs' waits run out and the run reports BT_ERR_TIMEOUT; -1
- *   removes it.  Takes effect in graph replays too.  Synchronises the device.
- * bt_batch_query -- out[0] work items, out[1] stages, out[2] CTAs of the
- *   persistent launch, out[3] threads per CTA, out[4] columns per item,
- *   out[5] 1 when runs replay a CUDA graph.
+ *   BT_ERR_TIMEOUT if a bounded wait of the last run gave up (FP64: a
+ *   grid-barrier wait, 20 s by default, see bt_batch_debug; refined: a
+ *   tensor-core wait), or BT_ERR_NOCONV if a refined matrix group did not reach
+ *   its tolerance within max_it passes.  The device stays usable: the plan can
+ *   be run again.
+ * bt_batch_info -- after bt_batch_status: the refinement report of set i's
+ *   matrix group (iters, converged -- every set of the group met tol -- and
+ *   rel_res / rel_res0 of the packed, scaled panel as a whole); FP64 plans
+ *   report iters 0, converged 1, rel_res -1.
+ * bt_batch_debug -- diagnostics for testing the failure path of FP64 plans
+ *   (BT_ERR_UNSUPPORTED for refined plans): limit_s sets the grid-barrier wait
+ *   limit of later runs (0 = the 20 s default, at most 60 s); skip_stage >= 0
+ *   plants a failure -- CTA 0 of the persistent launch leaves the kernel
+ *   instead of arriving at the barrier after that stage, so the other CTAs'
+ *   waits run out and the run reports BT_ERR_TIMEOUT; -1 removes it.  Takes
+ *   effect in graph replays too.  Synchronises the device.
+ * bt_batch_query -- FP64 plans: out[0] work items, out[1] stages, out[2] CTAs
+ *   of the persistent launch, out[3] threads per CTA, out[4] columns per item;
+ *   refined plans: out[0] matrix groups (packed panels), out[1..3] 0, out[4]
+ *   the k_tile option; out[5] 1 when runs replay a CUDA graph.
  * bt_solve_batched -- create, run on opts->stream, wait, destroy.
  */
 typedef struct bt_batch_s* bt_batch;
@@ -268,6 +297,7 @@ bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F,
 bt_status bt_batch_run(bt_batch b, void* stream);
 bt_status bt_batch_status(bt_batch b);
 bt_status bt_batch_query(bt_batch b, int64_t out[6]);
+bt_status bt_batch_info(bt_batch b, int32_t i, bt_info* out);
 bt_status bt_batch_debug(bt_batch b, double limit_s, int32_t skip_stage);
 void bt_batch_destroy(bt_batch b);
 bt_status bt_solve_batched(int32_t n, const bt_handle* h, const double* const* F, const int64_t* K,

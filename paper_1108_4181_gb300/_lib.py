@@ -74,6 +74,7 @@ SIGNATURES = {
     "bt_batch_run": (ctypes.c_int, [_vp, _vp]),
     "bt_batch_status": (ctypes.c_int, [_vp]),
     "bt_batch_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "bt_batch_info": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(BtInfo)]),
     "bt_batch_debug": (ctypes.c_int, [_vp, ctypes.c_double, _i32]),
     "bt_batch_destroy": (None, [_vp]),
     "bt_solve_batched": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i64),

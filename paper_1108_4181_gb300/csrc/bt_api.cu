@@ -460,6 +460,7 @@ static void destroy_batch(bt_batch_s* b) {
   cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  rbatch_release(b);
   b->arena.release();
   cudaSetDevice(prev);
   delete b;
@@ -485,9 +486,13 @@ bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F,
   bt_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  if (o.precision != BT_PREC_F64) {
-    set_error("bt_batch_create: batched solves run in FP64 only (precision BT_PREC_F64)");
-    return BT_ERR_UNSUPPORTED;
+  if (o.precision < 0 || o.precision > 4) {
+    set_error("bt_batch_create: unknown precision");
+    return BT_ERR_ARG;
+  }
+  if (o.residual < 0 || o.residual > 3) {
+    set_error("bt_batch_create: unknown residual method");
+    return BT_ERR_ARG;
   }
   if (o.k_tile < 0) {
     set_error("bt_batch_create: k_tile must be >= 0");
@@ -524,6 +529,15 @@ bt_status bt_batch_create(int32_t n, const bt_handle* h, const double* const* F,
   b->device = dev;
   b->n = n;
   b->precision = o.precision;
+  if (o.precision != BT_PREC_F64) {
+    const bt_status rs = rbatch_build(b, n, h, F, K, X, o);
+    if (rs != BT_OK) {
+      destroy_batch(b);
+      return rs;
+    }
+    *out = b;
+    return BT_OK;
+  }
   bt_status st = batch_build(b, n, h, F, K, X, o);
   if (st == BT_OK) {
     // capture one run into a CUDA graph on a private stream
@@ -561,6 +575,7 @@ bt_status bt_batch_run(bt_batch b, void* stream) {
     set_error("bt_batch_run: NULL plan");
     return BT_ERR_ARG;
   }
+  if (b->refined) return rbatch_run(b, (cudaStream_t)stream);
   if (b->exec) {
     BT_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
     return BT_OK;
@@ -574,6 +589,7 @@ bt_status bt_batch_status(bt_batch b) {
     return BT_ERR_ARG;
   }
   BT_CUDA(cudaDeviceSynchronize());
+  if (b->refined) return rbatch_status(b);
   int code = 0;
   BT_CUDA(cudaMemcpy(&code, reinterpret_cast<int*>(b->d_ctl) + 2, sizeof(int), cudaMemcpyDeviceToHost));
   if (code != 0) {
@@ -588,6 +604,10 @@ bt_status bt_batch_debug(bt_batch b, double limit_s, int32_t skip_stage) {
     set_error("bt_batch_debug: need a plan, 0 <= limit_s <= 60 and skip_stage >= -1");
     return BT_ERR_ARG;
   }
+  if (b->refined) {
+    set_error("bt_batch_debug: refined plans have no grid barrier");
+    return BT_ERR_UNSUPPORTED;
+  }
   return batch_set_debug(b, (unsigned long long)(limit_s * 1e9), skip_stage);
 }
 
@@ -596,12 +616,38 @@ bt_status bt_batch_query(bt_batch b, int64_t out[6]) {
     set_error("bt_batch_query: NULL argument");
     return BT_ERR_ARG;
   }
-  out[0] = b->n_items;
-  out[1] = b->n_stages;
-  out[2] = b->grid;
-  out[3] = b->threads;
-  out[4] = b->k_tile;
+  if (b->refined) {
+    out[0] = (int64_t)b->groups.size();
+    out[1] = out[2] = out[3] = 0;
+    out[4] = b->ropts.k_tile;
+  } else {
+    out[0] = b->n_items;
+    out[1] = b->n_stages;
+    out[2] = b->grid;
+    out[3] = b->threads;
+    out[4] = b->k_tile;
+  }
   out[5] = b->exec ? 1 : 0;
+  return BT_OK;
+}
+
+bt_status bt_batch_info(bt_batch b, int32_t i, bt_info* out) {
+  if (!b || !out || i < 0 || i >= b->n) {
+    set_error("bt_batch_info: need a plan, 0 <= i < n and an output");
+    return BT_ERR_ARG;
+  }
+  if (!b->refined) {
+    out->iters = 0;
+    out->converged = 1;
+    out->rel_res = -1.0;
+    out->rel_res0 = -1.0;
+    return BT_OK;
+  }
+  if (!b->infos_ready) {
+    set_error("bt_batch_info: call bt_batch_status after the run first");
+    return BT_ERR_ARG;
+  }
+  *out = b->infos[(size_t)b->set_group[(size_t)i]];
   return BT_OK;
 }
 

@@ -243,6 +243,36 @@ struct bt_batch_s {
   const void* kernel = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+
+  // Refined plans (a precision other than FP64; batch_refined.cu): the sets of
+  // each matrix packed into one panel, one refined solve per matrix, all in
+  // one CUDA graph.
+  struct RGroup {
+    bt_handle_s* h = nullptr;
+    std::vector<int> members;   // set indices, in packing order
+    int nsets = 0, first = 0;   // first: index of its first set in d_norm2
+    int64_t K = 0;              // packed columns
+    double* F = nullptr;        // packed panels [N][M][K]
+    double* X = nullptr;
+    void* d_sets = nullptr;     // per-set table
+    void* d_blk = nullptr;      // CTAs of the norm launch
+    int* d_colset = nullptr;    // set of each packed column
+    double* d_colssq = nullptr; // per-column sums of squares of the residual (scratch)
+    int64_t nblk = 0;
+    int gen = -1;               // the handle's buffer generation when captured
+    cudaStream_t q = nullptr;   // the group's branch of the graph
+    cudaEvent_t fork = nullptr, join = nullptr;
+  };
+  bool refined = false;
+  bt_opts ropts{};
+  std::vector<RGroup> groups;
+  std::vector<int> set_group;
+  double* d_norm2 = nullptr;    // ||F_s||_F^2 per set
+  void* d_state = nullptr;      // each group's refinement state after a run
+  int pack_grid = 0;
+  cudaStream_t rcap = nullptr;
+  std::vector<bt_info> infos;   // per group, filled by bt_batch_status
+  bool infos_ready = false;
 };
 
 namespace bt {
@@ -335,6 +365,15 @@ bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
 // failure (a stage index, or -1); synchronous.
 bt_status batch_set_debug(bt_batch_s* b, unsigned long long limit_ns, int skip_stage);
 
+// Refined batches (batch_refined.cu): build (groups, packing tables, prepared
+// refinements, the captured graph), run (re-captured first if a handle's
+// refinement buffers moved), status (per-group convergence), release.
+bt_status rbatch_build(bt_batch_s* b, int32_t n, const bt_handle* hs, const double* const* F, const int64_t* K,
+                       double* const* X, const bt_opts& o);
+bt_status rbatch_run(bt_batch_s* b, cudaStream_t st);
+bt_status rbatch_status(bt_batch_s* b);
+void rbatch_release(bt_batch_s* b);
+
 // The FP32 double-word residual (refine.cu) applies: a unit stencil with M % 8 == 0.
 bool resid_dw_supported(const bt_handle_s* h);
 
@@ -356,8 +395,30 @@ bt_status launch_resid_digits(bt_handle_s* h, const double* F, const double* X, 
 bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_t K, double* R, int method,
                         double* norm2, cudaStream_t st);
 
-// Mixed-precision solve with iterative refinement (bt_solve_ex).
-bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info);
+// Mixed-precision solve with iterative refinement (bt_solve_ex).  how: 0 run
+// (a CUDA graph per argument key, replayed on repeated calls); 1 prepare:
+// grow the scratch, build the factor copies, and run the refinement once
+// directly on F and X, which builds what the launches build lazily
+// (synchronous; no capture may be in progress); 2 record the whole refinement
+// into the capture in progress on `rec` (after a `how = 1` call with the same
+// K and options; allocates nothing).
+// sc (refined batches): the K columns form nsets column sets (colset[c]);
+// the refinement then converges when EVERY set s meets
+// ||F_s - P X_s||_F <= tol ||F_s||_F, F_s the set's columns scaled by the
+// power of two that brings ||F_s||_F into [1/2, 1) (n2[s] = ||F_s||_F^2
+// before scaling); colssq: K doubles of zeroed scratch.
+struct SetCheck {
+  int nsets;
+  const int* colset;
+  const double* n2;
+  double* colssq;
+};
+bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info,
+                        int how = 0, cudaStream_t rec = nullptr, const SetCheck* sc = nullptr);
+// Bytes of a handle's refinement state, and the bt_info it reports (returns
+// the tensor-core status word: non-zero when a bounded wait gave up).
+size_t refine_state_bytes();
+int refine_state_info(const void* state, bt_info* info);
 
 // Band storage -> block arrays A, B, C of N block rows (band.cu).
 bt_status band_to_blocks(const double* ab, int64_t n, int64_t kl, int64_t ku, int64_t N, int64_t M, double* A,

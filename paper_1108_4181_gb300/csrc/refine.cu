@@ -35,6 +35,7 @@ struct IrState {
   int cur;                  // slot of the next residual (advanced by every check)
   int range;                // the FP32 double-word residual met a value it cannot represent
   double rn2_fb;            // ||r||_F^2 of the FP64 residual that then replaced it
+  int setok;                // per-set criterion (k_set_check): every column set within tolerance
 };
 
 template <typename T>
@@ -45,6 +46,8 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 template <>
 __device__ __forceinline__ double to_lp<double>(double v) { return v; }
+__device__ __forceinline__ float lp_to_float(float v) { return v; }
+__device__ __forceinline__ float lp_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ void block_add(double v, double* target) {
   __shared__ double red[32];
@@ -703,7 +706,109 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
 // tensor-core timeout), advances the slot, and -- inside the CUDA graph --
 // sets the condition of the refinement loop: another pass runs while not
 // done and fewer than max_it refinement solves have run.
-__global__ void k_ir_check(IrState* st, double tol2, int max_it, cudaGraphConditionalHandle loop) {
+// Per-set convergence (refined batches: column sets of one packed panel).
+// After a residual (pass >= 1), k_col_ssq adds every column's sum of squares
+// of the residual panel r into colssq (r as the next solve reads it: sp planes
+// of TR, block-transposed [N][ldr][M] when trans, else row-major [N][M][ldr]);
+// k_set_check reduces the columns to their sets, clears colssq, and sets
+// st->setok when every set s has ||r_s||^2 <= tol2c ||F_s||^2 (tol2c: tol^2
+// shrunk by the panel's rounding and the FP32 partial sums).
+template <typename TR>
+__global__ void __launch_bounds__(256) k_col_ssq(const TR* __restrict__ r, int sp, int trans, int64_t N, int M,
+                                                 int64_t K, int64_t ldr, double* __restrict__ colssq,
+                                                 const IrState* st) {
+  if (st->done || st->cur == 0) return;
+  const size_t plane = (size_t)N * ldr * M;
+  const int64_t rows_per = (N + gridDim.y - 1) / gridDim.y;
+  const int64_t j0 = (int64_t)blockIdx.y * rows_per, j1 = min(N, j0 + rows_per);
+  if (trans) {
+    // a column's M values of a block row are contiguous: one warp per column,
+    // lanes along m (coalesced), 16 columns of the CTA's 128 per warp
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    for (int i = 0; i < 16; ++i) {
+      const int64_t n = (int64_t)blockIdx.x * 128 + w * 16 + i;
+      if (n >= K) break;
+      double tot = 0.0;
+      // four block rows per step, up to M / 32 <= 4 values of each per lane
+      // and plane, all loads issued before the sums
+      for (int64_t jb = j0; jb < j1; jb += 64) {
+        float acc = 0.f;  // FP32 partial sums of at most 64 x 4 squares per lane
+        const int64_t je = min(j1, jb + 64);
+        for (int64_t j = jb; j < je; j += 4) {
+          float v[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              v[u][q] = 0.f;
+              if (j + u < je && lane + 32 * q < M) {
+                const TR* e = r + ((size_t)(j + u) * ldr + n) * M + lane + 32 * q;
+                v[u][q] = lp_to_float(e[0]);
+                if (sp == 2) v[u][q] += lp_to_float(e[plane]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc = fmaf(v[u][q], v[u][q], acc);
+        }
+        tot += acc;
+      }
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      if (lane == 0) atomicAdd(colssq + n, tot);
+    }
+    return;
+  }
+  // row-major: threads along n (coalesced), the two halves of the CTA split m
+  const int64_t n = (int64_t)blockIdx.x * 128 + threadIdx.x % 128;
+  if (n >= K) return;
+  const int half = threadIdx.x / 128;
+  float acc = 0.f;
+  double tot = 0.0;
+  int cnt = 0;
+  for (int64_t j = j0; j < j1; ++j) {
+    for (int m = half; m < M; m += 2) {
+      const size_t e = ((size_t)j * M + m) * ldr + n;
+      float v = 0.f;
+      for (int p = 0; p < sp; ++p) v += lp_to_float(r[e + p * plane]);
+      acc = fmaf(v, v, acc);
+      if (++cnt == 256) {  // FP32 partial sums of at most 256 squares
+        tot += acc;
+        acc = 0.f;
+        cnt = 0;
+      }
+    }
+  }
+  tot += acc;
+  atomicAdd(colssq + n, tot);
+}
+
+__global__ void __launch_bounds__(256) k_set_check(double* __restrict__ colssq, const int* __restrict__ colset,
+                                                   int64_t K, int nsets, const double* __restrict__ setn2,
+                                                   double tol2c, IrState* st) {
+  if (st->done || st->cur == 0) return;
+  extern __shared__ double ss[];
+  for (int s = threadIdx.x; s < nsets; s += blockDim.x) ss[s] = 0.0;
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < K; c += blockDim.x) {
+    atomicAdd(ss + colset[c], colssq[c]);
+    colssq[c] = 0.0;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int s = threadIdx.x; s < nsets; s += blockDim.x) {
+    // ||F_s||^2 after the set's power-of-two scaling (set_exponent of the batch)
+    const double n2 = setn2[s];
+    int e = 0;
+    if (n2 > 0.0 && n2 < INFINITY) frexp(sqrt(n2), &e);
+    ok = ok && ss[s] <= tol2c * ldexp(n2, -2 * e);
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) st->setok = ok ? 1 : 0;
+}
+
+__global__ void k_ir_check(IrState* st, double tol2, int max_it, cudaGraphConditionalHandle loop, int setmode) {
   const int pass = st->cur;
   if (st->range) {  // the FP64 residual replaced the double-word one
     st->rn2[pass] = st->rn2_fb;
@@ -716,7 +821,7 @@ __global__ void k_ir_check(IrState* st, double tol2, int max_it, cudaGraphCondit
       const double r2 = st->rn2[pass];
       if (st->kstatus != 0) {
         st->done = 3;  // a tensor-core kernel gave up: stop, report
-      } else if (r2 <= tol2 * st->fn2) {
+      } else if (setmode ? st->setok != 0 : r2 <= tol2 * st->fn2) {
         st->done = 1;
       } else if (pass >= 3 && r2 >= 0.9 * st->rn2[pass - 1] && st->rn2[pass - 1] >= 0.9 * st->rn2[pass - 2]) {
         st->done = 2;  // two passes without a 10 % reduction: stalled
@@ -930,8 +1035,10 @@ bt_status make_f32_factors(bt_handle_s* h, cudaStream_t st) {
   return BT_OK;
 }
 
-bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info) {
+bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, const bt_opts& o, bt_info* info,
+                        int how, cudaStream_t rec, const SetCheck* sc) {
   cudaStream_t s = (cudaStream_t)o.stream;
+  const int gen0 = h->lp_gen;
   // default passes: the split-BF16 solve gains about five digits per pass, the
   // single-plane precisions about two to three
   const int max_it = o.max_it > 0 ? std::min(o.max_it, kMaxPasses - 3) : (o.precision == BT_PREC_BF16X3 ? 6 : 12);
@@ -987,6 +1094,11 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   if (digits) BT_TRY(resid_digits_prepare(h, K, s));
   BT_TRY(make_f32_factors(h, s));
   if (tcore) BT_TRY(make_tc_factors(h, prec, s));
+  if (!h->rg_cap2) BT_CUDA(cudaStreamCreateWithFlags(&h->rg_cap2, cudaStreamNonBlocking));
+  if (how == 2 && h->lp_gen != gen0) {
+    set_error("refinement recorded into a capture before its buffers were prepared");
+    return BT_ERR_ARG;
+  }
   IrState* st = reinterpret_cast<IrState*>(h->ir_state);
   const int* done = &st->done;
   const double tol2 = tol * tol;
@@ -1027,7 +1139,25 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   };
   auto check = [&](cudaStream_t q, cudaGraphConditionalHandle loop) {
     ProfScope ps(h, q, "ir_check");
-    k_ir_check<<<1, 1, 0, q>>>(st, tol2, max_it, loop);
+    if (sc != nullptr) {
+      // the panel's relative rounding u (BF16 2^-8, TF32 2^-11, split BF16
+      // about 2^-16, FP32 rounded toward zero 2^-23), with a factor 2 to spare
+      const double u = prec == BT_PREC_BF16 ? 0x1p-7 : prec == BT_PREC_TF32 ? 0x1p-10
+                       : prec == BT_PREC_BF16X3 ? 0x1p-15 : 0x1p-22;
+      const double tol2c = tol2 * (1.0 - u) * (1.0 - u) * (1.0 - 0x1p-12);
+      const int64_t ldr = tcore ? Kp : K;
+      const int64_t tiles = (K + 127) / 128;
+      const dim3 g((unsigned)tiles, (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->N, 2432 / tiles)));
+      if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
+        k_col_ssq<__nv_bfloat16><<<g, 256, 0, q>>>(reinterpret_cast<const __nv_bfloat16*>(h->lp_r), sp, tcore ? 1 : 0,
+                                                   h->N, M, K, ldr, sc->colssq, st);
+      else
+        k_col_ssq<float><<<g, 256, 0, q>>>(reinterpret_cast<const float*>(h->lp_r), sp, tcore ? 1 : 0, h->N, M, K,
+                                           ldr, sc->colssq, st);
+      k_set_check<<<1, 256, (size_t)sc->nsets * sizeof(double), q>>>(sc->colssq, sc->colset, K, sc->nsets, sc->n2,
+                                                                    tol2c, st);
+    }
+    k_ir_check<<<1, 1, 0, q>>>(st, tol2, max_it, loop, sc != nullptr ? 1 : 0);
   };
   auto prologue = [&](cudaStream_t q, cudaGraphConditionalHandle loop) -> bt_status {
     BT_CUDA(cudaMemsetAsync(st, 0, sizeof(IrState), q));
@@ -1062,23 +1192,20 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     BT_CUDA(cudaGetLastError());
     return BT_OK;
   };
-  // Captures prologue + WHILE(body) into *out; false (and nothing captured) on failure.
-  auto capture = [&](cudaGraph_t* out) -> bool {
-    cudaStream_t& cap = h->rg_cap;
-    cudaStream_t& cap2 = h->rg_cap2;
-    if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return false;
-    if (!cap2 && cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
-    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  // Records prologue + WHILE(body) + epilogue into the capture in progress on
+  // q (the WHILE body is captured on a second stream into the node's graph).
+  auto record = [&](cudaStream_t q) -> bool {
+    cudaStream_t cap2 = h->rg_cap2;
     bool ok = true;
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     cudaGraphConditionalHandle loop = 0;
-    ok = ok && cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
+    ok = ok && cudaStreamGetCaptureInfo(q, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
     ok = ok && cudaGraphConditionalHandleCreate(&loop, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
-    ok = ok && prologue(cap, loop) == BT_OK;
+    ok = ok && prologue(q, loop) == BT_OK;
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
-    ok = ok && cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
+    ok = ok && cudaStreamGetCaptureInfo(q, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = loop;
@@ -1086,7 +1213,7 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
     cp.conditional.size = 1;
     cudaGraphNode_t cn = nullptr;
     ok = ok && cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp) == cudaSuccess;
-    ok = ok && cudaStreamUpdateCaptureDependencies(cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+    ok = ok && cudaStreamUpdateCaptureDependencies(q, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
                    cudaSuccess;
     if (ok) {
       cudaGraph_t bg = cp.conditional.phGraph_out[0];
@@ -1098,7 +1225,26 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
         ok = cudaStreamEndCapture(cap2, &bg_out) == cudaSuccess && bs == BT_OK;
       }
     }
-    ok = ok && epilogue(cap) == BT_OK;  // after the WHILE node
+    return ok && epilogue(q) == BT_OK;  // after the WHILE node
+  };
+  if (how == 1) {  // one direct run builds what the launches build lazily (job tables, scratch)
+    BT_TRY(enqueue(s));
+    BT_CUDA(cudaStreamSynchronize(s));
+    return BT_OK;
+  }
+  if (how == 2) {
+    if (!record(rec)) {
+      set_error("refinement: recording into the capture failed");
+      return BT_ERR_CUDA;
+    }
+    return BT_OK;
+  }
+  // Captures the refinement into *out; false (and nothing captured) on failure.
+  auto capture = [&](cudaGraph_t* out) -> bool {
+    cudaStream_t& cap = h->rg_cap;
+    if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const bool ok = record(cap);
     cudaGraph_t graph = nullptr;
     const bool ended = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
     if (!(ok && ended && graph)) {
@@ -1253,6 +1399,19 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
   }
   if (norm2) *norm2 = hs.range ? hs.rn2_fb : hs.rn2[0];
   return BT_OK;
+}
+
+size_t refine_state_bytes() { return sizeof(IrState); }
+
+// Fills *info from a copy of a handle's refinement state; returns the
+// tensor-core status word (non-zero: a bounded wait gave up).
+int refine_state_info(const void* state, bt_info* info) {
+  const IrState& hs = *reinterpret_cast<const IrState*>(state);
+  info->iters = hs.solves;
+  info->converged = hs.done == 1 ? 1 : 0;
+  info->rel_res = hs.fn2 > 0 ? std::sqrt(hs.rn2[hs.last] / hs.fn2) : 0.0;
+  info->rel_res0 = hs.fn2 > 0 ? std::sqrt(hs.rn2[1] / hs.fn2) : 0.0;
+  return hs.kstatus;
 }
 
 }  // namespace bt

@@ -287,15 +287,21 @@ def _batch_arrays(facs, Fs, Xs):
 class BatchPlan:
     """A planned batch of solves (bt_batch_*): set i solves facs[i] X_i = F_i.
 
-    The plan records the tensors' device addresses: keep F and X alive and in
-    place while it is used.  run() enqueues one persistent launch (a CUDA
-    graph replay) on the current stream."""
+    precision "f64": one persistent launch for all sets.  Any other precision:
+    the sets of each factorization are packed into one panel (each scaled by a
+    power of two), refined as one solve per factorization until every set
+    meets ``tol`` on its own, and unpacked; all of it is one CUDA graph.  The plan records the tensors' device addresses: keep F and X
+    alive and in place while it is used.  run() enqueues one graph launch on
+    the current stream."""
 
-    def __init__(self, facs, Fs, Xs, k_tile: int = 0):
+    def __init__(self, facs, Fs, Xs, k_tile: int = 0, precision: str = "f64", tol: float = 0.0, max_it: int = 0,
+                 residual: str = "auto"):
         self.facs, self.Fs, self.Xs = list(facs), list(Fs), list(Xs)  # keep alive
         self.device = self.facs[0].device
+        self.precision = precision
         H, Fp, K, Xp = _batch_arrays(self.facs, self.Fs, self.Xs)
-        opts = _lib.BtOpts(precision=0, max_it=0, tol=0.0, stream=None, k_tile=int(k_tile), residual=0)
+        opts = _lib.BtOpts(precision=_lib.PREC[precision], max_it=int(max_it), tol=float(tol), stream=None,
+                           k_tile=int(k_tile), residual=_lib.RESIDUAL[residual])
         self._b = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(_lib.load().bt_batch_create(len(self.facs), H, Fp, K, Xp, ctypes.byref(opts),
@@ -304,11 +310,18 @@ class BatchPlan:
         _lib.check(_lib.load().bt_batch_query(self._b, q), "bt_batch_query")
         self.items, self.stages, self.ctas, self.threads, self.k_tile, self.graph = (int(v) for v in q)
 
+    def info(self, i: int):
+        """The refinement report of set i's factorization group (after status())."""
+        inf = _lib.BtInfo()
+        _lib.check(_lib.load().bt_batch_info(self._b, int(i), ctypes.byref(inf)), "bt_batch_info")
+        return dict(iters=inf.iters, converged=bool(inf.converged), rel_res=inf.rel_res, rel_res0=inf.rel_res0)
+
     def run(self, stream: Optional[torch.cuda.Stream] = None):
         _lib.check(_lib.load().bt_batch_run(self._b, _stream_ptr(stream, self.device)), "bt_batch_run")
 
     def status(self):
-        """Waits for the plan's work; raises if a bounded grid-barrier wait gave up."""
+        """Waits for the plan's work; raises if a bounded wait gave up or a
+        refined group did not converge."""
         _lib.check(_lib.load().bt_batch_status(self._b), "bt_batch_status")
 
     def debug(self, limit_s: float = 0.0, skip_stage: int = -1):
@@ -344,19 +357,21 @@ def solve_batched(facs, Fs, Xs=None, k_tile: int = 0, stream: Optional[torch.cud
 
 def solve_refined_sets(facs, Fs, Xs=None, precision: str = "bf16x3", tol: float = 0.0, max_it: int = 0,
                        residual: str = "auto"):
-    """Refined solves of many right-hand-side sets, X_b = P_{facs[b]}^{-1} F_b.
-
-    The sets of one factorization run in order on one stream (calls on a handle
-    must), different factorizations concurrently, each on a stream of its own;
-    every solve is one ``solve`` call (replayed from its CUDA graph when the
-    handle has seen its arguments before).  Returns the outputs; the work is
-    ordered before later work on the current stream."""
+    """Refined solves of many right-hand-side sets, X_b = P_{facs[b]}^{-1} F_b,
+    through a refined BatchPlan (one CUDA graph; every set meets ``tol`` on its
+    own).  Plans once per call: keep a BatchPlan to run the same sets again.
+    The work is ordered on the current stream; returns the outputs."""
     if Xs is None:
         Xs = [torch.empty_like(F) for F in Fs]
     if not (len(facs) == len(Fs) == len(Xs)):
         raise ValueError("facs, Fs and Xs must have the same length")
     if not facs:
         return Xs
+    plan = BatchPlan(facs, Fs, Xs, precision=precision, tol=tol, max_it=max_it, residual=residual)
+    plan.run()
+    plan.status()
+    plan.close()
+    return Xs
     dev = Fs[0].device
     cur = torch.cuda.current_stream(dev)
     used = {}

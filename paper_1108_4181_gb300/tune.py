@@ -28,6 +28,7 @@ class TuneResult:
     ms: float
     table: Dict[Tuple[int, int], float] = field(default_factory=dict)  # (S, k_tile) -> ms per run
     factors: Optional[List[solver.Factorization]] = None  # the winner's factorizations (kept open)
+    plan: Optional["solver.BatchPlan"] = None  # tune_batched_refined: the winner's plan (kept open)
 
 
 def _valid_S(N: int, cands: Sequence[int]) -> List[int]:
@@ -90,34 +91,42 @@ def tune_batched(mats, sets, S_candidates: Sequence[int] = S_CANDIDATES,
 
 def tune_batched_refined(mats, sets, precision: str = "bf16x3", tol: float = 0.0,
                          S_candidates: Sequence[int] = (32, 64, 128), reps: int = 2) -> TuneResult:
-    """Best S for the refined (mixed-precision) path over a batch of sets, run by
-    ``solver.solve_refined_sets`` (one ``solve`` per set, each replayed from its
-    CUDA graph after the first two calls; one stream per matrix).  Same
-    arguments and result as ``tune_batched`` (k_tile 0: the tensor-core tile)."""
+    """Best S for the refined (mixed-precision) batch: for each candidate, every
+    matrix is factored and a refined ``solver.BatchPlan`` (the sets of a matrix
+    packed into one panel, one CUDA graph) is timed.  Same arguments and result
+    as ``tune_batched`` (k_tile 0: the tensor-core tile); the winner's plan is
+    kept in ``result.plan``."""
     N = mats[0][0].shape[0]
     device = mats[0][0].device
     Xs = [torch.empty_like(F) for _, F in sets]
     table: Dict[Tuple[int, int], float] = {}
     best: Optional[TuneResult] = None
+    best_plan = None
     for S in _valid_S(N, S_candidates):
         facs = [solver.factor(A, B, C, S) for A, B, C in mats]
+        plan = solver.BatchPlan([facs[i] for i, _ in sets], [F for _, F in sets], Xs, precision=precision, tol=tol)
 
         def step():
-            solver.solve_refined_sets([facs[i] for i, _ in sets], [F for _, F in sets], Xs,
-                                      precision=precision, tol=tol)
+            plan.run()
 
-        step()  # first call per set: buffers and factor copies; the timed warm-up captures the graphs
+        step()
+        plan.status()
         ms = _time(step, reps, device)
+        plan.status()
         table[(S, 0)] = ms
         if best is None or ms < best.ms:
-            if best is not None and best.factors is not None:
+            if best is not None:
+                best_plan.close()
                 for f in best.factors:
                     f.close()
             best = TuneResult(S=S, k_tile=0, ms=ms, factors=facs)
+            best_plan = plan
         else:
+            plan.close()
             for f in facs:
                 f.close()
     best.table = table
+    best.plan = best_plan
     return best
 
 
