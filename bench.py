@@ -764,18 +764,19 @@ def run_schur(args):
     with bt.SchurPCG(256, 8, 2, 0.0, d=2, S=8) as sp0:  # library and context set-up outside the timings
         sp0.solve(torch.ones((17, 256, 1), dtype=torch.float64, device=dev))
     rows = []
-    for d in [int(v) for v in args.schur_bands.split(",")]:
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        sp = bt.SchurPCG(nr, h, p, 0.0, d=d, S=Sg)
-        torch.cuda.synchronize(dev)
-        t1 = time.perf_counter()
-        _, info = sp.solve(F, tol=tol, max_it=5000, return_info=True, check=False)
-        torch.cuda.synchronize(dev)
-        t2 = time.perf_counter()
-        sp.close()
-        rows.append({"d": d, "gen_s": t1 - t0, "total_s": t2 - t1, **info})
-        print(f"schur d={d}: {json.dumps(rows[-1])}", file=sys.stderr, flush=True)
+    with ClockSampler(0) as clk:
+        for d in [int(v) for v in args.schur_bands.split(",")]:
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            sp = bt.SchurPCG(nr, h, p, 0.0, d=d, S=Sg)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            _, info = sp.solve(F, tol=tol, max_it=5000, return_info=True, check=False)
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+            sp.close()
+            rows.append({"d": d, "gen_s": t1 - t0, "total_s": t2 - t1, **info})
+            print(f"schur d={d}: {json.dumps(rows[-1])}", file=sys.stderr, flush=True)
     base = next((r for r in rows if r["d"] < 0), None)
     best = min(rows, key=lambda r: r["total_s"])
     line = {
@@ -786,6 +787,7 @@ def run_schur(args):
         "config": {"workload": f"Schur-complement CG: five-point operator on a {nz} x {nr} grid, {p} strips of "
                                f"{h} rows, K={K}, strip solves S={Sg}, tol {tol}"},
         "bands": rows,
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0

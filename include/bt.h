@@ -393,9 +393,14 @@ bt_status bt_schur_rhs(bt_schur s, const double* F, int64_t K, double* g, void* 
  * a column stopping once ||g - S x_G|| <= tol ||g|| (the recursively updated
  * residual), at most max_it iterations; then the interiors (eq.
  * domains_equation) and X.  Each iteration: one product with S (one
- * dichotomy solve of p K columns), one solve with B, four column dot products;
- * the host reads the number of unconverged columns once per iteration
- * (synchronous).  X must not overlap F.  info (may be NULL): iterations,
+ * dichotomy solve of p K columns), one solve with B, three column dot
+ * products and the convergence check.  The whole solve is one CUDA graph: the
+ * iterations are the body of a device-side WHILE node whose condition the
+ * check sets (active columns remain, fewer than max_it iterations), so the
+ * host does not wait per iteration.  A call with new arguments (F, X, K, tol,
+ * max_it) or after a buffer moved first runs every sub-solve once directly and
+ * captures the graph (synchronous); repeated calls replay it.  The call
+ * synchronises `stream` once at the end.  X must not overlap F.  info (may be NULL): iterations,
  * converged, rel_res = the largest relative residual over the columns,
  * rel_res0 = 1.  BT_ERR_NOCONV if a column did not converge (X is then the
  * solution for the last iterate).

@@ -1,5 +1,8 @@
 // C-ABI entry points: argument validation, handle lifetime, dispatch.
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 
@@ -17,13 +20,28 @@ bt_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 int resident_grid(const void* fn, int threads, size_t smem) {
+  // cached per (device, kernel, shape): the first query of a kernel may load
+  // its module, which must not happen inside a stream capture
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  const auto key = std::make_tuple(dev, fn, threads, smem);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 152;
   }
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = sms * per_sm;
   return sms * per_sm;
 }
 

@@ -48,8 +48,19 @@ struct bt_schur_s {
   double* vbuf = nullptr;     // interface panels g, x, r, z, pd, q: [ng][K] each
   size_t vbytes = 0;
   double* cbuf = nullptr;     // per-column scalars: rz, rz', pq, rr, gn2
-  int* ibuf = nullptr;        // active flags [K] + active count
+  int* ibuf = nullptr;        // active flags [K] + active count + iteration count
   size_t cK = 0;
+  // The PCG solve as one CUDA graph (prologue, device-side WHILE over the
+  // iterations, epilogue) for the last argument key; `ptrs` are the buffers
+  // it was captured with (a reallocation anywhere captures again).
+  cudaGraphExec_t pcg_exec = nullptr;
+  const double* pcg_F = nullptr;
+  double* pcg_X = nullptr;
+  int64_t pcg_K = 0;
+  double pcg_tol = 0.0;
+  int32_t pcg_max = -1;
+  std::vector<const void*> pcg_ptrs;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
 };
 
 namespace bt {
@@ -172,8 +183,26 @@ __global__ void __launch_bounds__(1024) k_coldot(const double* __restrict__ a, c
   }
 }
 
-// active[c] &= rr[c] > tol^2 gn2[c]; count the active columns
-__global__ void k_pcg_check(const double* rr, const double* gn2, double tol2, int64_t K, int* active, int* count) {
+// CG start: rz = +inf (so the first step takes beta = 0), every column active,
+// no iteration yet
+__global__ void k_pcg_init(double* rz, int64_t K, int* active, int* it) {
+  for (int64_t c = threadIdx.x; c < K; c += blockDim.x) {
+    rz[c] = INFINITY;
+    active[c] = 1;
+  }
+  if (threadIdx.x == 0) *it = 0;
+}
+
+__global__ void k_copy_cols(double* __restrict__ dst, const double* __restrict__ src, int64_t K) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < K; c += (int64_t)gridDim.x * blockDim.x)
+    dst[c] = src[c];
+}
+
+// active[c] &= rr[c] > tol^2 gn2[c]; count the active columns.  step 1 (after
+// an iteration) also counts the iteration; the loop condition is set to
+// "active columns remain and fewer than max_it iterations ran".
+__global__ void k_pcg_check(const double* rr, const double* gn2, double tol2, int64_t K, int* active, int* count,
+                            int* it, int max_it, int step, cudaGraphConditionalHandle loop) {
   int n = 0;
   for (int64_t c = threadIdx.x; c < K; c += blockDim.x) {
     const int a = active[c] && rr[c] > tol2 * gn2[c];
@@ -188,6 +217,9 @@ __global__ void k_pcg_check(const double* rr, const double* gn2, double tol2, in
     int t = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
     *count = t;
+    const int done = *it + step;
+    *it = done;
+    if (loop) cudaGraphSetConditional(loop, (t > 0 && done < max_it) ? 1u : 0u);
   }
 }
 
@@ -263,7 +295,7 @@ bt_status ensure_k(bt_schur_s* s, int64_t K) {
     s->ibuf = nullptr;
     s->cK = 0;
     BT_CUDA(cudaMalloc((void**)&s->cbuf, 5 * (size_t)K * sizeof(double)));
-    BT_CUDA(cudaMalloc((void**)&s->ibuf, ((size_t)K + 1) * sizeof(int)));
+    BT_CUDA(cudaMalloc((void**)&s->ibuf, ((size_t)K + 2) * sizeof(int)));
     s->cK = (size_t)K;
   }
   return BT_OK;
@@ -310,6 +342,9 @@ void destroy(bt_schur_s* s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
   cudaDeviceSynchronize();
+  if (s->pcg_exec) cudaGraphExecDestroy(s->pcg_exec);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->cap2) cudaStreamDestroy(s->cap2);
   if (s->strip) bt_destroy(s->strip);
   if (s->band) bt_destroy(s->band);
   for (void* q : {(void*)s->ab, (void*)s->sbuf, (void*)s->vbuf, (void*)s->cbuf, (void*)s->ibuf})
@@ -448,42 +483,122 @@ bt_status bt_schur_solve(bt_schur s, const double* F, int64_t K, double* X, doub
   double *rz = s->cbuf, *rz2 = rz + K, *pq = rz2 + K, *rr = pq + K, *gn2 = rr + K;
   int* active = s->ibuf;
   int* count = s->ibuf + K;
-  // g (eq. schur_decomp, right-hand side) and the CG start x = 0, r = g
-  BT_TRY(reduce_rhs(s, F, K, g, st));
-  BT_CUDA(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
-  BT_CUDA(cudaMemcpyAsync(r, g, nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  BT_TRY(precond(s, r, K, z, st));
-  BT_CUDA(cudaMemcpyAsync(pd, z, nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  BT_TRY(coldot(r, z, s->ng, K, rz, st));
-  BT_TRY(coldot(g, g, s->ng, K, gn2, st));
-  std::vector<int> ones((size_t)K, 1);
-  BT_CUDA(cudaMemcpyAsync(active, ones.data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice, st));
+  int* itc = s->ibuf + K + 1;
   const double tol2 = tol * tol;
-  k_pcg_check<<<1, 1024, 0, st>>>(gn2, gn2, tol2, K, active, count);
-  BT_CUDA(cudaGetLastError());
-  int hcount = 0;
-  BT_CUDA(cudaMemcpyAsync(&hcount, count, sizeof(int), cudaMemcpyDeviceToHost, st));
-  BT_CUDA(cudaStreamSynchronize(st));
-  int it = 0;
-  while (hcount > 0 && it < max_it) {
+  // g (eq. schur_decomp, right-hand side), the CG start x = 0, r = g, p = 0
+  auto prologue = [&](cudaStream_t st, cudaGraphConditionalHandle loop) -> bt_status {
+    BT_TRY(reduce_rhs(s, F, K, g, st));
+    BT_CUDA(cudaMemsetAsync(x, 0, nv * sizeof(double), st));
+    BT_CUDA(cudaMemsetAsync(pd, 0, nv * sizeof(double), st));
+    BT_CUDA(cudaMemcpyAsync(r, g, nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    BT_TRY(coldot(g, g, s->ng, K, gn2, st));
+    k_pcg_init<<<1, 1024, 0, st>>>(rz, K, active, itc);
+    k_pcg_check<<<1, 1024, 0, st>>>(gn2, gn2, tol2, K, active, count, itc, max_it, 0, loop);
+    BT_CUDA(cudaGetLastError());
+    return BT_OK;
+  };
+  // one PCG iteration: z = B^-1 r, beta = (r, z) / (r, z)_old, p = z + beta p,
+  // q = S p, alpha = (r, z) / (p, q), x += alpha p, r -= alpha q, check
+  auto body = [&](cudaStream_t st, cudaGraphConditionalHandle loop) -> bt_status {
+    BT_TRY(precond(s, r, K, z, st));
+    BT_TRY(coldot(r, z, s->ng, K, rz2, st));
+    EW(k_pcg_p, nv, pd, z, rz2, rz, active, s->ng, K);
+    k_copy_cols<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(rz, rz2, K);
     BT_TRY(apply_S(s, pd, K, q, st));
     BT_TRY(coldot(pd, q, s->ng, K, pq, st));
     EW(k_pcg_xr, nv, x, r, pd, q, rz, pq, active, s->ng, K);
     BT_TRY(coldot(r, r, s->ng, K, rr, st));
-    k_pcg_check<<<1, 1024, 0, st>>>(rr, gn2, tol2, K, active, count);
+    k_pcg_check<<<1, 1024, 0, st>>>(rr, gn2, tol2, K, active, count, itc, max_it, 1, loop);
     BT_CUDA(cudaGetLastError());
-    BT_CUDA(cudaMemcpyAsync(&hcount, count, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BT_CUDA(cudaStreamSynchronize(st));
-    ++it;
-    if (hcount == 0) break;
-    BT_TRY(precond(s, r, K, z, st));
-    BT_TRY(coldot(r, z, s->ng, K, rz2, st));
-    EW(k_pcg_p, nv, pd, z, rz2, rz, active, s->ng, K);
-    std::swap(rz, rz2);
-  }
+    return BT_OK;
+  };
   // interiors (eq. domains_equation) and the whole grid panel
-  BT_TRY(strip_solve(s, F, x, K, st));
-  EW(k_grid_out, (size_t)s->nz * s->nr * K, strip_out(s, K), x, s->nr, (int)s->h, (int)s->p, K, X);
+  auto epilogue = [&](cudaStream_t st) -> bt_status {
+    BT_TRY(strip_solve(s, F, x, K, st));
+    EW(k_grid_out, (size_t)s->nz * s->nr * K, strip_out(s, K), x, s->nr, (int)s->h, (int)s->p, K, X);
+    return BT_OK;
+  };
+  // the buffers a captured graph holds (the strip and band solves' own scratch included)
+  const std::vector<const void*> ptrs = {s->sbuf, s->vbuf, s->cbuf, s->ibuf, s->strip->scratch,
+                                         s->band ? s->band->scratch : nullptr, s->band ? s->band->band_buf : nullptr};
+  const bool same = s->pcg_exec && s->pcg_F == F && s->pcg_X == X && s->pcg_K == K && s->pcg_tol == tol &&
+                    s->pcg_max == max_it && s->pcg_ptrs == ptrs;
+  if (!same) {
+    if (s->pcg_exec) cudaGraphExecDestroy(s->pcg_exec);
+    s->pcg_exec = nullptr;
+    // one direct pass of every sub-solve grows what they allocate on first use,
+    // and every kernel of the graph is launched (loaded) once before the capture
+    BT_TRY(reduce_rhs(s, F, K, g, st));
+    BT_TRY(precond(s, g, K, z, st));
+    BT_TRY(apply_S(s, z, K, q, st));
+    BT_TRY(coldot(g, g, s->ng, K, gn2, st));
+    k_pcg_init<<<1, 1024, 0, st>>>(rz, K, active, itc);
+    k_copy_cols<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(rz2, rz, K);
+    k_pcg_check<<<1, 1024, 0, st>>>(gn2, gn2, tol2, K, active, count, itc, max_it, 0, 0);
+    BT_CUDA(cudaMemsetAsync(pd, 0, nv * sizeof(double), st));
+    EW(k_pcg_p, nv, pd, z, rz2, rz, active, s->ng, K);
+    EW(k_pcg_xr, nv, x, r, pd, q, rz, pq, active, s->ng, K);
+    (void)grid_for((const void*)k_grid_out, (size_t)s->nz * s->nr * K);
+    BT_CUDA(cudaStreamSynchronize(st));
+    const std::vector<const void*> ptrs2 = {s->sbuf, s->vbuf, s->cbuf, s->ibuf, s->strip->scratch,
+                                            s->band ? s->band->scratch : nullptr,
+                                            s->band ? s->band->band_buf : nullptr};
+    if (!s->cap) BT_CUDA(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+    if (!s->cap2) BT_CUDA(cudaStreamCreateWithFlags(&s->cap2, cudaStreamNonBlocking));
+    BT_CUDA(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    bool ok = true;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle loop = 0;
+    ok = ok && cudaStreamGetCaptureInfo(s->cap, &cs, nullptr, &cg) == cudaSuccess && cg != nullptr;
+    ok = ok && cudaGraphConditionalHandleCreate(&loop, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    ok = ok && prologue(s->cap, loop) == BT_OK;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ok = ok && cudaStreamGetCaptureInfo(s->cap, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn = nullptr;
+    ok = ok && cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp) == cudaSuccess;
+    ok = ok && cudaStreamUpdateCaptureDependencies(s->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                   cudaSuccess;
+    if (ok) {
+      ok = cudaStreamBeginCaptureToGraph(s->cap2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bt_status bs = body(s->cap2, loop);
+        cudaGraph_t bg = nullptr;
+        ok = cudaStreamEndCapture(s->cap2, &bg) == cudaSuccess && bs == BT_OK;
+      }
+    }
+    ok = ok && epilogue(s->cap) == BT_OK;
+    cudaGraph_t graph = nullptr;
+    const bool ended = cudaStreamEndCapture(s->cap, &graph) == cudaSuccess;
+    // nothing may have moved while capturing (the prepare pass grew every buffer)
+    const std::vector<const void*> ptrs3 = {s->sbuf, s->vbuf, s->cbuf, s->ibuf, s->strip->scratch,
+                                            s->band ? s->band->scratch : nullptr,
+                                            s->band ? s->band->band_buf : nullptr};
+    ok = ok && ended && graph && ptrs3 == ptrs2 && cudaGraphInstantiate(&s->pcg_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      s->pcg_exec = nullptr;
+      const cudaError_t e = cudaGetLastError();
+      set_error(std::string("bt_schur_solve: capturing the PCG loop failed: ") + cudaGetErrorString(e));
+      return BT_ERR_CUDA;
+    }
+    s->pcg_F = F;
+    s->pcg_X = X;
+    s->pcg_K = K;
+    s->pcg_tol = tol;
+    s->pcg_max = max_it;
+    s->pcg_ptrs = ptrs2;
+  }
+  BT_CUDA(cudaGraphLaunch(s->pcg_exec, st));
+  int hc[2] = {0, 0};  // active columns left, iterations
+  BT_CUDA(cudaMemcpyAsync(hc, count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   if (info) {
     // ||r|| of the last iterate per column (recomputed for columns stopped earlier)
     BT_TRY(coldot(r, r, s->ng, K, rr, st));
@@ -493,12 +608,14 @@ bt_status bt_schur_solve(bt_schur s, const double* F, int64_t K, double* X, doub
     BT_CUDA(cudaStreamSynchronize(st));
     double worst = 0.0;
     for (int64_t c = 0; c < K; ++c) worst = std::max(worst, hgn[c] > 0 ? std::sqrt(hrr[c] / hgn[c]) : 0.0);
-    info->iters = it;
-    info->converged = hcount == 0 ? 1 : 0;
+    info->iters = hc[1];
+    info->converged = hc[0] == 0 ? 1 : 0;
     info->rel_res = worst;
     info->rel_res0 = 1.0;
+  } else {
+    BT_CUDA(cudaStreamSynchronize(st));
   }
-  return hcount == 0 ? BT_OK : BT_ERR_NOCONV;
+  return hc[0] == 0 ? BT_OK : BT_ERR_NOCONV;
 }
 
 }  // extern "C"
