@@ -199,12 +199,14 @@ FP64_OPS_PEAK = 152 * 2 * 2.070e9  # FP64 pipe operations per second (nominal un
 # code at capture time; once that file changes the figure no longer describes
 # the kernel and is reported as null.
 TRAFFIC = {
-    # k_resid_warp, one full residual pass of N=1024 (M=128, K=512, S=16):
-    # 1.078 GB read + 0.253 GB written for 6.7e7 unknowns; the kernel streams
-    # F and X once per pass, so traffic scales with the unknowns
-    "residual": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
-                 "sha256": "48b564ed045e2d9a0ef25b010efcf23d2d97023418e10e02598f551cb7941cef",
-                 "bytes_per_unknown": 19.8262},
+    # the double-word residual kernels of one refined solve of N=1024 (M=128,
+    # K=512, S=16; F, X 537 MB each): after the first solve 0.821 GB read +
+    # 0.249 GB written, the first refinement pass 1.109 + 0.772 GB, the gated
+    # launches 0.3 MB: 43.97 bytes per unknown against 44 algorithmic; the
+    # kernels stream every panel once, so traffic scales with the unknowns
+    "resid_dw": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
+                 "sha256": "bc4c0c3cafba81ddcb96db201f260473578a077fff9e90ddebd67fcd7b21991c",
+                 "bytes_per_unknown": 43.9686},
 }
 
 
@@ -259,11 +261,20 @@ def _kernel_work(name, prof, steps, info, precision):
         # FP64 X read, FP64 X written
         return "hbm", NMK * ((0.0 if direct_first else 12.0) + 20.0 * (full - 1)), "B"
     if name == "tc_sweep":
+        if panels:
+            # the forward pass of the unit-stencil flow (k_tc_fwd): r in, y out;
+            # Dinv and Z = U^T per interior row (once: the column tiles of a row
+            # share them through L2)
+            return "hbm", full * (2.0 * pb * NMK + 2.0 * fb * (N - S)), "B"
         # forward: r in, y out; backward: y in, W out (the y panel of a
         # segment exceeds on-chip memory, so it makes one round trip); Dinv,
         # E, G per interior row
         return "hbm", full * (4.0 * pb * NMK + 3.0 * fb * (N - S)), "B"
     if name == "tc_correct":
+        if panels:
+            # the backward pass (k_tc_bwd): y in, X out as an FP32 panel; G and
+            # Y per interior row
+            return "hbm", full * ((pb + 4.0) * NMK + 2.0 * fb * (N - S)), "B"
         # W in, d (FP32) out -- X (FP64) out in the first solve when the
         # correction writes it -- U, V per interior row
         first_out = 8.0 if direct_first else 4.0
@@ -437,8 +448,8 @@ def run_ours(args):
         roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "kernel": dom_name}
     roof["traffic"] = _traffic(dom_name)
     if roof["traffic"] is not None:
-        roof["traffic_note"] = ("DRAM bytes of one full residual pass (ncu capture of a smaller case scaled by "
-                                "unknowns); algorithmic bytes of the same pass: 20 per unknown")
+        roof["traffic_note"] = ("DRAM bytes of the kernel group in one step (ncu capture of a smaller case, scaled "
+                                "by unknowns); algorithmic bytes of the same: 44 per unknown")
     roof["kernels"] = roofs
     if info is not None:
         ab = _step_algorithmic_bytes(info, precision)
