@@ -199,14 +199,16 @@ FP64_OPS_PEAK = 152 * 2 * 2.070e9  # FP64 pipe operations per second (nominal un
 # code at capture time; once that file changes the figure no longer describes
 # the kernel and is reported as null.
 TRAFFIC = {
-    # the double-word residual kernels of one refined solve of N=1024 (M=128,
-    # K=512, S=16; F, X 537 MB each): after the first solve 0.821 GB read +
-    # 0.249 GB written, the first refinement pass 1.109 + 0.772 GB, the gated
-    # launches 0.3 MB: 43.97 bytes per unknown against 44 algorithmic; the
-    # kernels stream every panel once, so traffic scales with the unknowns
+    # the double-word residual's launches of one refined solve of N=1024 (M=128,
+    # K=512, S=16; F, X 537 MB each; the ncu --set full capture of
+    # `bench.py --rows 1024 --segments 16`): after the first solve 0.821 GB read
+    # + 0.249 GB written, the first refinement pass 1.109 + 0.776 GB, the gated
+    # launches about 0.04 MB each: 44.04 bytes per unknown against 44
+    # algorithmic; the kernels stream every panel once, so traffic scales with
+    # the unknowns
     "resid_dw": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
                  "sha256": "bc4c0c3cafba81ddcb96db201f260473578a077fff9e90ddebd67fcd7b21991c",
-                 "bytes_per_unknown": 43.9686},
+                 "bytes_per_unknown": 44.04},
 }
 
 
