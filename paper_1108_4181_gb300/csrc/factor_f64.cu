@@ -316,11 +316,14 @@ __global__ void k_band_profile(const double* A, const double* B, int64_t N, int 
 // Schedule builder
 // ---------------------------------------------------------------------------
 struct Op {
-  int kind;  // 0 = GEMM, 1 = INV
+  int kind;  // 0 = GEMM, 1 = INV, 2 = join (lane 0 waits for lane 1)
   int batch;
   size_t off;  // into the pointer table
   double alpha, beta;
   int4 bp;     // operand bands of a GEMM (see k_gemm_batched)
+  int lane;    // 0: the caller's stream; 1: a second, lower-priority stream
+               // that runs beside lane 0 and first waits for everything
+               // enqueued on lane 0 before it
 };
 
 struct Schedule {
@@ -329,9 +332,9 @@ struct Schedule {
   // GEMM batch under construction
   void gemm(double alpha, double beta, int4 bp, const std::vector<const double*>& X,
             const std::vector<const double*>& Y, const std::vector<const double*>& Z,
-            const std::vector<double*>& D) {
+            const std::vector<double*>& D, int lane = 0) {
     if (D.empty()) return;
-    Op o{0, (int)D.size(), tab.size(), alpha, beta, bp};
+    Op o{0, (int)D.size(), tab.size(), alpha, beta, bp, lane};
     for (size_t b = 0; b < D.size(); ++b) {
       tab.push_back(X[b]);
       tab.push_back(Y[b]);
@@ -342,13 +345,14 @@ struct Schedule {
   }
   void inv(const std::vector<const double*>& X, const std::vector<double*>& Y) {
     if (Y.empty()) return;
-    Op o{1, (int)Y.size(), tab.size(), 0.0, 0.0, make_int4(0, 0, 0, 0)};
+    Op o{1, (int)Y.size(), tab.size(), 0.0, 0.0, make_int4(0, 0, 0, 0), 0};
     for (size_t b = 0; b < Y.size(); ++b) {
       tab.push_back(X[b]);
       tab.push_back(Y[b]);
     }
     ops.push_back(o);
   }
+  void join() { ops.push_back(Op{2, 0, 0, 0.0, 0.0, make_int4(0, 0, 0, 0), 0}); }
 };
 
 // Helper collecting one batched GEMM entry at a time.
@@ -363,8 +367,8 @@ struct GemmBatch {
   }
   int4 dense = make_int4(-1024, 1024, -1024, 1024);
   void flush(Schedule& s, double alpha, double beta) { flush(s, alpha, beta, dense); }
-  void flush(Schedule& s, double alpha, double beta, int4 bp) {
-    s.gemm(alpha, beta, bp, X, Y, Z, D);
+  void flush(Schedule& s, double alpha, double beta, int4 bp, int lane = 0) {
+    s.gemm(alpha, beta, bp, X, Y, Z, D, lane);
     X.clear(); Y.clear(); Z.clear(); D.clear();
   }
 };
@@ -395,20 +399,57 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
   const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
   const int GT = (double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64;
   const int tiles = (M + GT - 1) / GT;
+  // lane 1: created on first use, lowest priority (lane 0 holds the critical path)
+  cudaStream_t lane1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool pending1 = false;  // lane 1 has work lane 0 has not joined
   for (const Op& o : sc.ops) {
+    if (o.kind == 2) {
+      if (pending1) {
+        BT_CUDA(cudaEventRecord(ev1, lane1));
+        BT_CUDA(cudaStreamWaitEvent(st, ev1, 0));
+        pending1 = false;
+      }
+      continue;
+    }
+    cudaStream_t q = st;
+    if (o.lane == 1) {
+      if (!lane1) {
+        int lo = 0, hi = 0;
+        BT_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        BT_CUDA(cudaStreamCreateWithPriority(&lane1, cudaStreamNonBlocking, lo));
+        BT_CUDA(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+        BT_CUDA(cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming));
+      }
+      BT_CUDA(cudaEventRecord(ev0, st));
+      BT_CUDA(cudaStreamWaitEvent(lane1, ev0, 0));
+      q = lane1;
+      pending1 = true;
+    }
     // grid.z / grid.x limits: split very large batches
     for (int b0 = 0; b0 < o.batch; b0 += 65535) {
       int nb = std::min(65535, o.batch - b0);
       if (o.kind == 0) {
         dim3 grid(tiles, tiles, nb);
         if (GT == 32)
-          k_gemm_batched<32><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
+          k_gemm_batched<32><<<grid, 256, 0, q>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
         else
-          k_gemm_batched<64><<<grid, 256, 0, st>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
+          k_gemm_batched<64><<<grid, 256, 0, q>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
       } else {
-        k_inverse_batched<<<nb, inv_threads, inv_smem, st>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
+        k_inverse_batched<<<nb, inv_threads, inv_smem, q>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
       }
     }
+  }
+  if (pending1) {
+    BT_CUDA(cudaEventRecord(ev1, lane1));
+    BT_CUDA(cudaStreamWaitEvent(st, ev1, 0));
+  }
+  if (lane1) {
+    // the stream and events may go once the work is enqueued (their
+    // destruction is deferred until it completes)
+    cudaStreamDestroy(lane1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
   }
   BT_CUDA(cudaGetLastError());
   return BT_OK;
@@ -514,6 +555,16 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   const bool split = h->band[0] != h->band[2] || h->band[1] != h->band[3];
 
   // ---- step 1.1: block sweep factorisation of every segment interior ------
+  // The forward products of E of eq. sub1 (Y_i = E_i Y_{i-1}, kept in U until
+  // the backward products) trail the sweep by one row on lane 1: row t-1's
+  // product runs beside row t's pivot inversions, which hold only S SMs.
+  auto y_step = [&](int64_t t) {
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t i = s * L + t;
+      g.add(blk(h->E, i), t == 1 ? Iw : blk(h->U, i - 1), nullptr, blk(h->U, i));
+    }
+    g.flush(sc, 1.0, 0.0, g.dense, 1);
+  };
   for (int64_t t = 1; t < L; ++t) {
     if (t > 1) {
       for (int64_t s = 0; s < S; ++s) {
@@ -521,6 +572,7 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
         g.add(Aj(i), blk(h->G, i - 1), blk(h->C, i), blk(Dw, s));
       }
       g.flush(sc, -1.0, 1.0, xA);  // D = C_i - A_i G_{i-1}
+      y_step(t - 1);
       for (int64_t s = 0; s < S; ++s) iv.add(blk(Dw, s), blk(h->Dinv, s * L + t));
     } else {
       for (int64_t s = 0; s < S; ++s) iv.add(blk(h->C, s * L + t), blk(h->Dinv, s * L + t));
@@ -539,14 +591,9 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
     }
     g.flush(sc, 1.0, 0.0);
   }
-  // U (eq. sub1): forward products of E into U, then U_i = Y_i + G_i U_{i+1}
-  for (int64_t t = 1; t < L; ++t) {
-    for (int64_t s = 0; s < S; ++s) {
-      int64_t i = s * L + t;
-      g.add(blk(h->E, i), t == 1 ? Iw : blk(h->U, i - 1), nullptr, blk(h->U, i));
-    }
-    g.flush(sc, 1.0, 0.0);
-  }
+  // U (eq. sub1): the last forward product, then U_i = Y_i + G_i U_{i+1}
+  if (L > 1) y_step(L - 1);
+  sc.join();
   for (int64_t t = L - 2; t >= 1; --t) {
     for (int64_t s = 0; s < S; ++s) {
       int64_t i = s * L + t;
@@ -573,61 +620,141 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   g.flush(sc, -1.0, 1.0, xB);
 
   // ---- step 1.3: rows of the inverses for Algorithm 1 on P~ ---------------
-  // Pw holds DL_j^{-1} / DR_j^{-1}; Dw holds DL_j / DR_j / Sigma; Tw products.
+  // The Schur-complement chains of a node and the propagation of its block
+  // row depend only on the reduced system, so the levels are independent:
+  // with work buffers per level (Pw: DL_j^{-1} / DR_j^{-1}, Dw: DL_j / DR_j /
+  // Sigma, Tw: products) the chains of ALL levels advance together, t steps
+  // for the longest chain instead of the sum over levels, in batches that
+  // hold every level's blocks.  Past a memory budget the levels run one
+  // after the other on shared buffers.
   h->level_off.assign(depth + 1, 0);
   for (auto& n : h->nodes) h->level_off[n.level + 1]++;
   for (int l = 0; l < depth; ++l) h->level_off[l + 1] += h->level_off[l];
   auto Rb = [&](int level, int j) { return h->R + ((size_t)level * S + j) * MM; };
-  for (int lev = 0; lev < depth; ++lev) {
-    std::vector<TreeNode> ns(h->nodes.begin() + h->level_off[lev], h->nodes.begin() + h->level_off[lev + 1]);
+  const bool together = depth > 1 && 3.0 * depth * S * MM * sizeof(double) <= 4.0 * (1ull << 30);
+  double *PwL = Pw, *DwL = Dw, *TwL = Tw;
+  double* lvl_buf = nullptr;  // released once the schedule has run
+  if (together) {
+    const size_t lvl = (size_t)depth * S * MM;
+    if (cudaMallocAsync((void**)&lvl_buf, 3 * lvl * sizeof(double), st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("bt_factor: work buffer allocation failed");
+      return BT_ERR_OOM;
+    }
+    PwL = lvl_buf;
+    DwL = lvl_buf + lvl;
+    TwL = lvl_buf + 2 * lvl;
+  }
+  auto lb = [&](double* base, int lev, int j) { return base + ((size_t)(together ? lev : 0) * S + j) * MM; };
+  for (int g0 = 0; g0 < depth; g0 = together ? depth : g0 + 1) {
+    const int g1 = together ? depth : g0 + 1;
+    struct LN {
+      TreeNode n;
+      int lev;
+    };
+    std::vector<LN> ns;
+    for (int lev = g0; lev < g1; ++lev)
+      for (int q = h->level_off[lev]; q < h->level_off[lev + 1]; ++q) ns.push_back({h->nodes[q], lev});
     int maxlen = 0;
-    for (auto& n : ns) maxlen = std::max(maxlen, std::max(n.m - n.l, n.r - n.m));
+    for (auto& x : ns) maxlen = std::max(maxlen, std::max(x.n.m - x.n.l, x.n.r - x.n.m));
     // chains of Schur complements from both ends towards m
     for (int t = 0; t < maxlen; ++t) {
       bool any = false;
-      for (auto& n : ns) {
-        if (t > 0 && t < n.m - n.l) { int j = n.l + t; g.add(blk(h->At, j), blk(Pw, j - 1), nullptr, blk(Tw, j)); any = true; }
-        if (t > 0 && t < n.r - n.m) { int j = n.r - t; g.add(blk(h->Bt, j), blk(Pw, j + 1), nullptr, blk(Tw, j)); any = true; }
+      for (auto& x : ns) {
+        const TreeNode& n = x.n;
+        if (t > 0 && t < n.m - n.l) {
+          int j = n.l + t;
+          g.add(blk(h->At, j), lb(PwL, x.lev, j - 1), nullptr, lb(TwL, x.lev, j));
+          any = true;
+        }
+        if (t > 0 && t < n.r - n.m) {
+          int j = n.r - t;
+          g.add(blk(h->Bt, j), lb(PwL, x.lev, j + 1), nullptr, lb(TwL, x.lev, j));
+          any = true;
+        }
       }
       if (any) g.flush(sc, 1.0, 0.0);
-      for (auto& n : ns) {
-        if (t > 0 && t < n.m - n.l) { int j = n.l + t; g.add(blk(Tw, j), blk(h->Bt, j - 1), blk(h->Ct, j), blk(Dw, j)); }
-        if (t > 0 && t < n.r - n.m) { int j = n.r - t; g.add(blk(Tw, j), blk(h->At, j + 1), blk(h->Ct, j), blk(Dw, j)); }
+      for (auto& x : ns) {
+        const TreeNode& n = x.n;
+        if (t > 0 && t < n.m - n.l) {
+          int j = n.l + t;
+          g.add(lb(TwL, x.lev, j), blk(h->Bt, j - 1), blk(h->Ct, j), lb(DwL, x.lev, j));
+        }
+        if (t > 0 && t < n.r - n.m) {
+          int j = n.r - t;
+          g.add(lb(TwL, x.lev, j), blk(h->At, j + 1), blk(h->Ct, j), lb(DwL, x.lev, j));
+        }
       }
       g.flush(sc, -1.0, 1.0);
-      for (auto& n : ns) {
-        if (t < n.m - n.l) { int j = n.l + t; iv.add(t == 0 ? blk(h->Ct, j) : blk(Dw, j), blk(Pw, j)); }
-        if (t < n.r - n.m) { int j = n.r - t; iv.add(t == 0 ? blk(h->Ct, j) : blk(Dw, j), blk(Pw, j)); }
+      for (auto& x : ns) {
+        const TreeNode& n = x.n;
+        if (t < n.m - n.l) {
+          int j = n.l + t;
+          iv.add(t == 0 ? blk(h->Ct, j) : lb(DwL, x.lev, j), lb(PwL, x.lev, j));
+        }
+        if (t < n.r - n.m) {
+          int j = n.r - t;
+          iv.add(t == 0 ? blk(h->Ct, j) : lb(DwL, x.lev, j), lb(PwL, x.lev, j));
+        }
       }
       iv.flush(sc);
     }
     // Sigma_m and R_mm
-    for (auto& n : ns) g.add(n.m > n.l ? blk(h->At, n.m) : Zw, n.m > n.l ? blk(Pw, n.m - 1) : Zw, nullptr, blk(Tw, n.m));
+    for (auto& x : ns) {
+      const TreeNode& n = x.n;
+      g.add(n.m > n.l ? blk(h->At, n.m) : Zw, n.m > n.l ? lb(PwL, x.lev, n.m - 1) : Zw, nullptr,
+            lb(TwL, x.lev, n.m));
+    }
     g.flush(sc, 1.0, 0.0);
-    for (auto& n : ns) g.add(blk(Tw, n.m), n.m > n.l ? blk(h->Bt, n.m - 1) : Zw, blk(h->Ct, n.m), blk(Dw, n.m));
+    for (auto& x : ns) {
+      const TreeNode& n = x.n;
+      g.add(lb(TwL, x.lev, n.m), n.m > n.l ? blk(h->Bt, n.m - 1) : Zw, blk(h->Ct, n.m), lb(DwL, x.lev, n.m));
+    }
     g.flush(sc, -1.0, 1.0);
-    for (auto& n : ns) g.add(n.m < n.r ? blk(h->Bt, n.m) : Zw, n.m < n.r ? blk(Pw, n.m + 1) : Zw, nullptr, blk(Tw, n.m));
+    for (auto& x : ns) {
+      const TreeNode& n = x.n;
+      g.add(n.m < n.r ? blk(h->Bt, n.m) : Zw, n.m < n.r ? lb(PwL, x.lev, n.m + 1) : Zw, nullptr,
+            lb(TwL, x.lev, n.m));
+    }
     g.flush(sc, 1.0, 0.0);
-    for (auto& n : ns) g.add(blk(Tw, n.m), n.m < n.r ? blk(h->At, n.m + 1) : Zw, blk(Dw, n.m), blk(Dw, n.m));
+    for (auto& x : ns) {
+      const TreeNode& n = x.n;
+      g.add(lb(TwL, x.lev, n.m), n.m < n.r ? blk(h->At, n.m + 1) : Zw, lb(DwL, x.lev, n.m), lb(DwL, x.lev, n.m));
+    }
     g.flush(sc, -1.0, 1.0);
-    for (auto& n : ns) iv.add(blk(Dw, n.m), Rb(lev, n.m));
+    for (auto& x : ns) iv.add(lb(DwL, x.lev, x.n.m), Rb(x.lev, x.n.m));
     iv.flush(sc);
     // propagate the block row outwards
     for (int t = 1; t <= maxlen; ++t) {
-      for (auto& n : ns) {
-        if (t <= n.m - n.l) { int j = n.m - t; g.add(Rb(lev, j + 1), blk(h->At, j + 1), nullptr, blk(Tw, j)); }
-        if (t <= n.r - n.m) { int j = n.m + t; g.add(Rb(lev, j - 1), blk(h->Bt, j - 1), nullptr, blk(Tw, j)); }
+      for (auto& x : ns) {
+        const TreeNode& n = x.n;
+        if (t <= n.m - n.l) {
+          int j = n.m - t;
+          g.add(Rb(x.lev, j + 1), blk(h->At, j + 1), nullptr, lb(TwL, x.lev, j));
+        }
+        if (t <= n.r - n.m) {
+          int j = n.m + t;
+          g.add(Rb(x.lev, j - 1), blk(h->Bt, j - 1), nullptr, lb(TwL, x.lev, j));
+        }
       }
       g.flush(sc, 1.0, 0.0);
-      for (auto& n : ns) {
-        if (t <= n.m - n.l) { int j = n.m - t; g.add(blk(Tw, j), blk(Pw, j), nullptr, Rb(lev, j)); }
-        if (t <= n.r - n.m) { int j = n.m + t; g.add(blk(Tw, j), blk(Pw, j), nullptr, Rb(lev, j)); }
+      for (auto& x : ns) {
+        const TreeNode& n = x.n;
+        if (t <= n.m - n.l) {
+          int j = n.m - t;
+          g.add(lb(TwL, x.lev, j), lb(PwL, x.lev, j), nullptr, Rb(x.lev, j));
+        }
+        if (t <= n.r - n.m) {
+          int j = n.m + t;
+          g.add(lb(TwL, x.lev, j), lb(PwL, x.lev, j), nullptr, Rb(x.lev, j));
+        }
       }
       g.flush(sc, 1.0, 0.0);
     }
-    for (auto& n : ns) {
-      if (n.l > 0) g.add(Rb(lev, n.l), blk(h->At, n.l), nullptr, blk(h->HL, n.m));
-      if (n.r < S - 1) g.add(Rb(lev, n.r), blk(h->Bt, n.r), nullptr, blk(h->HR, n.m));
+    for (auto& x : ns) {
+      const TreeNode& n = x.n;
+      if (n.l > 0) g.add(Rb(x.lev, n.l), blk(h->At, n.l), nullptr, blk(h->HL, n.m));
+      if (n.r < S - 1) g.add(Rb(x.lev, n.r), blk(h->Bt, n.r), nullptr, blk(h->HR, n.m));
     }
     g.flush(sc, 1.0, 0.0);
   }
@@ -673,6 +800,7 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_CUDA(cudaStreamSynchronize(st));
   BT_CUDA(cudaFreeAsync(dtab, st));
   BT_CUDA(cudaFreeAsync(dstatus, st));
+  if (lvl_buf) BT_CUDA(cudaFreeAsync(lvl_buf, st));
   h->stencil = hstatus[1] ? 0 : 1;
   h->stencil_unit = (h->stencil && !hstatus[2]) ? 1 : 0;
   if (hstatus[0]) {
