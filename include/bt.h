@@ -162,7 +162,10 @@ bt_status bt_solve(bt_handle h, const double* F, int64_t K, double* X, void* str
  * synchronises the stream and fills it; with info == NULL it is asynchronous
  * and never returns BT_ERR_NOCONV.  The residual is formed per opts->residual
  * (see bt_opts; for dense blocks with M = 64 or 128 exactly on the tensor
- * cores by default).  The handle keeps the refinement as CUDA graphs, one per
+ * cores by default).  The tensor-core precisions take block sizes M <= 128:
+ * below the tiles (64, 128) the factor blocks, interface blocks and internal
+ * panels are padded with zero rows and columns, whose unknowns stay zero
+ * (BT_ERR_UNSUPPORTED past 128).  The handle keeps the refinement as CUDA graphs, one per
  * argument key (F, X, K, precision, tol, max_it, residual method; at most 64,
  * least recently used out, dropped when a refinement buffer is reallocated): a
  * key's second call captures, later calls replay.  Calls on one handle must be

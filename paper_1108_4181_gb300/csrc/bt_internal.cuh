@@ -331,6 +331,10 @@ struct TcBuffers {
 
 // Column tile of the tensor-core kernels for a precision and block size (0: unsupported).
 int tc_col_tile(int precision, int M);
+// Block size of the tensor-core layouts: M padded to 64 or 128 (0 past 128).
+// Factor blocks, interface blocks and the block-transposed panels of the
+// tensor-core path carry Mt rows (and columns) per block, zero past M.
+int tc_M(const bt_handle_s* h);
 // Operand planes of a tensor-core precision (2 for the split BF16 precision).
 int tc_planes(int precision);
 // Builds the tensor-core factor copies for `precision` (once per handle).

@@ -172,14 +172,16 @@ __global__ void __launch_bounds__(256) k_resid_stencil(const double* __restrict_
 template <typename TR>
 __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict__ F, const double* __restrict__ X,
                                                       const double* __restrict__ Cd, TR* __restrict__ r, int64_t N,
-                                                      int M, int64_t K, int64_t Kp, int pass, int sp,
+                                                      int M, int Mr, int64_t K, int64_t Kp, int pass, int sp,
                                                       IrState* st, const int* gate) {
+  // Mr: rows per block row of the panel (M padded to the tensor-core tile;
+  // rows past M are written as zeros)
   constexpr int first = 0;
   if (st->done || (gate != nullptr && *(volatile const int*)gate == 0)) return;
-  const size_t plane = (size_t)N * Kp * M;
+  const size_t plane = (size_t)N * Kp * Mr;
   const size_t MK = (size_t)M * K;
   const int lane = threadIdx.x % 32;
-  const int tn = (int)((Kp + 31) / 32), tm = M / 8;
+  const int tn = (int)((Kp + 31) / 32), tm = Mr / 8;
   const int64_t nitem = N * tm * tn;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   Ssq acc;
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
     const double* fj = F + (size_t)j * MK + n;
     double f[8], xs[10], xu[8], xd[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) f[q] = ncol ? fj[(size_t)(m0 + q) * K] : 0.0;
+    for (int q = 0; q < 8; ++q) f[q] = (ncol && m0 + q < M) ? fj[(size_t)(m0 + q) * K] : 0.0;
     if (!first) {
 #pragma unroll
       for (int q = 0; q < 10; ++q) {
@@ -201,8 +203,9 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        xu[q] = (ncol && j > 0) ? xj[(size_t)(m0 + q) * K - MK] : 0.0;
-        xd[q] = (ncol && j + 1 < N) ? xj[(size_t)(m0 + q) * K + MK] : 0.0;
+        const bool in = ncol && m0 + q < M;
+        xu[q] = (in && j > 0) ? xj[(size_t)(m0 + q) * K - MK] : 0.0;
+        xd[q] = (in && j + 1 < N) ? xj[(size_t)(m0 + q) * K + MK] : 0.0;
       }
     }
     float v[8];
@@ -210,18 +213,18 @@ __global__ void __launch_bounds__(256, 2) k_resid_warp(const double* __restrict_
     for (int q = 0; q < 8; ++q) {
       const int m = m0 + q;
       double w = f[q];
-      if (!first) {
+      if (!first && m < M) {
         const double* cd = Cd + 3 * ((size_t)j * M + m);
         w = (w + xu[q]) + xd[q];
         w = fma(-cd[1], xs[q + 1], w);
         if (m > 0) w = fma(-cd[0], xs[q], w);
         if (m + 1 < M) w = fma(-cd[2], xs[q + 2], w);
       }
-      v[q] = ncol ? f64_to_f32_rz(w) : 0.f;
+      v[q] = (ncol && m < M) ? f64_to_f32_rz(w) : 0.f;
       acc.add(v[q]);
     }
     if (n < Kp) {
-      TR* o = r + ((size_t)j * Kp + n) * M + m0;
+      TR* o = r + ((size_t)j * Kp + n) * Mr + m0;
       if constexpr (sizeof(TR) == 2) {
         uint32_t h[4], l[4];
 #pragma unroll
@@ -586,11 +589,13 @@ __global__ void __launch_bounds__(256) k_x_add_panel(const float* __restrict__ D
 // HBM-bound: 8 bytes read and 2 sp (BF16) or 4 sp (FP32) bytes written per entry.
 template <typename TR>
 __global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F, TR* __restrict__ r, int64_t N, int M,
-                                                   int64_t K, int64_t Kp, int sp, IrState* st) {
+                                                   int Mr, int64_t K, int64_t Kp, int sp, IrState* st) {
+  // Mr: rows per block row of the panel (M padded to the tensor-core tile;
+  // rows past M are written as zeros)
   if (st->done) return;
-  const size_t plane = (size_t)N * Kp * M;
+  const size_t plane = (size_t)N * Kp * Mr;
   const int lane = threadIdx.x % 32;
-  const int tn = (int)((Kp + 31) / 32), tm = M / 16;
+  const int tn = (int)((Kp + 31) / 32), tm = Mr / 16;
   const int64_t nitem = N * tm * tn;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   Ssq acc;
@@ -603,10 +608,10 @@ __global__ void __launch_bounds__(256) k_round_rhs(const double* __restrict__ F,
     float v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      v[q] = n < K ? f64_to_f32_rz(fj[(size_t)q * K]) : 0.f;
+      v[q] = (n < K && m0 + q < M) ? f64_to_f32_rz(fj[(size_t)q * K]) : 0.f;
       acc.add(v[q]);
     }
-    TR* o = r + ((size_t)j * Kp + n) * M + m0;
+    TR* o = r + ((size_t)j * Kp + n) * Mr + m0;
     if constexpr (sizeof(TR) == 2) {
       uint32_t h[8], l[8];
 #pragma unroll
@@ -649,7 +654,8 @@ template <typename TR, int CW, bool TRANS>
 __global__ void k_resid_dense(const double* __restrict__ F, const double* __restrict__ X,
                               const double* __restrict__ A, const double* __restrict__ B,
                               const double* __restrict__ C, TR* __restrict__ r, int64_t N, int M, int64_t K,
-                              int64_t ldr, int pass, int sp, IrState* st) {
+                              int64_t ldr, int pass, int sp, IrState* st, int Mr) {
+  // TRANS: the panel has Mr >= M rows per block row (rows past M get zeros)
   if (st->done) return;
   extern __shared__ double sm[];
   const int CG = blockDim.x / M, kt = CW * CG;
@@ -691,11 +697,17 @@ __global__ void k_resid_dense(const double* __restrict__ F, const double* __rest
       if (in) part += acc[c] * acc[c];
       if (TRANS) {
         if (col + c < ldr)
-          put_planes(r, ((size_t)j * ldr + col + c) * M + m, (size_t)N * ldr * M, sp,
+          put_planes(r, ((size_t)j * ldr + col + c) * Mr + m, (size_t)N * ldr * Mr, sp,
                      in ? f64_to_f32_rz(acc[c]) : 0.f);
       } else if (in) {
         r[j * (size_t)M * ldr + (size_t)m * ldr + col + c] = to_lp<TR>(acc[c]);
       }
+    }
+  }
+  if (TRANS && Mr > M) {  // the padding rows of the tile's columns
+    for (int e = t; e < (Mr - M) * kt; e += blockDim.x) {
+      const int64_t cl = col0 + e / (Mr - M);
+      if (cl < ldr) put_planes(r, ((size_t)j * ldr + cl) * Mr + M + e % (Mr - M), (size_t)N * ldr * Mr, sp, 0.f);
     }
   }
   (void)pass;
@@ -885,7 +897,7 @@ bt_status launch_fallback(bt_handle_s* h, const double* F, const double* X, TR* 
     static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
     const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
     const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
-    k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, &st->range);
+    k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, M, K, Kp, pass, sp, st, &st->range);
   } else {
     const size_t n = (size_t)h->N * M * K;
     static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_stencil<TR>), 256, 0);
@@ -950,6 +962,7 @@ template <typename TR>
 bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* r, int64_t K, int64_t Kp, bool trans,
                           int sp, int first, int pass, IrState* st, int rmode, cudaStream_t s) {
   const int M = (int)h->M;
+  const int Mr = trans ? tc_M(h) : M;  // rows per block row of the tensor-core panel
   const bool digits = rmode == 2;
   if (digits && !first)  // dense blocks: the exact residual on the tensor cores
     return launch_resid_digits(h, F, X, K, trans ? 0 : 1, sizeof(TR) == 4, r, sp, &st->done, st->rn2, &st->cur,
@@ -969,17 +982,17 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
   }
   ProfScope ps(h, s, first ? "rhs_round" : "residual");
   if (first || h->stencil) {
-    if (trans) {  // the tensor-core panels: M is 64 or 128
+    if (trans) {  // the tensor-core panels: Mr is 64 or 128
       if (first) {
         static const int grid = resident_grid(reinterpret_cast<const void*>(&k_round_rhs<TR>), 256, 0);
-        const int64_t items = h->N * (M / 16) * ((Kp + 31) / 32);
+        const int64_t items = h->N * (Mr / 16) * ((Kp + 31) / 32);
         const int blocks = (int)std::min<int64_t>((items + 7) / 8, grid);
-        k_round_rhs<TR><<<blocks, 256, 0, s>>>(F, r, h->N, M, K, Kp, sp, st);
+        k_round_rhs<TR><<<blocks, 256, 0, s>>>(F, r, h->N, M, Mr, K, Kp, sp, st);
       } else {
         static const int grid = resident_grid(reinterpret_cast<const void*>(&k_resid_warp<TR>), 256, 0);
-        const int64_t nwarp_items = h->N * (M / 8) * ((Kp + 31) / 32);
+        const int64_t nwarp_items = h->N * (Mr / 8) * ((Kp + 31) / 32);
         const int blocks = (int)std::min<int64_t>((nwarp_items + 7) / 8, grid);
-        k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, K, Kp, pass, sp, st, nullptr);
+        k_resid_warp<TR><<<blocks, 256, 0, s>>>(F, X, h->Cdiag, r, h->N, M, Mr, K, Kp, pass, sp, st, nullptr);
       }
     } else {
       const size_t n = (size_t)h->N * M * K;
@@ -998,12 +1011,12 @@ bt_status launch_residual(bt_handle_s* h, const double* F, const double* X, TR* 
       if (smem > 48 * 1024)
         BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_resid_dense<TR, CW, true><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
-          F, X, h->A, h->B, h->C, r, h->N, M, K, Kp, pass, sp, st);
+          F, X, h->A, h->B, h->C, r, h->N, M, K, Kp, pass, sp, st, Mr);
     } else {
       if (smem > 48 * 1024)
         BT_CUDA(cudaFuncSetAttribute(k_resid_dense<TR, CW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_resid_dense<TR, CW, false><<<dim3((unsigned)h->N, (unsigned)ntiles), M * CG, smem, s>>>(
-          F, X, h->A, h->B, h->C, r, h->N, M, K, K, pass, 1, st);
+          F, X, h->A, h->B, h->C, r, h->N, M, K, K, pass, 1, st, M);
     }
   }
   BT_CUDA(cudaGetLastError());
@@ -1047,12 +1060,15 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   const bool tcore = prec == BT_PREC_BF16 || prec == BT_PREC_TF32 || prec == BT_PREC_BF16X3;
   const int sp = tcore ? tc_planes(prec) : 1;
   const int M = (int)h->M;
+  // rows per block row of the low-precision panels: the tensor-core tile
+  // (64 or 128, zero padding past M), else M
+  const int Mt = tcore ? tc_M(h) : M;
   int64_t Kp = K;
   size_t eb = sizeof(float);
   if (tcore) {
     const int nt = tc_col_tile(prec, M);
-    if (nt == 0) {
-      set_error("bt_solve_ex: the tensor-core precisions support block sizes M = 64 and M = 128");
+    if (nt == 0 || Mt == 0) {
+      set_error("bt_solve_ex: the tensor-core precisions support block sizes M <= 128");
       return BT_ERR_UNSUPPORTED;
     }
     Kp = (K + nt - 1) / nt * nt;
@@ -1062,14 +1078,15 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   // the FP32 double-word residual for unit stencils, where they apply), 1 FP64
   // on the CUDA cores, 2 the tensor-core digit residual, 3 double-word
   const bool dig_ok = resid_digits_supported(h, K);
-  const bool dw_ok = resid_dw_supported(h);
+  // the double-word residual writes unpadded tensor-core panels
+  const bool dw_ok = resid_dw_supported(h) && (!tcore || Mt == M);
   if (o.residual == 2 && !dig_ok) {
     set_error("bt_solve_ex: the tensor-core residual needs dense blocks with M = 64 or M = 128");
     return BT_ERR_UNSUPPORTED;
   }
   if (o.residual == 3 && !dw_ok) {
     set_error("bt_solve_ex: the double-word residual needs A_j = B_j = I, C_j = tridiag(-1, c, -1) with "
-              "2^-30 <= |c| <= 2^30, and M a multiple of 8");
+              "2^-30 <= |c| <= 2^30, and M a multiple of 8 (64 or 128 with the tensor-core precisions)");
     return BT_ERR_UNSUPPORTED;
   }
   const bool digits = o.residual == 2 || (o.residual == 0 && dig_ok);
@@ -1079,13 +1096,13 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
   // with its residual (launch_residual_panels)
   const bool pairflow = tcore && rmode == 3 && prec == BT_PREC_BF16X3 && M == 128;
   const void* before[5] = {h->lp_r, h->lp_d, h->lp_c, h->lp_x, h->lp_x1};
-  const size_t panel = (size_t)sp * h->N * M * Kp * eb;
+  const size_t panel = (size_t)sp * h->N * Mt * Kp * eb;
   // series terms [depth][S] and, for the tensor-core step 2.2, one node sum per tree node
-  const size_t cbytes = ((size_t)h->depth * h->S + h->nodes.size()) * M * Kp * sizeof(float);
+  const size_t cbytes = ((size_t)h->depth * h->S + h->nodes.size()) * Mt * Kp * sizeof(float);
   BT_TRY(grow(&h->lp_r, &h->lp_panel_bytes, panel, s));
   BT_TRY(grow(&h->lp_d, &h->lp_d_bytes, panel, s));
   BT_TRY(grow(&h->lp_c, &h->lp_c_bytes, cbytes, s));
-  if (tcore) BT_TRY(grow(&h->lp_x, &h->lp_x_bytes, (size_t)h->N * M * Kp * sizeof(float), s));
+  if (tcore) BT_TRY(grow(&h->lp_x, &h->lp_x_bytes, (size_t)h->N * Mt * Kp * sizeof(float), s));
   if (pairflow) BT_TRY(grow(&h->lp_x1, &h->lp_x1_bytes, (size_t)h->N * M * K * sizeof(float), s));
   if (before[0] != h->lp_r || before[1] != h->lp_d || before[2] != h->lp_c || before[3] != h->lp_x ||
       before[4] != h->lp_x1)
@@ -1150,9 +1167,9 @@ bt_status solve_refined(bt_handle_s* h, const double* F, int64_t K, double* X, c
       const dim3 g((unsigned)tiles, (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->N, 2432 / tiles)));
       if (prec == BT_PREC_BF16 || prec == BT_PREC_BF16X3)
         k_col_ssq<__nv_bfloat16><<<g, 256, 0, q>>>(reinterpret_cast<const __nv_bfloat16*>(h->lp_r), sp, tcore ? 1 : 0,
-                                                   h->N, M, K, ldr, sc->colssq, st);
+                                                   h->N, Mt, K, ldr, sc->colssq, st);
       else
-        k_col_ssq<float><<<g, 256, 0, q>>>(reinterpret_cast<const float*>(h->lp_r), sp, tcore ? 1 : 0, h->N, M, K,
+        k_col_ssq<float><<<g, 256, 0, q>>>(reinterpret_cast<const float*>(h->lp_r), sp, tcore ? 1 : 0, h->N, Mt, K,
                                            ldr, sc->colssq, st);
       k_set_check<<<1, 256, (size_t)sc->nsets * sizeof(double), q>>>(sc->colssq, sc->colset, K, sc->nsets, sc->n2,
                                                                     tol2c, st);
@@ -1386,7 +1403,7 @@ bt_status residual_diag(bt_handle_s* h, const double* F, const double* X, int64_
         BT_CUDA(cudaFuncSetAttribute(k_resid_dense<double, CW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
       k_resid_dense<double, CW, false><<<dim3((unsigned)h->N, (unsigned)((K + kt - 1) / kt)), M * CG, smem, s>>>(
-          F, X, h->A, h->B, h->C, R, h->N, M, K, K, 0, 1, st);
+          F, X, h->A, h->B, h->C, R, h->N, M, K, K, 0, 1, st, M);
     }
     BT_CUDA(cudaGetLastError());
   }

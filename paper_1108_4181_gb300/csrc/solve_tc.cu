@@ -1747,12 +1747,13 @@ __global__ void k_cast_fb(const double* __restrict__ D, const double* __restrict
 // row-major FP64 solution, one warp per (block row j, 8 rows m, 32 columns n): lane n
 // reads its 8 FP32 corrections (32 contiguous bytes of the block-transposed
 // panel) and updates rows m0..m0+7 of column n of the row-major solution
-// (each a coalesced 256-byte row); no shared memory, no barrier.  M % 8 == 0.
+// (each a coalesced 256-byte row); no shared memory, no barrier.  The panel
+// has Mt >= M rows per block row (Mt % 8 == 0); rows past M are padding.
 __global__ void __launch_bounds__(256) k_x_update_warp(const float* __restrict__ d, double* __restrict__ X, int N,
-                                                       int M, int K, int Kp, int accumulate, const int* done) {
+                                                       int M, int Mt, int K, int Kp, int accumulate, const int* done) {
   if (flag_set(done)) return;
   const int lane = threadIdx.x % 32;
-  const int tn = (K + 31) / 32, tm = M / 8;
+  const int tn = (K + 31) / 32, tm = (M + 7) / 8;
   const int64_t nitem = (int64_t)N * tm * tn;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < nitem; it += warps) {
@@ -1760,16 +1761,19 @@ __global__ void __launch_bounds__(256) k_x_update_warp(const float* __restrict__
     const int m0 = (int)((it / tn) % tm) * 8;
     const int64_t j = it / ((int64_t)tn * tm);
     if (n >= K) continue;
-    const float4* src = reinterpret_cast<const float4*>(d + ((size_t)j * Kp + n) * M + m0);
+    const float4* src = reinterpret_cast<const float4*>(d + ((size_t)j * Kp + n) * Mt + m0);
     const float4 a = __ldg(src), b = __ldg(src + 1);
     const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     double* x = X + ((size_t)j * M + m0) * K + n;
+    const int rows = min(8, M - m0);
     if (accumulate) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[(size_t)q * K] += f32_to_f64(v[q]);
+      for (int q = 0; q < 8; ++q)
+        if (q < rows) x[(size_t)q * K] += f32_to_f64(v[q]);
     } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[(size_t)q * K] = f32_to_f64(v[q]);
+      for (int q = 0; q < 8; ++q)
+        if (q < rows) x[(size_t)q * K] = f32_to_f64(v[q]);
     }
   }
 }
@@ -1926,12 +1930,23 @@ __global__ void k_tc_dichotomy(E* __restrict__ w, const float* __restrict__ cbuf
 }
 
 // FP32 transposed copies of the interface blocks (element (m, k) at k*M + m).
-__global__ void k_cast_transpose(const double* __restrict__ src, float* __restrict__ dst, size_t nblk, int M) {
-  const size_t MM = (size_t)M * M, n = nblk * MM;
+// Entry e of a block array padded from M x M to Mt x Mt blocks (zero rows and
+// columns past M): the padded system holds the real one in its leading rows
+// and columns, and every padded unknown stays zero through the solve.
+__device__ __forceinline__ double padded(const double* __restrict__ src, size_t e, int M, int Mt) {
+  const size_t MMt = (size_t)Mt * Mt;
+  const size_t b = e / MMt, o = e % MMt;
+  const int r = (int)(o / Mt), c = (int)(o % Mt);
+  return (r < M && c < M) ? src[b * M * M + (size_t)r * M + c] : 0.0;
+}
+
+// Transposed FP32 copy of nblk blocks, padded to Mt x Mt.
+__global__ void k_cast_transpose(const double* __restrict__ src, float* __restrict__ dst, size_t nblk, int M, int Mt) {
+  const size_t MMt = (size_t)Mt * Mt, n = nblk * MMt;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t bI = e / MM, o = e % MM;
-    const int k = (int)(o / M), m = (int)(o % M);
-    dst[e] = (float)src[bI * MM + (size_t)m * M + k];
+    const size_t bI = e / MMt, o = e % MMt;
+    const int k = (int)(o / Mt), m = (int)(o % Mt);
+    dst[e] = (k < M && m < M) ? (float)src[bI * M * M + (size_t)m * M + k] : 0.f;
   }
 }
 
@@ -1975,12 +1990,13 @@ bt_status make_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int
 template <typename E, int SP>
 __global__ void k_cast_factors(const double* __restrict__ D, const double* __restrict__ Ee,
                                const double* __restrict__ G, const double* __restrict__ U,
-                               const double* __restrict__ V, E* __restrict__ out, size_t nb) {
+                               const double* __restrict__ V, E* __restrict__ out, size_t nb, int M, int Mt) {
+  // nb: entries of one padded factor array (N Mt Mt)
   const size_t n = 5 * nb;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const size_t w = e / nb, o = e % nb;
     const double* src = w == 0 ? D : w == 1 ? Ee : w == 2 ? G : w == 3 ? U : V;
-    const double x = src[o];
+    const double x = padded(src, o, M, Mt);
     if (SP == 2) {
       E hi, lo;
       // remainder taken against the FP64 value, then rounded
@@ -1995,10 +2011,12 @@ __global__ void k_cast_factors(const double* __restrict__ D, const double* __res
   }
 }
 
-// Split-BF16 copy of n FP64 values: plane 0 at dst, plane 1 (remainder) at dst + plane.
-__global__ void k_cast_split(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n, size_t plane) {
+// Split-BF16 copy of blocks padded to Mt x Mt (n padded entries): plane 0 at
+// dst, plane 1 (remainder) at dst + plane.
+__global__ void k_cast_split(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n, size_t plane,
+                             int M, int Mt) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double x = src[e];
+    const double x = padded(src, e, M, Mt);
     const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
     dst[e] = hi;
     dst[e + plane] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
@@ -2032,7 +2050,8 @@ __global__ void __launch_bounds__(256) k_node_sums(const float* __restrict__ c, 
 bt_status make_tc_interface(bt_handle_s* h, cudaStream_t st) {
   if (h->tc_if_bf16x3) return BT_OK;
   const int S = (int)h->S, L = (int)h->L, N = (int)h->N, depth = h->depth;
-  const size_t MM = (size_t)h->M * h->M;
+  const int Mt = tc_M(h);
+  const size_t MM = (size_t)Mt * Mt;
   const size_t nblk = (size_t)(4 + depth) * S;
   void* buf = nullptr;
   BT_TRY(h->arena.alloc(&buf, 2 * nblk * MM * sizeof(__nv_bfloat16)));
@@ -2044,7 +2063,7 @@ bt_status make_tc_interface(bt_handle_s* h, cudaStream_t st) {
   } srcs[] = {{h->AK, (size_t)S}, {h->BK, (size_t)S}, {h->R, (size_t)depth * S}, {h->HL, (size_t)S}, {h->HR, (size_t)S}};
   size_t at = 0;
   for (const Src& q : srcs) {
-    k_cast_split<<<512, 256, 0, st>>>(q.p, d + at * MM, q.nb * MM, plane);
+    k_cast_split<<<512, 256, 0, st>>>(q.p, d + at * MM, q.nb * MM, plane, (int)h->M, Mt);
     at += q.nb;
   }
   BT_CUDA(cudaGetLastError());
@@ -2280,7 +2299,8 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
       ProfScope ps(h, st, "tc_correct");
       // first solve: X = d written by the correction itself (no FP32 round trip)
       k_tc_correct_ta<CT, true><<<dim3(ntiles, S, chunks), CT::THREADS, smem, st>>>(
-          tm_fac_c, tm_wc, (const E*)w, tb.d, accumulate == 0 ? X : nullptr, accumulate == 2 ? tb.drow : nullptr,
+          tm_fac_c, tm_wc, (const E*)w, tb.d, (accumulate == 0 && h->M == CT::M) ? X : nullptr,
+          accumulate == 2 ? tb.drow : nullptr,
           (int)K, N, L, S, Kp, L > 1 ? rpc : 0, done,
           status);
     } else {
@@ -2291,13 +2311,15 @@ bt_status run_tc(bt_handle_s* h, const TcBuffers& tb, int64_t K, double* X, int 
           tm_fac_c, tm_wc, tm_d, (const E*)w, tb.d, N, L, S, Kp, L > 1 ? rpc : 0, done, status);
     }
     BT_CUDA(cudaGetLastError());
-    const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && accumulate == 0;
-    if (!direct_x && accumulate != 2) {  // M is 64 or 128
-      const int64_t nitem = (int64_t)((K + 31) / 32) * (M / 8) * N;
+    // the correction writes X itself in the first split-BF16 solve (M = 128, unpadded)
+    const bool direct_x = CC::SW && CC::SP == 2 && CC::M == 128 && accumulate == 0 && h->M == CC::M;
+    if (!direct_x && accumulate != 2) {
+      const int Mr = (int)h->M;  // the true block size; the panel has M (= Mt) rows
+      const int64_t nitem = (int64_t)((K + 31) / 32) * ((Mr + 7) / 8) * N;
       static const int grid = resident_grid(reinterpret_cast<const void*>(&k_x_update_warp), 256, 0);
       const int blocks = (int)std::min<int64_t>((nitem + 7) / 8, grid);
       ProfScope ps(h, st, "x_update");
-      k_x_update_warp<<<blocks, 256, 0, st>>>(tb.d, X, N, M, (int)K, Kp, accumulate, done);
+      k_x_update_warp<<<blocks, 256, 0, st>>>(tb.d, X, N, Mr, M, (int)K, Kp, accumulate, done);
     }
   }
   BT_CUDA(cudaGetLastError());
@@ -2326,15 +2348,18 @@ using CoX64 = Cfg<__nv_bfloat16, 64, 64, 6, 2, 4>;
 int tc_col_tile(int precision, int M) {
   (void)precision;
   // internal panels are padded to a multiple of every column tile in use
-  return (M == 128 || M == 64) ? 128 : 0;
+  return (M >= 1 && M <= 128) ? 128 : 0;
 }
+
+int tc_M(const bt_handle_s* h) { return h->M <= 64 ? 64 : h->M <= 128 ? 128 : 0; }
 
 int tc_planes(int precision) { return precision == BT_PREC_BF16X3 ? 2 : 1; }
 
 bt_status make_f32t_factors(bt_handle_s* h, cudaStream_t st) {
   TransposedF32& f = h->f32t;
   if (f.ready) return BT_OK;
-  const size_t MM = (size_t)h->M * h->M;
+  const int Mt = tc_M(h);
+  const size_t MM = (size_t)Mt * Mt;
   struct Item {
     float** dst;
     const double* src;
@@ -2343,7 +2368,7 @@ bt_status make_f32t_factors(bt_handle_s* h, cudaStream_t st) {
                {&f.HL, h->HL, (size_t)h->S}, {&f.HR, h->HR, (size_t)h->S}};
   for (auto& it : items) {
     BT_TRY(h->arena.alloc((void**)it.dst, it.nblk * MM * sizeof(float)));
-    k_cast_transpose<<<512, 256, 0, st>>>(it.src, *it.dst, it.nblk, (int)h->M);
+    k_cast_transpose<<<512, 256, 0, st>>>(it.src, *it.dst, it.nblk, (int)h->M, Mt);
   }
   BT_CUDA(cudaGetLastError());
   f.ready = true;
@@ -2364,26 +2389,27 @@ bt_status make_tc_factors(bt_handle_s* h, int precision, cudaStream_t st) {
   }
   void** slot = precision == BT_PREC_BF16 ? &h->tc_fac_bf16 : precision == BT_PREC_TF32 ? &h->tc_fac_tf32 : &h->tc_fac_bf16x3;
   if (*slot) return BT_OK;
-  const size_t nb = (size_t)h->N * h->M * h->M;
+  const int Mt = tc_M(h), M = (int)h->M;
+  const size_t nb = (size_t)h->N * Mt * Mt;
   const int sp = tc_planes(precision);
   const size_t eb = precision == BT_PREC_TF32 ? 4 : 2;
   BT_TRY(h->arena.alloc(slot, (size_t)sp * 5 * nb * eb));
   if (precision == BT_PREC_BF16)
     k_cast_factors<__nv_bfloat16, 1><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
-                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb);
+                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb, M, Mt);
   else if (precision == BT_PREC_TF32)
     k_cast_factors<float, 1><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V, reinterpret_cast<float*>(*slot),
-                                                   nb);
+                                                   nb, M, Mt);
   else
     k_cast_factors<__nv_bfloat16, 2><<<1024, 256, 0, st>>>(h->Dinv, h->E, h->G, h->U, h->V,
-                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb);
+                                                           reinterpret_cast<__nv_bfloat16*>(*slot), nb, M, Mt);
   BT_CUDA(cudaGetLastError());
   return BT_OK;
 }
 
 bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K, double* X, int accumulate,
                    const int* done, int* status, cudaStream_t st) {
-  const int M = (int)h->M;
+  const int M = tc_M(h);  // the block size, padded to the tile
   if (precision == BT_PREC_BF16) {
     if (M == 128) return run_tc<__nv_bfloat16, SwB128, CoB128>(h, tb, K, X, accumulate, done, status, st);
     if (M == 64) return run_tc<__nv_bfloat16, SwB64, CoB64>(h, tb, K, X, accumulate, done, status, st);
@@ -2394,7 +2420,7 @@ bt_status solve_tc(bt_handle_s* h, int precision, const TcBuffers& tb, int64_t K
     if (M == 128) return run_tc<__nv_bfloat16, SwX128, CoX128>(h, tb, K, X, accumulate, done, status, st);
     if (M == 64) return run_tc<__nv_bfloat16, SwX64, CoX64>(h, tb, K, X, accumulate, done, status, st);
   }
-  set_error("the tensor-core solve supports block sizes M = 64 and M = 128");
+  set_error("the tensor-core solve supports block sizes M <= 128");
   return BT_ERR_UNSUPPORTED;
 }
 

@@ -177,9 +177,9 @@ def test_refined_plan_arguments(bt):
             plan.info(1)
         assert ei.value.name == "BT_ERR_ARG"
         plan.close()
-        # the tensor-core precisions refuse block sizes they do not support, as bt_solve_ex does
-    with bt.factor(*(_t(a) for a in gen.dominant_blocks(N, 24, seed=1)), 4) as f24:
-        F = _t(gen.uniform_rhs(N, 24, 3, seed=2))
+    # the tensor-core precisions refuse block sizes past the largest tile, as bt_solve_ex does
+    with bt.factor(*(_t(a) for a in gen.dominant_blocks(8, 150, seed=1)), 4) as f150:
+        F = _t(gen.uniform_rhs(8, 150, 3, seed=2))
         with pytest.raises(bt.BtError) as ei:
-            bt.BatchPlan([f24], [F], [torch.empty_like(F)], precision="bf16x3")
+            bt.BatchPlan([f150], [F], [torch.empty_like(F)], precision="bf16x3")
         assert ei.value.name == "BT_ERR_UNSUPPORTED"

@@ -147,12 +147,44 @@ def test_tc_refined_acoustic_full_size(bt, prec):
 
 
 def test_tc_unsupported_block_size(bt):
-    A, B, C = gen.dominant_blocks(16, 8, seed=1)
-    F = gen.uniform_rhs(16, 8, 2, seed=2)
+    # past the largest tile (M > 128) the tensor-core precisions refuse
+    A, B, C = gen.dominant_blocks(8, 150, seed=1)
+    F = gen.uniform_rhs(8, 150, 2, seed=2)
     with bt.factor(_t(A), _t(B), _t(C), 4) as fac:
-        with pytest.raises(bt.BtError) as ei:
-            fac.solve(_t(F), precision="bf16")
-        assert ei.value.name == "BT_ERR_UNSUPPORTED"
+        for prec in TC:
+            with pytest.raises(bt.BtError) as ei:
+                fac.solve(_t(F), precision=prec)
+            assert ei.value.name == "BT_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("kind,N,M,K,S", [
+    ("dense", 64, 60, 40, 8),       # the paper's block size 60, padded to the 64 tile
+    ("dense", 48, 100, 130, 6),     # padded to 128, a ragged 128-column tile
+    ("dense", 32, 8, 3, 4),         # a small block
+    ("stencil", 64, 30, 33, 8),     # a unit stencil padded to 64 (FP64 stencil residual)
+    ("stencil", 40, 120, 20, 5),    # padded to 128
+])
+def test_tc_refined_padded_block_sizes(bt, prec, kind, N, M, K, S):
+    # block sizes below the tiles run on the tensor cores with the factor
+    # blocks, interface blocks and panels padded by zero rows and columns
+    if kind == "dense":
+        A, B, C = gen.dominant_blocks(N, M, seed=N + M)
+        F = gen.uniform_rhs(N, M, K, seed=K)
+    else:
+        A, B, C = gen.acoustic_system(N, M)
+        F = gen.acoustic_rhs(N, M, K, seed=K)
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    with bt.factor(_t(A), _t(B), _t(C), S) as fac:
+        X, info = fac.solve(_t(F), precision=prec, tol=1e-12, return_info=True)
+        X0, info0 = fac.solve(_t(F), precision=prec, tol=1.0, return_info=True)
+    X = X.cpu().numpy()
+    assert info["converged"]
+    assert oracle.rel_res(A, B, C, X, F) <= 2e-12
+    assert oracle.rel_err(X, Xr) <= 1e-10
+    assert oracle.col_err(X, Xr) <= 1e-10
+    # the first (unrefined) solve carries the tensor-core precision: it is a solve, not noise
+    assert info0["iters"] == 0 and oracle.rel_err(X0.cpu().numpy(), Xr) <= 5e-2
 
 
 def test_split_precision_needs_fewer_passes(bt):
