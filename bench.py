@@ -207,7 +207,7 @@ TRAFFIC = {
     # algorithmic; the kernels stream every panel once, so traffic scales with
     # the unknowns
     "resid_dw": {"file": "paper_1108_4181_gb300/csrc/refine.cu",
-                 "sha256": "bc4c0c3cafba81ddcb96db201f260473578a077fff9e90ddebd67fcd7b21991c",
+                 "sha256": "a616e6fea87ae5fc43ec4ea87e452a9f01ede64230a0503fb0d77c6397ca7966",
                  "bytes_per_unknown": 44.04},
 }
 
