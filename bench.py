@@ -414,6 +414,17 @@ def run_ours(args):
         graph_launches = fixed_n + info["iters"] * body_n
         launches = int(round(graph_launches * args.steps))
 
+    # ---- the same solve held to a tolerance that takes one more refinement
+    # pass (how the step time grows with the passes taken)
+    tighter = None
+    if precision != "f64" and info is not None:
+        tol2 = tol * 1e-2
+        k2 = max(1, min(args.steps, 5))
+        ms2, _ = _time_solves(fac, Fd, X, precision, tol2, k2, 3, barrier, stream, profile=False)
+        _, info2 = fac.solve(Fd, precision=precision, tol=tol2, out=X, return_info=True)
+        tighter = {"tol": tol2, "ms_per_step": ranks_max(ms2 / k2), "iters": info2["iters"],
+                   "rel_res": info2["rel_res"]}
+
     # ---- the plain FP64 GPU path beside it (fewer steps; its own warm-up)
     fp64 = None
     if precision != "f64" and not args.no_fp64_path:
@@ -474,6 +485,7 @@ def run_ours(args):
                    "parallelism": f"K-replicas x{ws}" if ws > 1 else "single GPU"},
         "gpu_launches": launches,
         "refinement": info,
+        "refinement_tighter_tol": tighter,
         "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": unknowns * 8,
                 "d2h_bytes_per_step": unknowns * 8},
         "roofline": roof,

@@ -30,6 +30,8 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "bt_internal.cuh"
 
 namespace bt {
@@ -218,6 +220,133 @@ __global__ void __launch_bounds__(1024) k_inverse_batched(const double* const* _
     for (int e = threadIdx.x; e < MM; e += nt) dst[e] = a[e];
 }
 
+// ---------------------------------------------------------------------------
+// The same Gauss-Jordan inversion on a two-CTA thread-block cluster per
+// matrix: CTA r holds columns [r Mc, (r+1) Mc) (Mc = ceil(M / 2)) in its
+// shared memory, so each SM does half of the FP64 elimination.  Step k: the
+// owner of column k finds the pivot row p, forms the multipliers of the
+// interchanged column (row k takes row p's entry and vice versa) and writes
+// p and the multipliers into both CTAs' shared memory (double-buffered by
+// the parity of k); one cluster barrier; then every CTA interchanges rows k
+// and p, scales row k and eliminates in its own columns.  The interchanges
+// are undone at the end by writing column c of the result to the column the
+// composed interchanges send it to.  Singular or non-finite pivots: as above.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* __restrict__ tab, int M, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double sh[];
+  __shared__ int s_p;
+  const int rank = (int)cl.block_rank();
+  const int mat = blockIdx.x / 2;
+  const double* src = tab[2 * mat + 0];
+  double* dst = const_cast<double*>(tab[2 * mat + 1]);
+  const int Mc = (M + 1) / 2;
+  const int c0 = rank * Mc, nc = min(Mc, M - c0);    // global columns c0 .. c0 + nc - 1
+  double* a = sh;                                    // [M][Mc], row-major
+  double* fbuf = sh + (size_t)M * Mc;                // [2][M] multipliers
+  int* pbuf = reinterpret_cast<int*>(fbuf + 2 * M);  // [2] pivot rows
+  int* perm = pbuf + 2;                              // [M]
+  int* pos = perm + M;                               // [M]
+  const int nt = blockDim.x;
+  for (int e = threadIdx.x; e < M * Mc; e += nt) {
+    const int i = e / Mc, lc = e % Mc;
+    a[e] = lc < nc ? src[(size_t)i * M + c0 + lc] : 0.0;
+  }
+  // elimination mapping: thread -> (local column jt, first row it0), rows strided by rstep
+  const int rstep = max(1, nt / Mc);
+  const int jt = threadIdx.x < rstep * Mc ? threadIdx.x % Mc : Mc;
+  const int it0 = threadIdx.x / Mc;
+  __syncthreads();
+  cl.sync();
+  for (int k = 0; k < M; ++k) {
+    const int owner = k / Mc, lk = k - owner * Mc, b = k & 1;
+    if (rank == owner) {
+      if (threadIdx.x < 32) {  // pivot search over rows k..M-1 of column k
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < M; i += 32) {
+          const double v = fabs(a[(size_t)i * Mc + lk]);
+          if (v > best || (v == best && i < bi)) {
+            best = v;
+            bi = i;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        if (threadIdx.x == 0) s_p = bi;
+      }
+      __syncthreads();
+      const int p = s_p;
+      // multipliers of the interchanged column k into both CTAs
+      for (int e = threadIdx.x; e < 2 * M; e += nt) {
+        const int i = e % M, r = e / M;
+        double f = a[(size_t)(i == k ? p : i == p ? k : i) * Mc + lk];
+        if (i == k && (!(f != 0.0) || !isfinite(f))) {
+          atomicExch(status, 1);
+          f = 1.0;
+        }
+        double* fr = cl.map_shared_rank(fbuf, r);
+        fr[b * M + i] = f;
+        if (i == 0) cl.map_shared_rank(pbuf, r)[b] = p;
+      }
+    }
+    cl.sync();
+    const int p = pbuf[b];
+    const double* f = fbuf + b * M;
+    const double pv = f[k];
+    if (threadIdx.x == 0) perm[k] = p;
+    // interchange rows k and p, scale row k (column k becomes 1 / pivot)
+    if (p != k)
+      for (int j = threadIdx.x; j < Mc; j += nt) {
+        const double t = a[(size_t)k * Mc + j];
+        a[(size_t)k * Mc + j] = a[(size_t)p * Mc + j];
+        a[(size_t)p * Mc + j] = t;
+      }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Mc; j += nt) {
+      const double v = (j == lk && rank == owner) ? 1.0 : a[(size_t)k * Mc + j];
+      a[(size_t)k * Mc + j] = v / pv;
+    }
+    __syncthreads();
+    // eliminate column k from every other row
+    if (jt < Mc) {
+      const double pk = a[(size_t)k * Mc + jt];
+      const bool colk = rank == owner && jt == lk;
+      for (int i = it0; i < M; i += rstep) {
+        if (i == k) continue;
+        const size_t e = (size_t)i * Mc + jt;
+        a[e] = fma(-f[i], pk, colk ? 0.0 : a[e]);
+      }
+    }
+    __syncthreads();
+  }
+  // the interchanges undone as column interchanges, last first: position j
+  // ends up holding elimination column pos[j]; column c goes to perm[c]
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < M; ++c) pos[c] = c;
+    for (int k = M - 1; k >= 0; --k) {
+      const int q = perm[k];
+      const int t = pos[k];
+      pos[k] = pos[q];
+      pos[q] = t;
+    }
+    for (int j = 0; j < M; ++j) perm[pos[j]] = j;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < M * nc; e += nt) {
+    const int i = e / nc, lc = e % nc;
+    dst[(size_t)i * M + perm[c0 + lc]] = a[(size_t)i * Mc + lc];
+  }
+  cl.sync();  // no CTA leaves while its partner may still write into its shared memory
+}
+
 // Plain device copy (grid-stride).
 __global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -395,6 +524,15 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
                                    : M * sizeof(double) + M * sizeof(int);
   BT_CUDA(cudaFuncSetAttribute(k_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
   const int inv_threads = (int)std::min<size_t>(1024, std::max<size_t>(32, ((MM + 31) / 32) * 32));
+  // two-CTA clusters when a CTA's half of the matrix fits in shared memory
+  const int Mc = (M + 1) / 2;
+  const size_t clu_smem = ((size_t)M * Mc + 2 * (size_t)M) * sizeof(double) + (2 + 2 * (size_t)M) * sizeof(int);
+  const int clu_threads = (int)std::min<size_t>(1024, std::max<size_t>(64, (((size_t)M * Mc + 31) / 32) * 32));
+  bool clu_ok = M >= 32 && clu_smem <= 200 * 1024;
+  if (clu_ok)
+    clu_ok = cudaFuncSetAttribute(k_inverse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clu_smem) ==
+             cudaSuccess;
+  cudaGetLastError();
   // GEMM tile: 32 when 64-tiles would pad the block by more than about 15 % in area
   const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
   const int GT = (double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64;
@@ -436,7 +574,23 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
         else
           k_gemm_batched<64><<<grid, 256, 0, q>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
       } else {
-        k_inverse_batched<<<nb, inv_threads, inv_smem, q>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
+        if (clu_ok) {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(2 * nb);
+          cfg.blockDim = dim3(clu_threads);
+          cfg.dynamicSmemBytes = clu_smem;
+          cfg.stream = q;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = 2;
+          at[0].val.clusterDim.y = 1;
+          at[0].val.clusterDim.z = 1;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          BT_CUDA(cudaLaunchKernelEx(&cfg, k_inverse_cluster, dtab + o.off + 2 * (size_t)b0, M, dstatus));
+        } else {
+          k_inverse_batched<<<nb, inv_threads, inv_smem, q>>>(dtab + o.off + 2 * (size_t)b0, M, use_smem, dstatus);
+        }
       }
     }
   }
