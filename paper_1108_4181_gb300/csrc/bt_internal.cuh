@@ -369,6 +369,16 @@ bt_status batch_enqueue(bt_batch_s* b, cudaStream_t st);
 // failure (a stage index, or -1); synchronous.
 bt_status batch_set_debug(bt_batch_s* b, unsigned long long limit_ns, int skip_stage);
 
+// FP64-accurate batched block products on the tensor cores from BF16 digit
+// slices (gemm_digits.cu): whether a block size is supported (M = 128), the
+// scratch for batches of up to emax entries, and one batched product
+// D = alpha X Y + beta Z over a device table of (X, Y, Z, D) pointers per
+// entry; *status is set when a bounded wait gave up.
+bool digit_gemm_supported(int M);
+size_t digit_gemm_bytes(int emax);
+bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int E, double alpha, double beta,
+                         int* status, cudaStream_t st);
+
 // Refined batches (batch_refined.cu): build (groups, packing tables, prepared
 // refinements, the captured graph), run (re-captured first if a handle's
 // refinement buffers moved), status (per-group convergence), release.

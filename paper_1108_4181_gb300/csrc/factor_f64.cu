@@ -26,6 +26,7 @@
 //   HL = R_ml At_l (l > 0),  HR = R_mr Bt_r (r < S-1).
 // The recurrences for R follow from R P_node = [0 .. I .. 0] column by column.
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -516,8 +517,12 @@ struct InvBatch {
 };
 
 // Runs an uploaded schedule (pointer table dtab) of batched GEMMs and
-// inverses on `st`; singular pivots set dstatus[0].
-bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dstatus, cudaStream_t st) {
+// inverses on `st`; singular pivots set dstatus[0].  With gstatus non-null
+// and M = 128, the dense products run on the tensor cores from BF16 digit
+// slices (gemm_digits.cu: an FP64-level bound, FP64 issue rate left behind);
+// a bounded wait that gives up there sets *gstatus.
+bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dstatus, cudaStream_t st,
+                       int* gstatus = nullptr) {
   const size_t MM = (size_t)M * M;
   const int use_smem = M <= INV_SMEM_MAX ? 1 : 0;
   const size_t inv_smem = use_smem ? (MM + M) * sizeof(double) + M * sizeof(int)
@@ -540,6 +545,22 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
   // (measured at N=2048, M=128, S=64: 109 -> 86 ms per factorisation; M=64: 50 -> 32 ms)
   const int GT = M <= 192 ? 16 : ((double)pad32 * pad32 < 0.85 * (double)pad64 * pad64 ? 32 : 64);
   const int tiles = (M + GT - 1) / GT;
+  // digit-slice products: scratch per lane (the lanes run concurrently)
+  auto dense = [&](const Op& o) {
+    return o.bp.x <= -(M - 1) && o.bp.y >= M - 1 && o.bp.z <= -(M - 1) && o.bp.w >= M - 1;
+  };
+  const bool dig = gstatus != nullptr && digit_gemm_supported(M);
+  int emax = 0;
+  bool lane1_dense = false;
+  if (dig)
+    for (const Op& o : sc.ops)
+      if (o.kind == 0 && dense(o)) {
+        emax = std::max(emax, std::min(o.batch, 65535));
+        lane1_dense = lane1_dense || o.lane == 1;
+      }
+  void* dbuf[2] = {nullptr, nullptr};
+  for (int l = 0; l < (lane1_dense ? 2 : 1) && emax > 0; ++l)
+    BT_CUDA(cudaMallocAsync(&dbuf[l], digit_gemm_bytes(emax), st));
   // lane 1: created on first use, lowest priority (lane 0 holds the critical path)
   cudaStream_t lane1 = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -570,7 +591,9 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
     // grid.z / grid.x limits: split very large batches
     for (int b0 = 0; b0 < o.batch; b0 += 65535) {
       int nb = std::min(65535, o.batch - b0);
-      if (o.kind == 0) {
+      if (o.kind == 0 && emax > 0 && dense(o)) {
+        BT_TRY(digit_gemm_run(dbuf[o.lane], emax, dtab + o.off + 4 * (size_t)b0, nb, o.alpha, o.beta, gstatus, q));
+      } else if (o.kind == 0) {
         dim3 grid(tiles, tiles, nb);
         if (GT == 16)
           k_gemm_batched<16><<<grid, 256, 0, q>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
@@ -603,6 +626,8 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
     BT_CUDA(cudaEventRecord(ev1, lane1));
     BT_CUDA(cudaStreamWaitEvent(st, ev1, 0));
   }
+  for (void* b : dbuf)
+    if (b) BT_CUDA(cudaFreeAsync(b, st));  // after lane 1's work (joined above)
   if (lane1) {
     // the stream and events may go once the work is enqueued (their
     // destruction is deferred until it completes)
@@ -922,11 +947,11 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   const double** dtab = nullptr;
   int* dstatus = nullptr;
   BT_CUDA(cudaMallocAsync((void**)&dtab, std::max<size_t>(1, sc.tab.size()) * sizeof(double*), st));
-  BT_CUDA(cudaMallocAsync((void**)&dstatus, 3 * sizeof(int), st));
-  BT_CUDA(cudaMemsetAsync(dstatus, 0, 3 * sizeof(int), st));
+  BT_CUDA(cudaMallocAsync((void**)&dstatus, 4 * sizeof(int), st));
+  BT_CUDA(cudaMemsetAsync(dstatus, 0, 4 * sizeof(int), st));
   BT_CUDA(cudaMemcpyAsync(dtab, sc.tab.data(), sc.tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
 
-  BT_TRY(run_schedule(sc, dtab, M, dstatus, st));
+  BT_TRY(run_schedule(sc, dtab, M, dstatus, st, dstatus + 3));
 
   // stencil detection (A_j = B_j = I, tridiagonal C_j) for the residual
   k_detect_stencil<<<1024, 256, 0, st>>>(h->A, h->B, h->C, N, M, dstatus + 1);
@@ -954,14 +979,18 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   BT_CUDA(cudaMemcpyAsync(h->d_nodes, hn.data(), hn.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   BT_CUDA(cudaMemcpyAsync(h->d_mid_level, hml.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
 
-  int hstatus[3] = {0, 0, 0};
-  BT_CUDA(cudaMemcpyAsync(hstatus, dstatus, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hstatus[4] = {0, 0, 0, 0};
+  BT_CUDA(cudaMemcpyAsync(hstatus, dstatus, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   BT_CUDA(cudaStreamSynchronize(st));
   BT_CUDA(cudaFreeAsync(dtab, st));
   BT_CUDA(cudaFreeAsync(dstatus, st));
   if (lvl_buf) BT_CUDA(cudaFreeAsync(lvl_buf, st));
   h->stencil = hstatus[1] ? 0 : 1;
   h->stencil_unit = (h->stencil && !hstatus[2]) ? 1 : 0;
+  if (hstatus[3]) {
+    set_error("bt_factor: a bounded wait of the tensor-core block products gave up");
+    return BT_ERR_TIMEOUT;
+  }
   if (hstatus[0]) {
     set_error("bt_factor: a pivot block of the block sweep or of the reduced system is singular or non-finite");
     return BT_ERR_SINGULAR;
