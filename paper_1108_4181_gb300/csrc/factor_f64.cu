@@ -442,11 +442,23 @@ __global__ void k_band_profile(const double* A, const double* B, int64_t N, int 
   }
 }
 
+// D_e = X_e for every batch entry (pairs of block pointers), 4 values a thread.
+__global__ void k_copy_blocks(const double* const* __restrict__ tab, size_t MM) {
+  const double* X = tab[2 * blockIdx.y];
+  double* D = const_cast<double*>(tab[2 * blockIdx.y + 1]);
+  const size_t i0 = (size_t)blockIdx.x * 1024 + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const size_t i = i0 + (size_t)u * 256;
+    if (i < MM) D[i] = X[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Schedule builder
 // ---------------------------------------------------------------------------
 struct Op {
-  int kind;  // 0 = GEMM, 1 = INV, 2 = join (lane 0 waits for lane 1)
+  int kind;  // 0 = GEMM, 1 = INV, 2 = join (lane 0 waits for lane 1), 3 = copy
   int batch;
   size_t off;  // into the pointer table
   double alpha, beta;
@@ -459,13 +471,29 @@ struct Op {
 struct Schedule {
   std::vector<const double*> tab;
   std::vector<Op> ops;
+  // The identity block: a product X I with alpha = 1 and no Z is the copy
+  // D = X (exact on every path; the digit-slice products could not balance
+  // the contraction index of such a product against X's column scales)
+  const double* ident = nullptr;
   // GEMM batch under construction
   void gemm(double alpha, double beta, int4 bp, const std::vector<const double*>& X,
             const std::vector<const double*>& Y, const std::vector<const double*>& Z,
             const std::vector<double*>& D, int lane = 0) {
     if (D.empty()) return;
-    Op o{0, (int)D.size(), tab.size(), alpha, beta, bp, lane};
-    for (size_t b = 0; b < D.size(); ++b) {
+    std::vector<size_t> prod, copy;
+    for (size_t b = 0; b < D.size(); ++b)
+      (ident && Y[b] == ident && alpha == 1.0 && (beta == 0.0 || Z.empty() || !Z[b]) ? copy : prod).push_back(b);
+    if (!copy.empty()) {
+      Op o{3, (int)copy.size(), tab.size(), 0.0, 0.0, make_int4(0, 0, 0, 0), lane};
+      for (size_t b : copy) {
+        tab.push_back(X[b]);
+        tab.push_back(D[b]);
+      }
+      ops.push_back(o);
+    }
+    if (prod.empty()) return;
+    Op o{0, (int)prod.size(), tab.size(), alpha, beta, bp, lane};
+    for (size_t b : prod) {
       tab.push_back(X[b]);
       tab.push_back(Y[b]);
       tab.push_back(Z.empty() ? nullptr : Z[b]);
@@ -591,7 +619,10 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
     // grid.z / grid.x limits: split very large batches
     for (int b0 = 0; b0 < o.batch; b0 += 65535) {
       int nb = std::min(65535, o.batch - b0);
-      if (o.kind == 0 && emax > 0 && dense(o)) {
+      if (o.kind == 3) {
+        dim3 grid((unsigned)((MM + 1023) / 1024), (unsigned)nb);
+        k_copy_blocks<<<grid, 256, 0, q>>>(dtab + o.off + 2 * (size_t)b0, MM);
+      } else if (o.kind == 0 && emax > 0 && dense(o)) {
         BT_TRY(digit_gemm_run(dbuf[o.lane], emax, dtab + o.off + 4 * (size_t)b0, nb, o.alpha, o.beta, gstatus, q));
       } else if (o.kind == 0) {
         dim3 grid(tiles, tiles, nb);
@@ -727,6 +758,7 @@ bt_status factor_f64(bt_handle_s* h, const double* A_in, const double* B_in, con
   auto Bj = [&](int64_t j) -> const double* { return j == N - 1 ? Zw : blk(h->B, j); };
 
   Schedule sc;
+  sc.ident = Iw;
   GemmBatch g;
   InvBatch iv;
   // GEMM operand bands: A_j or B_j on the left (onX) or on the right (onY)
@@ -1016,6 +1048,7 @@ bt_status factor_left_responses(bt_handle_s* h, cudaStream_t st) {
   k_set_identity<<<(int)((MM + 255) / 256), 256, 0, st>>>(Iw, M);
   BT_CUDA(cudaGetLastError());
   Schedule sc;
+  sc.ident = Iw;
   GemmBatch g;
   auto blk = [&](double* base, int64_t j) { return base + (size_t)j * MM; };
   for (int64_t t = 1; t < L; ++t) {

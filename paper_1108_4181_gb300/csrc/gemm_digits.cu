@@ -8,11 +8,21 @@
 //   D_e = alpha X_e Y_e + beta Z_e      (every batch entry e; M x M row-major
 //                                        FP64 blocks; alpha = +-1, beta 0 or 1)
 //
+// Balancing.  X Y = (X 2^T)(2^-T Y) for T = diag(t_k); with cx(k) and ry(k)
+// the exponents (floor log2) of the largest |X[r][k]| over r and |Y[k][c]|
+// over c, t_k = floor((ry(k) - cx(k)) / 2) evens out the two sides of every
+// contraction index.  Scaling the contraction index by powers of two (X D,
+// D^-1 Y: the unknowns of a block row scaled by D) changes t_k by exactly the
+// opposite amount, so the digits below, and the product, do not change; an
+// index whose column of X or row of Y is zero contributes nothing and is
+// dropped.  Below, x and y are the balanced values x 2^t_k and 2^-t_k y.
+//
 // Digit split.  x = X[r][k] with max_k |X[r][k]| < 2^ex(r) is taken in fixed
 // point f = round(x 2^(56 - ex)), |f| <= 2^56, written in balanced base 128,
 //   f = sum_{p=0..7} a_p 128^(7-p),   |a_0| <= 128,  |a_p| <= 64 (p >= 1):
 // integers of at most 8 significant bits, exact in BF16.  Y's columns take
-// their own scales ey(c) and digits b_q the same way.
+// their own scales ey(c) and digits b_q the same way.  The split works on the
+// significand bits alone (integer pipe), the balancing included.
 //
 // Products.  sum_k x y = 2^(ex + ey - 112) sum_{p,q} 128^(14 - p - q) sum_k a_p b_q
 // (plus the operands' rounding).  The 36 pairs with p + q = d <= 7 accumulate
@@ -33,12 +43,14 @@
 // (15 - d) 128^(14 - d) < 7.05 2^54 units of 2^(ex + ey - 112), i.e.
 // 1.77 2^(ex + ey - 56) per term) and the rounding of T (at most
 // 2^-53 M 2^(ex + ey)): in all below M 2^(ex(r) + ey(c) - 52), an FP64-level
-// bound relative to M max_k |X[r][k]| max_k |Y[k][c]| (>= M 2^(ex + ey - 2)),
+// bound relative to M max_k |X[r][k] 2^t_k| max_k |2^-t_k Y[k][c]|
+// (>= M 2^(ex + ey - 2)),
 // before the final alpha / beta step's one rounding.  The bound and the
 // exactness of every accumulator are pinned on the CPU with exact integer
 // arithmetic (tests/test_digit_gemm_model.py).  A row or column holding a
 // NaN or an infinity gives NaN entries.
 //
+//   k_gdig_balance t [E][M] from the column maxima of X and the row maxima of Y
 //   k_gdig_rows   X digits [E][8][M][M] (row r, contraction k) and ex
 //   k_gdig_cols   Y digits [E][8][M][M] (column c, contraction k) and ey
 //   k_gemm_digits one CTA per (entry, 64-row half): TMA warp = MMA thread,
@@ -98,106 +110,175 @@ __device__ __forceinline__ long long fixed56(double v, int e) {
   return (b >> 63) ? -(long long)q : (long long)q;
 }
 
-// The 8 balanced base-128 digits of round(v 2^(56 - e)) (|v| < 2^e).
-__device__ __forceinline__ void digits8(double v, int e, __nv_bfloat16 (&d)[GD]) {
+// A small integer (|r| < 2^22) as the bits of an FP32 value without a
+// conversion instruction: r + 1.5 2^23 in the bits, minus 1.5 2^23 (exact).
+__device__ __forceinline__ uint32_t small_int_f32_bits(int r) {
+  return __float_as_uint(__int_as_float(0x4B400000 + r) - 12582912.0f);
+}
+
+// The 8 balanced base-128 digits of round(v 2^(56 - e)) (|v| < 2^e), each as
+// FP32 bits; every digit (|d| <= 128) is exact in BF16, whose bits are the
+// upper half of the FP32 ones.
+__device__ __forceinline__ void digits8(double v, int e, uint32_t (&d)[GD]) {
   long long f = fixed56(v, e);
 #pragma unroll
   for (int p = GD - 1; p >= 1; --p) {
-    const long long r = ((f + 64) & 127) - 64;
-    d[p] = __float2bfloat16_rn((float)r);
+    const int r = (int)((f + 64) & 127) - 64;
+    d[p] = small_int_f32_bits(r);
     f = (f - r) >> 7;
   }
-  d[0] = __float2bfloat16_rn((float)f);
+  d[0] = small_int_f32_bits((int)f);
 }
 
-__device__ __forceinline__ int scale_exp(double amax, bool bad) {
+// Four digits (FP32 bits, exact in BF16) packed as four BF16 values.
+__device__ __forceinline__ uint2 pack_bf16x4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  return make_uint2(__byte_perm(a, b, 0x7632), __byte_perm(c, d, 0x7632));
+}
+
+constexpr int kNoExp = -0x40000000;     // exponent of a zero (or skipped) value: below every other
+constexpr int kDropT = 0x40000000;      // t_k of a contraction index that contributes nothing
+
+__device__ __forceinline__ bool bits_nonfinite(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7FF) == 0x7FF;
+}
+
+// floor(log2 |v|) from the bits (subnormals included); kNoExp for a zero, a
+// NaN or an infinity.  No FP64 instruction.
+__device__ __forceinline__ int exp_floor(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  const int be = (int)(b >> 52);
+  if (b == 0 || be == 0x7FF) return kNoExp;
+  if (be != 0) return be - 1023;
+  return -1023 - __clzll((long long)(b << 12));  // subnormal: the leading bit of the fraction
+}
+
+__device__ __forceinline__ int warp_max_int(int m) {
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
+}
+
+// The scale e of a row of X (column of Y) with every balanced |value| < 2^e
+// (that of frexp of the largest): 0 for an all-zero row, kBadExp if the row
+// holds a NaN or an infinity.
+__device__ __forceinline__ int scale_from_max(int m, bool bad) {
   if (bad) return kBadExp;
-  int e = 0;
-  if (amax > 0.0) frexp(amax, &e);
-  return e;
+  return m == kNoExp ? 0 : m + 1;
+}
+
+// One CTA per entry: t_k from the column maxima of X_e (thread: column k
+// over half the rows) and the row maxima of Y_e (warp: 16 rows, a row per pass).
+__global__ void __launch_bounds__(256) k_gdig_balance(const double* const* __restrict__ tab, int* __restrict__ tk) {
+  __shared__ int cx[2][GM];
+  __shared__ int ry[GM];
+  const int e = blockIdx.x, tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  const double* X = tab[4 * e];
+  const double* Y = tab[4 * e + 1];
+  {
+    const int k = tid % GM, r0 = (tid / GM) * (GM / 2);
+    int m = kNoExp;
+#pragma unroll 8
+    for (int r = r0; r < r0 + GM / 2; ++r) m = max(m, exp_floor(X[(size_t)r * GM + k]));
+    cx[tid / GM][k] = m;
+  }
+  for (int k = w * 16; k < w * 16 + 16; ++k) {
+    int m = kNoExp;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) m = max(m, exp_floor(Y[(size_t)k * GM + lane + 32 * i]));
+    m = warp_max_int(m);
+    if (lane == 0) ry[k] = m;
+  }
+  __syncthreads();
+  if (tid < GM) {
+    const int a = max(cx[0][tid], cx[1][tid]), b = ry[tid];
+    tk[(size_t)e * GM + tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
+  }
 }
 
 // One warp per row r of X_e: its scale and 8 digit rows.
 __global__ void __launch_bounds__(256) k_gdig_rows(const double* const* __restrict__ tab, int E,
-                                                   __nv_bfloat16* __restrict__ Xd, int* __restrict__ ex) {
+                                                   const int* __restrict__ tk, __nv_bfloat16* __restrict__ Xd,
+                                                   int* __restrict__ ex) {
   const int lane = threadIdx.x % 32;
   const int64_t w = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
   if (w >= (int64_t)E * GM) return;
   const int e = (int)(w / GM), r = (int)(w % GM);
   const double* X = tab[4 * e];
   double v[4];
+  const int4 t4 = *reinterpret_cast<const int4*>(tk + (size_t)e * GM + 4 * lane);
+  const int t[4] = {t4.x, t4.y, t4.z, t4.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) v[i] = X[(size_t)r * GM + 4 * lane + i];
-  double m = 0.0;
+  int m = kNoExp;
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    bad = bad || !isfinite(v[i]);
-    m = fmax(m, fabs(v[i]));
+    bad = bad || bits_nonfinite(v[i]);
+    const int x = exp_floor(v[i]);
+    if (x != kNoExp && t[i] != kDropT) m = max(m, x + t[i]);
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  m = warp_max_int(m);
   bad = __any_sync(0xffffffffu, bad);
-  const int es = scale_exp(m, bad);
+  const int es = scale_from_max(m, bad);
   if (lane == 0) ex[(size_t)e * GM + r] = es;
-  __nv_bfloat16 d[4][GD];
+  uint32_t d[4][GD];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (bad) {
+    if (bad || t[i] == kDropT) {
 #pragma unroll
-      for (int p = 0; p < GD; ++p) d[i][p] = __float2bfloat16_rn(0.f);
+      for (int p = 0; p < GD; ++p) d[i][p] = 0u;
     } else {
-      digits8(v[i], es, d[i]);
+      digits8(v[i], es - t[i], d[i]);  // round(v 2^t 2^(56 - es))
     }
   }
 #pragma unroll
-  for (int p = 0; p < GD; ++p) {
-    const __nv_bfloat162 q01 = __halves2bfloat162(d[0][p], d[1][p]), q23 = __halves2bfloat162(d[2][p], d[3][p]);
+  for (int p = 0; p < GD; ++p)
     *reinterpret_cast<uint2*>(Xd + (((size_t)e * GD + p) * GM + r) * GM + 4 * lane) =
-        make_uint2(*reinterpret_cast<const uint32_t*>(&q01), *reinterpret_cast<const uint32_t*>(&q23));
-  }
+        pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
 }
 
 // One CTA per (entry e, 32 columns of Y_e): the columns through shared memory,
 // their scales, and 8 digit rows per column (contraction k contiguous).
 __global__ void __launch_bounds__(256) k_gdig_cols(const double* const* __restrict__ tab, int E,
-                                                   __nv_bfloat16* __restrict__ Yd, int* __restrict__ ey) {
+                                                   const int* __restrict__ tk, __nv_bfloat16* __restrict__ Yd,
+                                                   int* __restrict__ ey) {
   __shared__ double ys[GM][33];
   const int e = blockIdx.x / (GM / 32), c0 = (blockIdx.x % (GM / 32)) * 32;
   const double* Y = tab[4 * e + 1];
   for (int i = threadIdx.x; i < GM * 32; i += 256) ys[i / 32][i % 32] = Y[(size_t)(i / 32) * GM + c0 + i % 32];
   __syncthreads();
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int4 t4 = *reinterpret_cast<const int4*>(tk + (size_t)e * GM + 4 * lane);
+  const int t[4] = {t4.x, t4.y, t4.z, t4.w};  // rows 4 lane .. 4 lane + 3: Y scaled by 2^-t
   for (int jj = 0; jj < 4; ++jj) {
     const int j = w * 4 + jj;
     double v[4];  // rows 4 lane .. 4 lane + 3 of column j
-    double m = 0.0;
+    int m = kNoExp;
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       v[i] = ys[4 * lane + i][j];
-      bad = bad || !isfinite(v[i]);
-      m = fmax(m, fabs(v[i]));
+      bad = bad || bits_nonfinite(v[i]);
+      const int x = exp_floor(v[i]);
+      if (x != kNoExp && t[i] != kDropT) m = max(m, x - t[i]);
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    m = warp_max_int(m);
     bad = __any_sync(0xffffffffu, bad);
-    const int es = scale_exp(m, bad);
+    const int es = scale_from_max(m, bad);
     if (lane == 0) ey[(size_t)e * GM + c0 + j] = es;
-    __nv_bfloat16 d[4][GD];
+    uint32_t d[4][GD];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (bad) {
+      if (bad || t[i] == kDropT) {
 #pragma unroll
-        for (int p = 0; p < GD; ++p) d[i][p] = __float2bfloat16_rn(0.f);
+        for (int p = 0; p < GD; ++p) d[i][p] = 0u;
       } else {
-        digits8(v[i], es, d[i]);
+        digits8(v[i], es + t[i], d[i]);  // round(v 2^-t 2^(56 - es))
       }
     }
 #pragma unroll
-    for (int p = 0; p < GD; ++p) {
-      const __nv_bfloat162 q01 = __halves2bfloat162(d[0][p], d[1][p]), q23 = __halves2bfloat162(d[2][p], d[3][p]);
+    for (int p = 0; p < GD; ++p)
       *reinterpret_cast<uint2*>(Yd + (((size_t)e * GD + p) * GM + c0 + j) * GM + 4 * lane) =
-          make_uint2(*reinterpret_cast<const uint32_t*>(&q01), *reinterpret_cast<const uint32_t*>(&q23));
-    }
+          pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
   }
 }
 
@@ -296,11 +377,11 @@ __global__ void __launch_bounds__(GTHREADS, 1)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int r = h * 64 + rl + i;
-          long long cd[GD];
+          long long cd[GD];  // exact integers below 2^24: through int32 (FP32 pipe)
 #pragma unroll
           for (int d = 0; d < 4; ++d) {
-            cd[d] = (long long)__uint_as_float(a[8 * d + i]);
-            cd[d + 4] = (long long)__uint_as_float(b[8 * d + i]);
+            cd[d] = (int)__uint_as_float(a[8 * d + i]);
+            cd[d + 4] = (int)__uint_as_float(b[8 * d + i]);
           }
           const long long hi = ((cd[0] * 128 + cd[1]) * 128 + cd[2]) * 128 + cd[3];
           const long long lo = ((cd[4] * 128 + cd[5]) * 128 + cd[6]) * 128 + cd[7];
@@ -310,13 +391,20 @@ __global__ void __launch_bounds__(GTHREADS, 1)
           if (exr == kBadExp || eyc == kBadExp) {
             v = __longlong_as_double(0x7ff8000000000000LL);
           } else {
-            // alpha 2^(ex + ey - 63) from its exponent bits (a power of two: the product is exact)
+            // hi, lo (|x| < 2^44) as doubles exactly: x + 1.5 2^52 in the bits, minus 1.5 2^52
+            const double dh = __longlong_as_double(0x4338000000000000LL + hi) - 6755399441055744.0;
+            const double dl = __longlong_as_double(0x4338000000000000LL + lo) - 6755399441055744.0;
+            const double t = fma(dh, 268435456.0, dl);
+            // alpha 2^(ex + ey - 63): added to the exponent field and the sign bit (exact)
+            // while the result stays a normal number, else through ldexp
             const int sx = exr + eyc - 2 * GFB + 7 * (GD - 1);
-            const double t = fma((double)hi, 268435456.0, (double)lo);
-            if (sx > -1023 && sx < 1024)
-              v = t * __longlong_as_double(((long long)(sx + 1023) << 52) | (alpha < 0.0 ? (long long)1 << 63 : 0));
-            else
-              v = alpha * ldexp(t, sx);
+            const long long tb = __double_as_longlong(t);
+            const int te = (int)((tb >> 52) & 0x7FF);
+            if (te != 0 && te + sx > 0 && te + sx < 0x7FF) {
+              v = __longlong_as_double((tb + (long long)sx * (1LL << 52)) ^ (alpha < 0.0 ? (long long)(1ULL << 63) : 0LL));
+            } else {
+              v = t == 0.0 ? 0.0 : alpha * ldexp(t, sx);
+            }
           }
           if (beta != 0.0) v = fma(beta, Z[o], v);
           D[o] = v;
@@ -368,7 +456,7 @@ bt_status gd_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_r
 bool digit_gemm_supported(int M) { return M == GM; }
 
 size_t digit_gemm_bytes(int emax) {
-  return (size_t)emax * (2 * (size_t)GD * GM * GM * sizeof(__nv_bfloat16) + 2 * (size_t)GM * sizeof(int));
+  return (size_t)emax * (2 * (size_t)GD * GM * GM * sizeof(__nv_bfloat16) + 3 * (size_t)GM * sizeof(int));
 }
 
 bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int E, double alpha, double beta,
@@ -381,11 +469,13 @@ bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int
   __nv_bfloat16* Yd = Xd + (size_t)emax * GD * GM * GM;
   int* ex = reinterpret_cast<int*>(Yd + (size_t)emax * GD * GM * GM);
   int* ey = ex + (size_t)emax * GM;
+  int* tk = ey + (size_t)emax * GM;
   CUtensorMap tx, ty;
   BT_TRY(gd_map(&tx, Xd, (uint64_t)E * GD * GM, 64));
   BT_TRY(gd_map(&ty, Yd, (uint64_t)E * GD * GM, 128));
-  k_gdig_rows<<<(unsigned)((E * GM + 7) / 8), 256, 0, st>>>(dtab, E, Xd, ex);
-  k_gdig_cols<<<(unsigned)(E * (GM / 32)), 256, 0, st>>>(dtab, E, Yd, ey);
+  k_gdig_balance<<<(unsigned)E, 256, 0, st>>>(dtab, tk);
+  k_gdig_rows<<<(unsigned)((E * GM + 7) / 8), 256, 0, st>>>(dtab, E, tk, Xd, ex);
+  k_gdig_cols<<<(unsigned)(E * (GM / 32)), 256, 0, st>>>(dtab, E, tk, Yd, ey);
   static bool attr = false;
   if (!attr) {
     BT_CUDA(cudaFuncSetAttribute(k_gemm_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GSMEM));

@@ -1,6 +1,9 @@
 """Pins of the digit-slice block product (csrc/gemm_digits.cu) on the CPU.
 
-The method: x with max_k |X[r][k]| < 2^ex is taken in fixed point
+The method: every contraction index k is balanced, X[:, k] 2^t_k and
+2^-t_k Y[k, :] with t_k = floor((ry(k) - cx(k)) / 2) from the exponents of the
+column maxima of X and the row maxima of Y (an index whose column or row is
+zero is dropped); a balanced x with max_k |x| < 2^ex is taken in fixed point
 f = round(x 2^(56 - ex)) and written as 8 balanced base-128 digits; likewise Y's
 columns; the 36 digit pairs with p + q <= 7 are summed per level p + q (each
 level an exact FP32 sum on the tensor cores), and the levels are combined as
@@ -8,8 +11,11 @@ hi 2^28 + lo with one rounding, scaled by 2^(ex + ey - 63).  Here every step
 is carried out in exact integer arithmetic and compared with the exact
 rational product: the digits' ranges, the exactness of every level sum in FP32
 (|c_d| < 2^24 for M = 128), and the stated bound
-|D - sum_k X[r][k] Y[k][c]| <= M 2^(ex(r) + ey(c) - 52).  Planted mistakes (a
-dropped level, a wrong level weight, a transposed operand) break the bound.
+|D - sum_k X[r][k] Y[k][c]| <= M 2^(ex(r) + ey(c) - 52).  Scaling the
+contraction index by powers of two (X D, D^-1 Y) leaves the result unchanged,
+so a system whose unknowns span many binades keeps FP64-level products.
+Planted mistakes (a dropped level, a wrong level weight, a transposed operand,
+the balancing applied to one side only) break the bound.
 """
 
 import math
@@ -26,8 +32,24 @@ def _exp(amax):
     return math.frexp(amax)[1] if amax > 0 else 0
 
 
+def _floor_log2(v):
+    return math.frexp(abs(v))[1] - 1 if v != 0 else None
+
+
+def _balance(X, Y):
+    """t_k (None: the index is dropped) from the exponents of max_r |X[r][k]|
+    and max_c |Y[k][c]|."""
+    t = []
+    for k in range(M):
+        a = max((_floor_log2(v) for v in X[:, k] if v != 0), default=None)
+        b = max((_floor_log2(v) for v in Y[k, :] if v != 0), default=None)
+        t.append(None if a is None or b is None else (b - a) // 2)
+    return t
+
+
 def _digits(x, e):
     f = round(Fraction(x) * Fraction(2) ** (FB - e))  # nearest, ties to even
+    f = int(f)
     d = [0] * GD
     for p in range(GD - 1, 0, -1):
         r = ((f + 64) & 127) - 64
@@ -37,12 +59,18 @@ def _digits(x, e):
     return d
 
 
-def _product(X, Y, rows, cols, drop_level=None, weight=128, transpose_y=False):
+def _product(X, Y, rows, cols, drop_level=None, weight=128, transpose_y=False, one_sided=False):
     Yu = Y.T if transpose_y else Y
-    ex = {r: _exp(float(np.max(np.abs(X[r])))) for r in rows}
-    ey = {c: _exp(float(np.max(np.abs(Yu[:, c])))) for c in cols}
-    xd = {r: [_digits(X[r, k], ex[r]) for k in range(M)] for r in rows}
-    yd = {c: [_digits(Yu[k, c], ey[c]) for k in range(M)] for c in cols}
+    t = _balance(X, Yu)
+    # balanced operands, exact (powers of two; dropped indices as zeros)
+    Xb = [[Fraction(0) if t[k] is None else Fraction(float(X[r, k])) * Fraction(2) ** t[k] for k in range(M)]
+          for r in range(M)]
+    Yb = [[Fraction(0) if t[k] is None else Fraction(float(Yu[k, c])) * (1 if one_sided else Fraction(2) ** -t[k])
+           for c in range(M)] for k in range(M)]
+    ex = {r: _exp(max(abs(v) for v in Xb[r])) for r in rows}
+    ey = {c: _exp(max(abs(Yb[k][c]) for k in range(M))) for c in cols}
+    xd = {r: [_digits(Xb[r][k], ex[r]) for k in range(M)] for r in rows}
+    yd = {c: [_digits(Yb[k][c], ey[c]) for k in range(M)] for c in cols}
     out, levels = {}, []
     for r in rows:
         for c in cols:
@@ -80,6 +108,7 @@ ROWS, COLS = [0, 3, 5, 77, 127], [0, 9, 64, 100]
 
 def test_digits_levels_and_bound():
     X, Y = _inputs(1)
+    Y[11, :] = 0.0                   # a dropped contraction index
     out, levels, xd, yd = _product(X, Y, ROWS, COLS)
     for dig in list(xd.values()) + list(yd.values()):
         for d in dig:
@@ -93,6 +122,24 @@ def test_digits_levels_and_bound():
         scale = M * float(np.max(np.abs(X[r]))) * float(np.max(np.abs(Y[:, c])))
         if scale > 0:
             assert abs(v - float(_exact(X, Y, r, c))) <= 2.0 ** -49 * scale
+
+
+def test_contraction_scaling_leaves_the_product_unchanged():
+    # X D and D^-1 Y with D powers of two over 2^-300 .. 2^300 (the unknowns of
+    # a block row scaled): every digit and every result is the same, so the
+    # error stays at the unscaled product's FP64 level although the rows of
+    # X D span 600 binades
+    X, Y = _inputs(3)
+    Y[:, 9] *= 2.0 ** 1000           # (2^-1300 would not be representable)
+    d = np.exp2(np.random.default_rng(4).integers(-300, 301, M)).astype(np.float64)
+    rows, cols = [0, 5, 77], [0, 9, 100]
+    out, _, xd, yd = _product(X, Y, rows, cols)
+    out2, _, xd2, yd2 = _product(X * d[None, :], Y / d[:, None], rows, cols)
+    assert xd == xd2 and yd == yd2
+    assert {k: v[0] for k, v in out.items()} == {k: v[0] for k, v in out2.items()}
+    for (r, c), (v, er, ec) in out.items():
+        scale = M * float(np.max(np.abs(X[r]))) * float(np.max(np.abs(Y[:, c])))
+        assert abs(v - float(_exact(X, Y, r, c))) <= 2.0 ** -47 * scale
 
 
 def test_level_sums_stay_exact_at_the_worst_case():
@@ -116,3 +163,4 @@ def test_planted_mistakes_break_the_bound():
     assert violates(drop_level=5)
     assert violates(weight=64)
     assert violates(transpose_y=True)
+    assert violates(one_sided=True)

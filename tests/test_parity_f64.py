@@ -90,6 +90,37 @@ def test_paper_block_sizes(bt, N, M, S):
         assert oracle.rel_res(A, B, C, X, F) <= TOL
 
 
+@pytest.mark.parametrize("M,scaled", [(128, False), (128, True), (120, True)])
+def test_dense_factor_products_scaled_unknowns(bt, M, scaled):
+    # dense M = 128 blocks: the factorisation's block products run on the
+    # tensor cores as exact digit-slice sums (M = 120: FP64 products, the same
+    # bar).  The scaled case multiplies the unknowns by powers of two spread
+    # over 2^-200 .. 2^200 (A_j D, B_j D, C_j D), so the rows and columns of
+    # every product span a wide exponent range; couplings with zero rows and
+    # columns give products with all-zero rows or columns.  The solution of
+    # the scaled system is D^-1 X.
+    N, K, S = 256, 9, 8
+    A, B, C = gen.dominant_blocks(N, M, seed=M)
+    A[:, :5, :] = 0.0  # couplings only: C_j is the dominant diagonal block
+    B[:, :, 3] = 0.0
+    F = gen.uniform_rhs(N, M, K, seed=12)
+    d = np.ones(M)
+    if scaled:
+        d = np.exp2(np.random.default_rng(5).integers(-200, 201, M)).astype(np.float64)
+    As, Bs, Cs = A * d, B * d, C * d
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    with bt.factor(_t(As), _t(Bs), _t(Cs), S) as fac:
+        X = fac.solve(_t(F)).cpu().numpy() * d[None, :, None]
+        if not scaled:
+            U, V = oracle.segment_responses(A, B, C, S)
+            At, Ct, Bt = oracle.reduced_system(A, B, C, S, U, V)
+            for name, ref in (("U", U), ("V", V), ("At", At), ("Ct", Ct), ("Bt", Bt)):
+                got = fac.export(name).cpu().numpy()
+                np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()), err_msg=name)
+    assert oracle.rel_err(X, Xr) <= TOL
+    assert oracle.col_err(X, Xr) <= TOL
+
+
 def test_unused_corner_blocks_are_ignored(bt):
     N, M, K, S = 32, 4, 2, 4
     A, B, C = gen.dominant_blocks(N, M, seed=3)
