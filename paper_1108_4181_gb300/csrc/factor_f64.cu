@@ -222,115 +222,189 @@ __global__ void __launch_bounds__(1024) k_inverse_batched(const double* const* _
 }
 
 // ---------------------------------------------------------------------------
-// The same Gauss-Jordan inversion on a two-CTA thread-block cluster per
-// matrix: CTA r holds columns [r Mc, (r+1) Mc) (Mc = ceil(M / 2)) in its
-// shared memory, so each SM does half of the FP64 elimination.  Step k: the
-// owner of column k finds the pivot row p, forms the multipliers of the
-// interchanged column (row k takes row p's entry and vice versa) and writes
-// p and the multipliers into both CTAs' shared memory (double-buffered by
-// the parity of k); one cluster barrier; then every CTA interchanges rows k
-// and p, scales row k and eliminates in its own columns.  The interchanges
-// are undone at the end by writing column c of the result to the column the
-// composed interchanges send it to.  Singular or non-finite pivots: as above.
+// The same Gauss-Jordan inversion on a thread-block cluster of C CTAs per
+// matrix (C = 2, 4 or 8, chosen at launch), M <= 256.  CTA r holds columns
+// [r Mc, (r+1) Mc) (Mc = ceil(M / C)) column-major in its shared memory, and
+// each warp owns whole columns: the interchange of rows k and p and the
+// elimination touch only a warp's own columns, so within a step no warp
+// waits for another.  Row scaling is deferred: the stored rows keep their
+// raw values U and row k records s_k = 1 / pivot; the inverse is s_i U[i][j]
+// (rows scaled on the way out).  With g_i = U[i][k] / pivot (after the
+// interchange), step k is
+//   U[i][j] -= g_i U[k][j]      (i != k, j != k)
+//   U[i][k]  = -g_i             (i != k),   U[k][k] = 1,
+// the GJ step on s U.  The warp owning column k+1 updates it first, picks the
+// pivot of step k+1 (the largest |U[i][k+1]|, i > k; ties to the lower row),
+// forms 1 / pivot (an FP32 seed and two Newton-Raphson steps in FP64, four
+// dependent FP64 operations) and writes p, 1 / pivot and the multipliers g
+// into every CTA's shared memory (double-buffered by the parity of the step).
+// One cluster barrier per step, split: a warp arrives as soon as it has read
+// the step's pivot data (the publishing warp after publishing) and waits at
+// the start of the next step, so the pivot chain runs ahead of the bulk of
+// the elimination.  The interchanges are undone at the end by writing column
+// c of the result to the column the composed interchanges send it to.
+// Singular or non-finite pivots: as above.
 // ---------------------------------------------------------------------------
+
+// 1 / v for finite nonzero v: the FP32 reciprocal of v's leading significand
+// bits (exponent from the bits) as the seed, then two Newton-Raphson steps
+// r <- r + r (1 - v r) in FP64 (error about 2^-24 -> 2^-48 -> rounding);
+// a division outside the normal range.
+__device__ __forceinline__ double recip_newton(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7FF);
+  if (be < 4 || be > 2042) return 1.0 / v;
+  const float m = __uint_as_float(0x3F800000u | (unsigned)((b >> 29) & 0x7FFFFFu));  // [1, 2)
+  const unsigned rb = __float_as_uint(1.0f / m);                                     // (0.5, 1]
+  const int re = (int)((rb >> 23) & 0xFF) - 127 - (be - 1023) + 1023;
+  double r = __longlong_as_double((long long)((b & 0x8000000000000000ull) | ((unsigned long long)re << 52) |
+                                              ((unsigned long long)(rb & 0x7FFFFFu) << 29)));
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
+}
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+constexpr int kInvClusterMaxM = 256;  // 8 rows per lane
+
 __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* __restrict__ tab, int M, int* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double sh[];
-  __shared__ int s_p;
+  const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int mat = blockIdx.x / 2;
+  const int mat = blockIdx.x / C;
   const double* src = tab[2 * mat + 0];
   double* dst = const_cast<double*>(tab[2 * mat + 1]);
-  const int Mc = (M + 1) / 2;
-  const int c0 = rank * Mc, nc = min(Mc, M - c0);    // global columns c0 .. c0 + nc - 1
-  double* a = sh;                                    // [M][Mc], row-major
-  double* fbuf = sh + (size_t)M * Mc;                // [2][M] multipliers
-  int* pbuf = reinterpret_cast<int*>(fbuf + 2 * M);  // [2] pivot rows
-  int* perm = pbuf + 2;                              // [M]
-  int* pos = perm + M;                               // [M]
-  const int nt = blockDim.x;
-  for (int e = threadIdx.x; e < M * Mc; e += nt) {
+  const int Mc = (M + C - 1) / C;
+  const int c0 = rank * Mc, nc = max(0, min(Mc, M - c0));  // global columns c0 .. c0 + nc - 1
+  const int ldu = M | 1;                                   // column stride (odd: the transposing load spreads banks)
+  double* U = sh;                                          // [Mc][ldu]: local column j, row i
+  double* gbuf = U + (size_t)Mc * ldu;                     // [2][M] multipliers
+  double* rbuf = gbuf + 2 * M;                             // [2] 1 / pivot
+  double* srow = rbuf + 2;                                 // [M] row scales
+  int* pbuf = reinterpret_cast<int*>(srow + M);            // [2] pivot rows
+  int* perm = pbuf + 2;                                    // [M]
+  int* pos = perm + M;                                     // [M]
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  for (int e = tid; e < M * Mc; e += nt) {
     const int i = e / Mc, lc = e % Mc;
-    a[e] = lc < nc ? src[(size_t)i * M + c0 + lc] : 0.0;
+    U[(size_t)lc * ldu + i] = lc < nc ? src[(size_t)i * M + c0 + lc] : 0.0;
   }
-  // elimination mapping: thread -> (local column jt, first row it0), rows strided by rstep
-  const int rstep = max(1, nt / Mc);
-  const int jt = threadIdx.x < rstep * Mc ? threadIdx.x % Mc : Mc;
-  const int it0 = threadIdx.x / Mc;
   __syncthreads();
-  cl.sync();
+  cl.sync();  // every CTA of the cluster runs before any shared memory is written remotely
+  // The warp owning column kk (updated through step kk-1): pivot of step kk.
+  auto pivot_col = [&](int kk, int slot) {
+    const double* col = U + (size_t)(kk - c0) * ldu;
+    unsigned long long bb = 0;
+    int bi = 0x7fffffff;
+    for (int i = kk + lane; i < M; i += 32) {
+      const unsigned long long u = (unsigned long long)__double_as_longlong(col[i]) & 0x7FFFFFFFFFFFFFFFull;
+      if (u > bb || bi == 0x7fffffff) {
+        bb = u;
+        bi = i;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bb, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (oi != 0x7fffffff && (ob > bb || (ob == bb && oi < bi) || bi == 0x7fffffff)) {
+        bb = ob;
+        bi = oi;
+      }
+    }
+    const int p = bi;
+    const double xp = col[p], xk = col[kk];
+    double rinv = 0.0;
+    if (lane == 0) {
+      double pv = xp;
+      if (!(pv != 0.0) || !isfinite(pv)) {
+        atomicExch(status, 1);
+        pv = 1.0;
+      }
+      rinv = recip_newton(pv);
+    }
+    rinv = __shfl_sync(0xffffffffu, rinv, 0);
+    for (int i = lane; i < M; i += 32) {
+      const double gi = (i == p ? xk : col[i]) * rinv;
+      for (int r = 0; r < C; ++r) {
+        if (r == rank)
+          gbuf[slot * M + i] = gi;
+        else
+          cl.map_shared_rank(gbuf, r)[slot * M + i] = gi;
+      }
+    }
+    if (lane < C) {
+      cl.map_shared_rank(pbuf, lane)[slot] = p;
+      cl.map_shared_rank(rbuf, lane)[slot] = rinv;
+    }
+  };
+  if (rank == 0 && w == 0) pivot_col(0, 0);
+  cluster_arrive();
   for (int k = 0; k < M; ++k) {
-    const int owner = k / Mc, lk = k - owner * Mc, b = k & 1;
-    if (rank == owner) {
-      if (threadIdx.x < 32) {  // pivot search over rows k..M-1 of column k
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + threadIdx.x; i < M; i += 32) {
-          const double v = fabs(a[(size_t)i * Mc + lk]);
-          if (v > best || (v == best && i < bi)) {
-            best = v;
-            bi = i;
-          }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          const double ob = __shfl_down_sync(0xffffffffu, best, off);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-          if (ob > best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
-          }
-        }
-        if (threadIdx.x == 0) s_p = bi;
-      }
-      __syncthreads();
-      const int p = s_p;
-      // multipliers of the interchanged column k into both CTAs
-      for (int e = threadIdx.x; e < 2 * M; e += nt) {
-        const int i = e % M, r = e / M;
-        double f = a[(size_t)(i == k ? p : i == p ? k : i) * Mc + lk];
-        if (i == k && (!(f != 0.0) || !isfinite(f))) {
-          atomicExch(status, 1);
-          f = 1.0;
-        }
-        double* fr = cl.map_shared_rank(fbuf, r);
-        fr[b * M + i] = f;
-        if (i == 0) cl.map_shared_rank(pbuf, r)[b] = p;
-      }
-    }
-    cl.sync();
+    cluster_wait();  // the pivot of step k is published
+    const int b = k & 1;
     const int p = pbuf[b];
-    const double* f = fbuf + b * M;
-    const double pv = f[k];
-    if (threadIdx.x == 0) perm[k] = p;
-    // interchange rows k and p, scale row k (column k becomes 1 / pivot)
-    if (p != k)
-      for (int j = threadIdx.x; j < Mc; j += nt) {
-        const double t = a[(size_t)k * Mc + j];
-        a[(size_t)k * Mc + j] = a[(size_t)p * Mc + j];
-        a[(size_t)p * Mc + j] = t;
-      }
-    __syncthreads();
-    for (int j = threadIdx.x; j < Mc; j += nt) {
-      const double v = (j == lk && rank == owner) ? 1.0 : a[(size_t)k * Mc + j];
-      a[(size_t)k * Mc + j] = v / pv;
+    const double* g = gbuf + b * M;
+    if (tid == 0) {
+      perm[k] = p;
+      srow[k] = rbuf[b];
     }
-    __syncthreads();
-    // eliminate column k from every other row
-    if (jt < Mc) {
-      const double pk = a[(size_t)k * Mc + jt];
-      const bool colk = rank == owner && jt == lk;
-      for (int i = it0; i < M; i += rstep) {
-        if (i == k) continue;
-        const size_t e = (size_t)i * Mc + jt;
-        a[e] = fma(-f[i], pk, colk ? 0.0 : a[e]);
+    const int owner = k / Mc, lk = k - owner * Mc;
+    const int kn = k + 1;
+    const int jn = (kn < M && kn / Mc == rank && (kn - c0) % nw == w) ? kn - c0 : -1;  // this warp's next pivot column
+    double gv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = lane + 32 * m;
+      gv[m] = i < M ? g[i] : 0.0;
+    }
+    if (jn < 0) cluster_arrive();  // everything of step k is read
+    // this warp's columns, the next pivot column first
+    for (int t = -1; t * nw + w < Mc; ++t) {
+      int j;
+      if (t < 0) {
+        if (jn < 0) continue;
+        j = jn;
+      } else {
+        j = t * nw + w;
+        if (j == jn) continue;
+      }
+      double* col = U + (size_t)j * ldu;
+      const double vp = col[p], vk = col[k];
+      __syncwarp();
+      if (rank == owner && j == lk) {
+        // column k of the inverse: -g, and 1 in row k (whose scale is 1 / pivot)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = lane + 32 * m;
+          if (i < M) col[i] = i == k ? 1.0 : __longlong_as_double(__double_as_longlong(gv[m]) ^ (long long)(1ULL << 63));
+        }
+      } else {
+        // rows k and p interchanged: row k takes row p (vp), row p row k (vk)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int i = lane + 32 * m;
+          if (i < M) {
+            const double v = fma(-gv[m], vp, i == p ? vk : col[i]);
+            col[i] = i == k ? vp : v;
+          }
+        }
+      }
+      __syncwarp();
+      if (t < 0) {
+        pivot_col(kn, b ^ 1);
+        cluster_arrive();
       }
     }
-    __syncthreads();
   }
+  cluster_wait();
   // the interchanges undone as column interchanges, last first: position j
   // ends up holding elimination column pos[j]; column c goes to perm[c]
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     for (int c = 0; c < M; ++c) pos[c] = c;
     for (int k = M - 1; k >= 0; --k) {
       const int q = perm[k];
@@ -341,12 +415,19 @@ __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* _
     for (int j = 0; j < M; ++j) perm[pos[j]] = j;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < M * nc; e += nt) {
+  for (int e = tid; e < M * nc; e += nt) {
     const int i = e / nc, lc = e % nc;
-    dst[(size_t)i * M + perm[c0 + lc]] = a[(size_t)i * Mc + lc];
+    dst[(size_t)i * M + perm[c0 + lc]] = srow[i] * U[(size_t)lc * ldu + i];
   }
-  cl.sync();  // no CTA leaves while its partner may still write into its shared memory
+  cl.sync();  // no CTA leaves while a partner may still write into its shared memory
 }
+
+// Shared memory and threads of k_inverse_cluster for block size M on clusters of C CTAs.
+size_t inv_cluster_smem(int M, int C) {
+  const size_t Mc = (size_t)(M + C - 1) / C, ldu = (size_t)(M | 1);
+  return (Mc * ldu + 3 * (size_t)M + 2) * sizeof(double) + (2 + 2 * (size_t)M) * sizeof(int);
+}
+int inv_cluster_threads(int M, int C) { return 32 * std::min(32, (M + C - 1) / C); }
 
 // Plain device copy (grid-stride).
 __global__ void k_copy(const double* __restrict__ src, double* __restrict__ dst, size_t n) {
@@ -557,15 +638,43 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
                                    : M * sizeof(double) + M * sizeof(int);
   BT_CUDA(cudaFuncSetAttribute(k_inverse_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
   const int inv_threads = (int)std::min<size_t>(1024, std::max<size_t>(32, ((MM + 31) / 32) * 32));
-  // two-CTA clusters when a CTA's half of the matrix fits in shared memory
-  const int Mc = (M + 1) / 2;
-  const size_t clu_smem = ((size_t)M * Mc + 2 * (size_t)M) * sizeof(double) + (2 + 2 * (size_t)M) * sizeof(int);
-  const int clu_threads = (int)std::min<size_t>(1024, std::max<size_t>(64, (((size_t)M * Mc + 31) / 32) * 32));
-  bool clu_ok = M >= 32 && clu_smem <= 200 * 1024;
-  if (clu_ok)
-    clu_ok = cudaFuncSetAttribute(k_inverse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)clu_smem) ==
-             cudaSuccess;
+  // Cluster inversion (M <= 256): C = 2, 4 or 8 CTAs per matrix.  Each launch
+  // takes the largest C (at least 16 columns per CTA, its share of the matrix
+  // in shared memory) whose clusters for the whole batch fit on the GPU at
+  // once, else the smallest usable C; the one-CTA kernel when none is usable.
+  struct CluCfg {
+    int C = 0, threads = 0, fit = 0;  // fit: clusters resident at once
+    size_t smem = 0;
+  } clu[3];
+  for (int ci = 0; ci < 3; ++ci) {
+    const int C = 2 << ci, Mc = (M + C - 1) / C;
+    CluCfg& cc = clu[ci];
+    cc.smem = inv_cluster_smem(M, C);
+    cc.threads = inv_cluster_threads(M, C);
+    if (M < 32 || M > kInvClusterMaxM || (C > 2 && Mc < 16) || cc.smem > 200 * 1024) continue;
+    if (cudaFuncSetAttribute(k_inverse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc.smem) !=
+        cudaSuccess)
+      continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(cc.threads);
+    cfg.dynamicSmemBytes = cc.smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_inverse_cluster, &cfg) == cudaSuccess && n > 0) {
+      cc.C = C;
+      cc.fit = n;
+    }
+  }
   cudaGetLastError();
+  const bool clu_ok = clu[0].C || clu[1].C || clu[2].C;
+  size_t clu_attr = 0;  // the dynamic shared memory the kernel is currently set up for
   // GEMM tile: 32 when 64-tiles would pad the block by more than about 15 % in area
   const int pad64 = (M + 63) / 64 * 64, pad32 = (M + 31) / 32 * 32;
   // M <= 192: 16 x 16 tiles -- every launch holds 16x the CTAs of 64-tiles, which
@@ -634,14 +743,24 @@ bt_status run_schedule(const Schedule& sc, const double** dtab, int M, int* dsta
           k_gemm_batched<64><<<grid, 256, 0, q>>>(dtab + o.off + 4 * (size_t)b0, M, o.alpha, o.beta, o.bp);
       } else {
         if (clu_ok) {
+          int ci = -1;
+          for (int c = 2; c >= 0 && ci < 0; --c)
+            if (clu[c].C && nb <= clu[c].fit) ci = c;
+          for (int c = 0; c < 3 && ci < 0; ++c)
+            if (clu[c].C) ci = c;
+          const CluCfg& cc = clu[ci];
+          if (clu_attr < cc.smem) {
+            BT_CUDA(cudaFuncSetAttribute(k_inverse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc.smem));
+            clu_attr = cc.smem;
+          }
           cudaLaunchConfig_t cfg = {};
-          cfg.gridDim = dim3(2 * nb);
-          cfg.blockDim = dim3(clu_threads);
-          cfg.dynamicSmemBytes = clu_smem;
+          cfg.gridDim = dim3(cc.C * nb);
+          cfg.blockDim = dim3(cc.threads);
+          cfg.dynamicSmemBytes = cc.smem;
           cfg.stream = q;
           cudaLaunchAttribute at[1];
           at[0].id = cudaLaunchAttributeClusterDimension;
-          at[0].val.clusterDim.x = 2;
+          at[0].val.clusterDim.x = cc.C;
           at[0].val.clusterDim.y = 1;
           at[0].val.clusterDim.z = 1;
           cfg.attrs = at;

@@ -165,32 +165,39 @@ __device__ __forceinline__ int scale_from_max(int m, bool bad) {
   return m == kNoExp ? 0 : m + 1;
 }
 
-// One CTA per entry: t_k from the column maxima of X_e (thread: column k
-// over half the rows) and the row maxima of Y_e (warp: 16 rows, a row per pass).
+// One CTA per (entry e, 16 contraction indices k): t_k from the column
+// maxima of X_e (16 columns over all rows) and the row maxima of Y_e (16 rows,
+// two per warp).
 __global__ void __launch_bounds__(256) k_gdig_balance(const double* const* __restrict__ tab, int* __restrict__ tk) {
-  __shared__ int cx[2][GM];
-  __shared__ int ry[GM];
-  const int e = blockIdx.x, tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  __shared__ int cxp[16][17];
+  __shared__ int ry[16];
+  const int e = blockIdx.x / (GM / 16), k0 = (blockIdx.x % (GM / 16)) * 16;
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
   const double* X = tab[4 * e];
   const double* Y = tab[4 * e + 1];
   {
-    const int k = tid % GM, r0 = (tid / GM) * (GM / 2);
+    const int c = tid % 16, rg = tid / 16;  // rows rg, rg + 16, ...
     int m = kNoExp;
-#pragma unroll 8
-    for (int r = r0; r < r0 + GM / 2; ++r) m = max(m, exp_floor(X[(size_t)r * GM + k]));
-    cx[tid / GM][k] = m;
+#pragma unroll
+    for (int r = rg; r < GM; r += 16) m = max(m, exp_floor(X[(size_t)r * GM + k0 + c]));
+    cxp[rg][c] = m;
   }
-  for (int k = w * 16; k < w * 16 + 16; ++k) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = k0 + 2 * w + h;
     int m = kNoExp;
 #pragma unroll
     for (int i = 0; i < 4; ++i) m = max(m, exp_floor(Y[(size_t)k * GM + lane + 32 * i]));
     m = warp_max_int(m);
-    if (lane == 0) ry[k] = m;
+    if (lane == 0) ry[2 * w + h] = m;
   }
   __syncthreads();
-  if (tid < GM) {
-    const int a = max(cx[0][tid], cx[1][tid]), b = ry[tid];
-    tk[(size_t)e * GM + tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
+  if (tid < 16) {
+    int a = kNoExp;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) a = max(a, cxp[g][tid]);
+    const int b = ry[tid];
+    tk[(size_t)e * GM + k0 + tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
   }
 }
 
@@ -473,7 +480,7 @@ bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int
   CUtensorMap tx, ty;
   BT_TRY(gd_map(&tx, Xd, (uint64_t)E * GD * GM, 64));
   BT_TRY(gd_map(&ty, Yd, (uint64_t)E * GD * GM, 128));
-  k_gdig_balance<<<(unsigned)E, 256, 0, st>>>(dtab, tk);
+  k_gdig_balance<<<(unsigned)(E * (GM / 16)), 256, 0, st>>>(dtab, tk);
   k_gdig_rows<<<(unsigned)((E * GM + 7) / 8), 256, 0, st>>>(dtab, E, tk, Xd, ex);
   k_gdig_cols<<<(unsigned)(E * (GM / 32)), 256, 0, st>>>(dtab, E, tk, Yd, ey);
   static bool attr = false;

@@ -121,6 +121,19 @@ def test_dense_factor_products_scaled_unknowns(bt, M, scaled):
     assert oracle.col_err(X, Xr) <= TOL
 
 
+@pytest.mark.parametrize("N,M,S", [(16, 256, 4), (12, 200, 3), (64, 200, 16)])
+def test_large_block_sizes(bt, N, M, S):
+    # pivot blocks up to M = 256 (8 rows per lane in the cluster inversion,
+    # clusters of 4 or 8 CTAs for the small batches); M = 200: rows not a
+    # multiple of the warp
+    A, B, C = gen.dominant_blocks(N, M, seed=N + M)
+    F = gen.uniform_rhs(N, M, 3, seed=5)
+    X = _solve(bt, A, B, C, F, S)
+    Xr = oracle.solve_block_thomas(A, B, C, F)
+    assert oracle.rel_err(X, Xr) <= TOL
+    assert oracle.col_err(X, Xr) <= TOL
+
+
 def test_unused_corner_blocks_are_ignored(bt):
     N, M, K, S = 32, 4, 2, 4
     A, B, C = gen.dominant_blocks(N, M, seed=3)
@@ -168,8 +181,11 @@ def test_stencil_detection(bt):
         assert fac.stencil == 1
 
 
-def test_singular_pivot_is_reported(bt):
-    N, M, S = 16, 3, 4
+@pytest.mark.parametrize("M", [3, 64, 128])
+def test_singular_pivot_is_reported(bt, M):
+    # M = 3: one-CTA inversion; M = 64, 128: cluster inversions (4 pivot
+    # blocks per launch: clusters of 4 and 8 CTAs)
+    N, S = 16, 4
     A, B, C = gen.dominant_blocks(N, M, seed=1)
     C[5] = 0.0   # interior row of segment 1 with A_5 = B_5 = 0: D_5 singular
     A[5] = 0.0
