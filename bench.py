@@ -818,6 +818,76 @@ def run_schur(args):
     return 0
 
 
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # FP64 pipe, nominal: 2 FMA per clock per SM at 2070 MHz
+
+
+def run_factor(args):
+    """bt_factor (Algorithm 2, stage 1: the paper's Pre) on two M = 128 systems: dense diagonally
+    dominant blocks N=2048, S=64 (drawn on the device), and the acoustic operator N=4096, S=64 of
+    the headline.  Pre = wall time of bt_factor, which synchronises before it returns; median of
+    repeats after one warm-up factorisation.  Work model: 14 M^3 flop per block row (the pivot-block
+    inverse 2 M^3; the products G, E, the D update and the U, V, Y recurrences 12 M^3), counted as
+    FP64 flop; its rate is shown beside the FP64 pipe's nominal peak (the dense products run on
+    the tensor cores, so the rate can exceed it).  Each factorisation solves two right-hand sides
+    against the CPU oracle."""
+    import statistics
+
+    import torch
+
+    import oracle
+    import paper_1108_4181_gb300 as bt
+    from workloads import gen
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    with bt.factor(*(t.contiguous() for t in gen.dominant_blocks_device(64, 8, 0, dev)), 4) as f0:
+        f0.solve(torch.ones((64, 8, 1), dtype=torch.float64, device=dev))
+    reps = max(1, args.steps)
+    systems = []
+    with ClockSampler(0) as clk:
+        for name, Nn, Sv in (("dense", 2048, 64), ("acoustic", 4096, 64)):
+            Mm = 128
+            if name == "dense":
+                A, B, C = gen.dominant_blocks_device(Nn, Mm, 2048 + Mm, dev)
+            else:
+                A, B, C = (torch.from_numpy(a).to(dev) for a in gen.acoustic_system(Nn, Mm))
+            times = []
+            for r in range(reps + 1):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                fac = bt.factor(A, B, C, Sv)
+                t1 = time.perf_counter()
+                if r > 0:
+                    times.append(t1 - t0)
+                if r < reps:
+                    fac.close()
+            F = gen.uniform_rhs(Nn, Mm, 2, seed=3)
+            X = fac.solve(torch.from_numpy(F).to(dev)).cpu().numpy()
+            fac.close()
+            An, Bn, Cn = (t.cpu().numpy() for t in (A, B, C))
+            Xr = oracle.solve_block_thomas(An, Bn, Cn, F)
+            pre = statistics.median(times)
+            flop = 14.0 * Mm ** 3 * Nn
+            systems.append({"system": name, "N": Nn, "M": Mm, "S": Sv, "pre_ms": pre * 1e3,
+                            "pre_ms_all": [t * 1e3 for t in times], "work_model_gflop": flop / 1e9,
+                            "fp64_equiv_tflops": flop / pre / 1e12,
+                            "fraction_of_fp64_peak": flop / pre / 1e12 / FP64_PEAK_TFLOPS,
+                            "rel_err_vs_oracle": oracle.rel_err(X, Xr), "col_err_vs_oracle": oracle.col_err(X, Xr)})
+            print(f"factor {name}: {json.dumps(systems[-1])}", file=sys.stderr, flush=True)
+            del A, B, C, An, Bn, Cn
+            torch.cuda.empty_cache()
+    line = {
+        "metric": "Pre: bt_factor time, dense N=2048 M=128 S=64", "value": systems[0]["pre_ms"], "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": reps, "warmup": 1, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (dense: diagonally dominant blocks drawn on the device; acoustic: the headline operator)",
+        "config": {"workload": "bt_factor: dense N=2048 M=128 S=64 and acoustic N=4096 M=128 S=64"},
+        "fp64_peak_tflops_nominal": FP64_PEAK_TFLOPS, "systems": systems, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,10 +901,11 @@ def main():
                     help="refinement target ||F - P X|| / ||F|| (default 1e-10)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 GPU path beside")
-    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson", "paper", "schur"], default="acoustic",
+    ap.add_argument("--workload", choices=["acoustic", "batched", "poisson", "paper", "schur", "factor"],
+                    default="acoustic",
                     help="acoustic (the headline), the batched uneven-set workload, the Poisson workload "
-                         "(N=1024, M=256, K=64, S=64), the paper's Table 1-2 shapes, or the Schur-complement "
-                         "CG with probing")
+                         "(N=1024, M=256, K=64, S=64), the paper's Table 1-2 shapes, the Schur-complement "
+                         "CG with probing, or bt_factor (Pre) on the M = 128 systems")
     ap.add_argument("--schur-bands", default="-1,1,2,4,8,16,32",
                     help="with --workload schur: probing half-bandwidths d (-1 = no preconditioner)")
     ap.add_argument("--rows", type=int, default=N,
@@ -864,6 +935,8 @@ def main():
         return run_batched(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "factor":
+        return run_factor(args)
     if args.workload == "schur":
         return run_schur(args)
     return run_ours(args)
