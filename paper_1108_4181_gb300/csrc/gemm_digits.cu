@@ -50,9 +50,10 @@
 // arithmetic (tests/test_digit_gemm_model.py).  A row or column holding a
 // NaN or an infinity gives NaN entries.
 //
-//   k_gdig_balance t [E][M] from the column maxima of X and the row maxima of Y
-//   k_gdig_rows   X digits [E][8][M][M] (row r, contraction k) and ex
-//   k_gdig_cols   Y digits [E][8][M][M] (column c, contraction k) and ey
+//   k_gdig_prep   per entry (four CTAs): t from the column maxima of X and
+//                 the row maxima of Y, X digits [E][8][M][M] (row r,
+//                 contraction k) with ex, Y digits [E][8][M][M] (column c,
+//                 contraction k) with ey
 //   k_gemm_digits one CTA per (entry, 64-row half): TMA warp = MMA thread,
 //                 TMEM allocator warp, 8 epilogue warps
 
@@ -165,100 +166,89 @@ __device__ __forceinline__ int scale_from_max(int m, bool bad) {
   return m == kNoExp ? 0 : m + 1;
 }
 
-// One CTA per (entry e, 16 contraction indices k): t_k from the column
-// maxima of X_e (16 columns over all rows) and the row maxima of Y_e (16 rows,
-// two per warp).
-__global__ void __launch_bounds__(256) k_gdig_balance(const double* const* __restrict__ tab, int* __restrict__ tk) {
-  __shared__ int cxp[16][17];
-  __shared__ int ry[16];
-  const int e = blockIdx.x / (GM / 16), k0 = (blockIdx.x % (GM / 16)) * 16;
+// The digits of both operands of entry e, a quarter q of each per CTA (grid
+// 4 E, 512 threads).  (1) t_k for every k: the column maxima of X_e (thread:
+// one column over a quarter of the rows) and the row maxima of Y_e (warp:
+// eight rows), computed by each of the entry's four CTAs (the second to
+// fourth read X_e and Y_e from L2).  (2) Rows 32 q .. 32 q + 31 of X_e: a
+// warp per row, its scale and 8 digit rows.  (3) Columns 32 q .. 32 q + 31 of
+// Y_e through shared memory: a warp per column, its scale and 8 digit rows
+// (contraction k contiguous).
+constexpr int GPREP = 512;
+__global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __restrict__ tab, __nv_bfloat16* __restrict__ Xd,
+                                                     __nv_bfloat16* __restrict__ Yd, int* __restrict__ ex,
+                                                     int* __restrict__ ey) {
+  __shared__ double ys[GM][33];
+  __shared__ int cxp[GPREP / GM][GM];
+  __shared__ int ry[GM];
+  __shared__ int tks[GM];
+  const int e = blockIdx.x / 4, q = blockIdx.x % 4;
   const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  constexpr int NW = GPREP / 32;
   const double* X = tab[4 * e];
   const double* Y = tab[4 * e + 1];
+  // (1) balance
   {
-    const int c = tid % 16, rg = tid / 16;  // rows rg, rg + 16, ...
+    const int c = tid % GM, rg = tid / GM;
     int m = kNoExp;
-#pragma unroll
-    for (int r = rg; r < GM; r += 16) m = max(m, exp_floor(X[(size_t)r * GM + k0 + c]));
+#pragma unroll 8
+    for (int r = rg; r < GM; r += GPREP / GM) m = max(m, exp_floor(X[(size_t)r * GM + c]));
     cxp[rg][c] = m;
   }
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int k = k0 + 2 * w + h;
+  for (int k = w; k < GM; k += NW) {
     int m = kNoExp;
 #pragma unroll
     for (int i = 0; i < 4; ++i) m = max(m, exp_floor(Y[(size_t)k * GM + lane + 32 * i]));
     m = warp_max_int(m);
-    if (lane == 0) ry[2 * w + h] = m;
+    if (lane == 0) ry[k] = m;
   }
+  // stage this CTA's 32 columns of Y for (3)
+  for (int i = tid; i < GM * 32; i += GPREP) ys[i / 32][i % 32] = Y[(size_t)(i / 32) * GM + 32 * q + i % 32];
   __syncthreads();
-  if (tid < 16) {
+  if (tid < GM) {
     int a = kNoExp;
 #pragma unroll
-    for (int g = 0; g < 16; ++g) a = max(a, cxp[g][tid]);
+    for (int g = 0; g < GPREP / GM; ++g) a = max(a, cxp[g][tid]);
     const int b = ry[tid];
-    tk[(size_t)e * GM + k0 + tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
+    tks[tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
   }
-}
-
-// One warp per row r of X_e: its scale and 8 digit rows.
-__global__ void __launch_bounds__(256) k_gdig_rows(const double* const* __restrict__ tab, int E,
-                                                   const int* __restrict__ tk, __nv_bfloat16* __restrict__ Xd,
-                                                   int* __restrict__ ex) {
-  const int lane = threadIdx.x % 32;
-  const int64_t w = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
-  if (w >= (int64_t)E * GM) return;
-  const int e = (int)(w / GM), r = (int)(w % GM);
-  const double* X = tab[4 * e];
-  double v[4];
-  const int4 t4 = *reinterpret_cast<const int4*>(tk + (size_t)e * GM + 4 * lane);
-  const int t[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = X[(size_t)r * GM + 4 * lane + i];
-  int m = kNoExp;
-  bool bad = false;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    bad = bad || bits_nonfinite(v[i]);
-    const int x = exp_floor(v[i]);
-    if (x != kNoExp && t[i] != kDropT) m = max(m, x + t[i]);
-  }
-  m = warp_max_int(m);
-  bad = __any_sync(0xffffffffu, bad);
-  const int es = scale_from_max(m, bad);
-  if (lane == 0) ex[(size_t)e * GM + r] = es;
-  uint32_t d[4][GD];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (bad || t[i] == kDropT) {
-#pragma unroll
-      for (int p = 0; p < GD; ++p) d[i][p] = 0u;
-    } else {
-      digits8(v[i], es - t[i], d[i]);  // round(v 2^t 2^(56 - es))
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < GD; ++p)
-    *reinterpret_cast<uint2*>(Xd + (((size_t)e * GD + p) * GM + r) * GM + 4 * lane) =
-        pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
-}
-
-// One CTA per (entry e, 32 columns of Y_e): the columns through shared memory,
-// their scales, and 8 digit rows per column (contraction k contiguous).
-__global__ void __launch_bounds__(256) k_gdig_cols(const double* const* __restrict__ tab, int E,
-                                                   const int* __restrict__ tk, __nv_bfloat16* __restrict__ Yd,
-                                                   int* __restrict__ ey) {
-  __shared__ double ys[GM][33];
-  const int e = blockIdx.x / (GM / 32), c0 = (blockIdx.x % (GM / 32)) * 32;
-  const double* Y = tab[4 * e + 1];
-  for (int i = threadIdx.x; i < GM * 32; i += 256) ys[i / 32][i % 32] = Y[(size_t)(i / 32) * GM + c0 + i % 32];
   __syncthreads();
-  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int4 t4 = *reinterpret_cast<const int4*>(tk + (size_t)e * GM + 4 * lane);
-  const int t[4] = {t4.x, t4.y, t4.z, t4.w};  // rows 4 lane .. 4 lane + 3: Y scaled by 2^-t
-  for (int jj = 0; jj < 4; ++jj) {
-    const int j = w * 4 + jj;
-    double v[4];  // rows 4 lane .. 4 lane + 3 of column j
+  const int t[4] = {tks[4 * lane], tks[4 * lane + 1], tks[4 * lane + 2], tks[4 * lane + 3]};  // k = 4 lane + i
+  // (2) rows of X: x 2^t
+  for (int r = 32 * q + w; r < 32 * q + 32; r += NW) {
+    double v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = X[(size_t)r * GM + 4 * lane + i];
+    int m = kNoExp;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      bad = bad || bits_nonfinite(v[i]);
+      const int x = exp_floor(v[i]);
+      if (x != kNoExp && t[i] != kDropT) m = max(m, x + t[i]);
+    }
+    m = warp_max_int(m);
+    bad = __any_sync(0xffffffffu, bad);
+    const int es = scale_from_max(m, bad);
+    if (lane == 0) ex[(size_t)e * GM + r] = es;
+    uint32_t d[4][GD];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (bad || t[i] == kDropT) {
+#pragma unroll
+        for (int p = 0; p < GD; ++p) d[i][p] = 0u;
+      } else {
+        digits8(v[i], es - t[i], d[i]);  // round(v 2^t 2^(56 - es))
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < GD; ++p)
+      *reinterpret_cast<uint2*>(Xd + (((size_t)e * GD + p) * GM + r) * GM + 4 * lane) =
+          pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
+  }
+  // (3) columns of Y: 2^-t y
+  for (int j = w; j < 32; j += NW) {
+    double v[4];  // rows 4 lane .. 4 lane + 3 of column 32 q + j
     int m = kNoExp;
     bool bad = false;
 #pragma unroll
@@ -271,7 +261,8 @@ __global__ void __launch_bounds__(256) k_gdig_cols(const double* const* __restri
     m = warp_max_int(m);
     bad = __any_sync(0xffffffffu, bad);
     const int es = scale_from_max(m, bad);
-    if (lane == 0) ey[(size_t)e * GM + c0 + j] = es;
+    const int c = 32 * q + j;
+    if (lane == 0) ey[(size_t)e * GM + c] = es;
     uint32_t d[4][GD];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -284,7 +275,7 @@ __global__ void __launch_bounds__(256) k_gdig_cols(const double* const* __restri
     }
 #pragma unroll
     for (int p = 0; p < GD; ++p)
-      *reinterpret_cast<uint2*>(Yd + (((size_t)e * GD + p) * GM + c0 + j) * GM + 4 * lane) =
+      *reinterpret_cast<uint2*>(Yd + (((size_t)e * GD + p) * GM + c) * GM + 4 * lane) =
           pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
   }
 }
@@ -463,7 +454,7 @@ bt_status gd_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_r
 bool digit_gemm_supported(int M) { return M == GM; }
 
 size_t digit_gemm_bytes(int emax) {
-  return (size_t)emax * (2 * (size_t)GD * GM * GM * sizeof(__nv_bfloat16) + 3 * (size_t)GM * sizeof(int));
+  return (size_t)emax * (2 * (size_t)GD * GM * GM * sizeof(__nv_bfloat16) + 2 * (size_t)GM * sizeof(int));
 }
 
 bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int E, double alpha, double beta,
@@ -476,13 +467,10 @@ bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int
   __nv_bfloat16* Yd = Xd + (size_t)emax * GD * GM * GM;
   int* ex = reinterpret_cast<int*>(Yd + (size_t)emax * GD * GM * GM);
   int* ey = ex + (size_t)emax * GM;
-  int* tk = ey + (size_t)emax * GM;
   CUtensorMap tx, ty;
   BT_TRY(gd_map(&tx, Xd, (uint64_t)E * GD * GM, 64));
   BT_TRY(gd_map(&ty, Yd, (uint64_t)E * GD * GM, 128));
-  k_gdig_balance<<<(unsigned)(E * (GM / 16)), 256, 0, st>>>(dtab, tk);
-  k_gdig_rows<<<(unsigned)((E * GM + 7) / 8), 256, 0, st>>>(dtab, E, tk, Xd, ex);
-  k_gdig_cols<<<(unsigned)(E * (GM / 32)), 256, 0, st>>>(dtab, E, tk, Yd, ey);
+  k_gdig_prep<<<(unsigned)(4 * E), GPREP, 0, st>>>(dtab, Xd, Yd, ex, ey);
   static bool attr = false;
   if (!attr) {
     BT_CUDA(cudaFuncSetAttribute(k_gemm_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GSMEM));
