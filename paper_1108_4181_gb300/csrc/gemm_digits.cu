@@ -50,15 +50,16 @@
 // arithmetic (tests/test_digit_gemm_model.py).  A row or column holding a
 // NaN or an infinity gives NaN entries.
 //
-//   k_gdig_prep   per entry (four CTAs): t from the column maxima of X and
-//                 the row maxima of Y, X digits [E][8][M][M] (row r,
-//                 contraction k) with ex, Y digits [E][8][M][M] (column c,
-//                 contraction k) with ey
+//   k_gdig_prep   per entry (a cluster of four CTAs, a quarter each): t from
+//                 the column maxima of X and the row maxima of Y, X digits
+//                 [E][8][M][M] (row r, contraction k) with ex, Y digits
+//                 [E][8][M][M] (column c, contraction k) with ey
 //   k_gemm_digits one CTA per (entry, 64-row half): TMA warp = MMA thread,
 //                 TMEM allocator warp, 8 epilogue warps
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <string>
@@ -166,65 +167,74 @@ __device__ __forceinline__ int scale_from_max(int m, bool bad) {
   return m == kNoExp ? 0 : m + 1;
 }
 
-// The digits of both operands of entry e, a quarter q of each per CTA (grid
-// 4 E, 512 threads).  (1) t_k for every k: the column maxima of X_e (thread:
-// one column over a quarter of the rows) and the row maxima of Y_e (warp:
-// eight rows), computed by each of the entry's four CTAs (the second to
-// fourth read X_e and Y_e from L2).  (2) Rows 32 q .. 32 q + 31 of X_e: a
-// warp per row, its scale and 8 digit rows.  (3) Columns 32 q .. 32 q + 31 of
-// Y_e through shared memory: a warp per column, its scale and 8 digit rows
-// (contraction k contiguous).
+// The digits of both operands of entry e on a cluster of four CTAs, a
+// quarter q of each operand per CTA (512 threads).  (1) CTA q reads rows
+// 32 q .. 32 q + 31 of X_e (kept in registers) and columns 32 q .. 32 q + 31 of
+// Y_e (staged in shared memory) and forms the partial column maxima of X and
+// row maxima of Y over them; (2) the four partials meet through distributed
+// shared memory: t_k for every k; (3) the rows of X: a warp per row, its
+// scale and 8 digit rows; (4) the columns of Y: a warp per column, its scale
+// and 8 digit rows (contraction k contiguous).
 constexpr int GPREP = 512;
 __global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __restrict__ tab, __nv_bfloat16* __restrict__ Xd,
                                                      __nv_bfloat16* __restrict__ Yd, int* __restrict__ ex,
                                                      int* __restrict__ ey) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   __shared__ double ys[GM][33];
-  __shared__ int cxp[GPREP / GM][GM];
-  __shared__ int ry[GM];
+  __shared__ int cxw[GPREP / 32][GM];
+  __shared__ int cxq[GM], ryq[GM];  // this CTA's partial maxima (read by the others)
   __shared__ int tks[GM];
-  const int e = blockIdx.x / 4, q = blockIdx.x % 4;
+  const int e = blockIdx.x / 4, q = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
   constexpr int NW = GPREP / 32;
+  static_assert(2 * NW == 32, "two rows of X per warp");
   const double* X = tab[4 * e];
   const double* Y = tab[4 * e + 1];
-  // (1) balance
-  {
-    const int c = tid % GM, rg = tid / GM;
-    int m = kNoExp;
-#pragma unroll 8
-    for (int r = rg; r < GM; r += GPREP / GM) m = max(m, exp_floor(X[(size_t)r * GM + c]));
-    cxp[rg][c] = m;
-  }
-  for (int k = w; k < GM; k += NW) {
-    int m = kNoExp;
+  // (1) rows 32 q + 2 w + h of X in registers (columns 4 lane .. 4 lane + 3)
+  double v[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) m = max(m, exp_floor(Y[(size_t)k * GM + lane + 32 * i]));
-    m = warp_max_int(m);
-    if (lane == 0) ry[k] = m;
+  for (int h = 0; h < 2; ++h) {
+    const int r = 32 * q + 2 * w + h;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[h][i] = X[(size_t)r * GM + 4 * lane + i];
   }
-  // stage this CTA's 32 columns of Y for (3)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cxw[w][4 * lane + i] = max(exp_floor(v[0][i]), exp_floor(v[1][i]));
   for (int i = tid; i < GM * 32; i += GPREP) ys[i / 32][i % 32] = Y[(size_t)(i / 32) * GM + 32 * q + i % 32];
   __syncthreads();
   if (tid < GM) {
     int a = kNoExp;
 #pragma unroll
-    for (int g = 0; g < GPREP / GM; ++g) a = max(a, cxp[g][tid]);
-    const int b = ry[tid];
+    for (int g = 0; g < NW; ++g) a = max(a, cxw[g][tid]);
+    cxq[tid] = a;
+    int b = kNoExp;
+    for (int j = 0; j < 32; ++j) b = max(b, exp_floor(ys[tid][j]));
+    ryq[tid] = b;
+  }
+  // (2) every CTA's partials published: t_k = floor((ry_k - cx_k) / 2)
+  cl.sync();
+  if (tid < GM) {
+    int a = kNoExp, b = kNoExp;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a = max(a, cl.map_shared_rank(cxq, r)[tid]);
+      b = max(b, cl.map_shared_rank(ryq, r)[tid]);
+    }
     tks[tid] = (a == kNoExp || b == kNoExp) ? kDropT : (b - a) >> 1;  // floor
   }
   __syncthreads();
   const int t[4] = {tks[4 * lane], tks[4 * lane + 1], tks[4 * lane + 2], tks[4 * lane + 3]};  // k = 4 lane + i
-  // (2) rows of X: x 2^t
-  for (int r = 32 * q + w; r < 32 * q + 32; r += NW) {
-    double v[4];
+  // (3) rows of X: x 2^t
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = X[(size_t)r * GM + 4 * lane + i];
+  for (int h = 0; h < 2; ++h) {
+    const int r = 32 * q + 2 * w + h;
     int m = kNoExp;
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      bad = bad || bits_nonfinite(v[i]);
-      const int x = exp_floor(v[i]);
+      bad = bad || bits_nonfinite(v[h][i]);
+      const int x = exp_floor(v[h][i]);
       if (x != kNoExp && t[i] != kDropT) m = max(m, x + t[i]);
     }
     m = warp_max_int(m);
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __rest
 #pragma unroll
         for (int p = 0; p < GD; ++p) d[i][p] = 0u;
       } else {
-        digits8(v[i], es - t[i], d[i]);  // round(v 2^t 2^(56 - es))
+        digits8(v[h][i], es - t[i], d[i]);  // round(v 2^t 2^(56 - es))
       }
     }
 #pragma unroll
@@ -246,16 +256,16 @@ __global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __rest
       *reinterpret_cast<uint2*>(Xd + (((size_t)e * GD + p) * GM + r) * GM + 4 * lane) =
           pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
   }
-  // (3) columns of Y: 2^-t y
+  // (4) columns of Y: 2^-t y
   for (int j = w; j < 32; j += NW) {
-    double v[4];  // rows 4 lane .. 4 lane + 3 of column 32 q + j
+    double y[4];  // rows 4 lane .. 4 lane + 3 of column 32 q + j
     int m = kNoExp;
     bool bad = false;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      v[i] = ys[4 * lane + i][j];
-      bad = bad || bits_nonfinite(v[i]);
-      const int x = exp_floor(v[i]);
+      y[i] = ys[4 * lane + i][j];
+      bad = bad || bits_nonfinite(y[i]);
+      const int x = exp_floor(y[i]);
       if (x != kNoExp && t[i] != kDropT) m = max(m, x - t[i]);
     }
     m = warp_max_int(m);
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __rest
 #pragma unroll
         for (int p = 0; p < GD; ++p) d[i][p] = 0u;
       } else {
-        digits8(v[i], es + t[i], d[i]);  // round(v 2^-t 2^(56 - es))
+        digits8(y[i], es + t[i], d[i]);  // round(v 2^-t 2^(56 - es))
       }
     }
 #pragma unroll
@@ -278,6 +288,7 @@ __global__ void __launch_bounds__(GPREP) k_gdig_prep(const double* const* __rest
       *reinterpret_cast<uint2*>(Yd + (((size_t)e * GD + p) * GM + c) * GM + 4 * lane) =
           pack_bf16x4(d[0][p], d[1][p], d[2][p], d[3][p]);
   }
+  cl.sync();  // no CTA leaves while a partner may still read its partial maxima
 }
 
 __global__ void __launch_bounds__(GTHREADS, 1)
@@ -470,7 +481,20 @@ bt_status digit_gemm_run(void* scratch, int emax, const double* const* dtab, int
   CUtensorMap tx, ty;
   BT_TRY(gd_map(&tx, Xd, (uint64_t)E * GD * GM, 64));
   BT_TRY(gd_map(&ty, Yd, (uint64_t)E * GD * GM, 128));
-  k_gdig_prep<<<(unsigned)(4 * E), GPREP, 0, st>>>(dtab, Xd, Yd, ex, ey);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(4 * E));
+    cfg.blockDim = dim3(GPREP);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 4;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BT_CUDA(cudaLaunchKernelEx(&cfg, k_gdig_prep, dtab, Xd, Yd, ex, ey));
+  }
   static bool attr = false;
   if (!attr) {
     BT_CUDA(cudaFuncSetAttribute(k_gemm_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GSMEM));
