@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* _
   const int c0 = rank * Mc, nc = max(0, min(Mc, M - c0));  // global columns c0 .. c0 + nc - 1
   const int ldu = M | 1;                                   // column stride (odd: the transposing load spreads banks)
   double* U = sh;                                          // [Mc][ldu]: local column j, row i
-  double* gbuf = U + (size_t)Mc * ldu;                     // [2][M] multipliers
+  double* gbuf = U + (((size_t)Mc * ldu + 1) & ~(size_t)1);  // [2][M] multipliers (16-byte aligned)
   double* rbuf = gbuf + 2 * M;                             // [2] 1 / pivot
   double* srow = rbuf + 2;                                 // [M] row scales
   int* pbuf = reinterpret_cast<int*>(srow + M);            // [2] pivot rows
@@ -308,15 +308,12 @@ __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* _
         bi = i;
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bb, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (oi != 0x7fffffff && (ob > bb || (ob == bb && oi < bi) || bi == 0x7fffffff)) {
-        bb = ob;
-        bi = oi;
-      }
-    }
-    const int p = bi;
+    // the warp's largest 64-bit key, then the lowest row holding it: three reductions
+    const unsigned kh = (unsigned)(bb >> 32), kl = (unsigned)bb;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, bi != 0x7fffffff ? kh : 0u);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, (bi != 0x7fffffff && kh == mh) ? kl : 0u);
+    const int p = (int)__reduce_min_sync(0xffffffffu, (bi != 0x7fffffff && kh == mh && kl == ml) ? (unsigned)bi
+                                                                                                : 0x7fffffffu);
     const double xp = col[p], xk = col[kk];
     double rinv = 0.0;
     if (lane == 0) {
@@ -328,13 +325,23 @@ __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* _
       rinv = recip_newton(pv);
     }
     rinv = __shfl_sync(0xffffffffu, rinv, 0);
-    for (int i = lane; i < M; i += 32) {
-      const double gi = (i == p ? xk : col[i]) * rinv;
-      for (int r = 0; r < C; ++r) {
-        if (r == rank)
-          gbuf[slot * M + i] = gi;
-        else
-          cl.map_shared_rank(gbuf, r)[slot * M + i] = gi;
+    if ((M & 1) == 0) {  // rows in pairs: 16-byte stores
+      for (int i = 2 * lane; i < M; i += 64) {
+        const double2 gi = make_double2((i == p ? xk : col[i]) * rinv, (i + 1 == p ? xk : col[i + 1]) * rinv);
+        for (int r = 0; r < C; ++r) {
+          double* gr = r == rank ? gbuf : cl.map_shared_rank(gbuf, r);
+          *reinterpret_cast<double2*>(gr + slot * M + i) = gi;
+        }
+      }
+    } else {
+      for (int i = lane; i < M; i += 32) {
+        const double gi = (i == p ? xk : col[i]) * rinv;
+        for (int r = 0; r < C; ++r) {
+          if (r == rank)
+            gbuf[slot * M + i] = gi;
+          else
+            cl.map_shared_rank(gbuf, r)[slot * M + i] = gi;
+        }
       }
     }
     if (lane < C) {
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(1024) k_inverse_cluster(const double* const* _
 // Shared memory and threads of k_inverse_cluster for block size M on clusters of C CTAs.
 size_t inv_cluster_smem(int M, int C) {
   const size_t Mc = (size_t)(M + C - 1) / C, ldu = (size_t)(M | 1);
-  return (Mc * ldu + 3 * (size_t)M + 2) * sizeof(double) + (2 + 2 * (size_t)M) * sizeof(int);
+  return (Mc * ldu + 1 + 3 * (size_t)M + 2) * sizeof(double) + (2 + 2 * (size_t)M) * sizeof(int);
 }
 int inv_cluster_threads(int M, int C) { return 32 * std::min(32, (M + C - 1) / C); }
 
